@@ -1,0 +1,212 @@
+/*
+ * kmeans2.h -- C ABI of libkmeans2, a GB300 (sm_103a) implementation of the
+ * two-stage k-means of Salman et al., "Fast k-means algorithm clustering"
+ * (arXiv 1108.1351).
+ *
+ * The method (Section 2, Algorithm): draw a random subset S_s (per% of the
+ * data S_n) and k random initial centers from it; run Lloyd iterations on S_s
+ * until the centers stop moving (fast stage); then run Lloyd iterations on the
+ * whole S_n starting from those centers (slow stage).  One Lloyd iteration
+ * (Section 4.1, Lloyd's method) is: squared distance of every point to every
+ * center (Eq. 1 without the root, the Algorithm's "modified distance"),
+ * nearest-center label, the objective J (Eq. 3), new centers = cluster means,
+ * and the stop test on the largest center movement (Sections 5-6).
+ *
+ * Conventions shared by every entry point
+ *  - X is row-major FP32, n rows of d values.  Centers are row-major FP64,
+ *    k rows of d values.  Labels are int32 in [0, k).
+ *  - Every pointer may be a device pointer (cudaMalloc, torch tensors) or a
+ *    host pointer (pageable or pinned); the library checks each with
+ *    cudaPointerGetAttributes and stages host buffers through device memory.
+ *    Host staging copies are part of the call.
+ *  - The caller owns every buffer it passes.  The library allocates only
+ *    scratch (stream-ordered, from the device's default memory pool) and
+ *    frees it before returning.
+ *  - All calls are synchronous with respect to the host: outputs are ready
+ *    when the call returns.  Work is issued on options->stream (NULL: the
+ *    legacy default stream).  Calls on different streams may run concurrently;
+ *    calls sharing output buffers must not.
+ *  - Return value: KMEANS2_OK (0) or a negative status; kmeans2_strerror()
+ *    names it.  On error no output is guaranteed to be written.  Reaching
+ *    max_iter without convergence is NOT an error (see kmeans2_result).
+ *  - Limits: 1 <= d <= 4096, 1 <= k <= n < 2^31, and k*d <= 2^24.
+ *
+ * Numerics (the results the library guarantees)
+ *  - Labels: for given FP64 centers, the label of every point equals the
+ *    index of the smallest FP64 squared distance sum_t fma(x_t - c_t, ...)
+ *    evaluated left to right, the lowest index winning exact ties.  The fast
+ *    FP32 distance kernels decide every point whose best and second-best
+ *    distances are farther apart than a rigorous rounding-error bound; the
+ *    other points are re-evaluated in exactly that FP64 form.
+ *  - Cluster sums are exact integer (fixed-point) sums of the FP32 inputs at a
+ *    per-stage scale 2^F, F = 46 - ceil(log2 max|x|) (so a center is off the
+ *    exact mean by at most 2^-(F+1) per coordinate), which makes every mode
+ *    deterministic: results do not depend on thread scheduling.
+ *  - J is evaluated as sum_i ||x_i||^2 - sum_j (2 c_j . S_j - N_j ||c_j||^2)
+ *    from exact sums, in FP64.
+ */
+#ifndef KMEANS2_H
+#define KMEANS2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KMEANS2_API __attribute__((visibility("default")))
+#else
+#define KMEANS2_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define KMEANS2_OK 0
+#define KMEANS2_ERR_INVALID (-1)      /* an argument is out of range or NULL */
+#define KMEANS2_ERR_NOMEM (-2)        /* device or pinned-host allocation failed */
+#define KMEANS2_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define KMEANS2_ERR_NONFINITE (-4)    /* X holds a NaN or an infinity */
+#define KMEANS2_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define KMEANS2_ERR_ADMISSION (-6)    /* a server refused a job (HBM budget) */
+#define KMEANS2_ERR_UNSUPPORTED (-7)  /* shape or mode not available on this build */
+
+/* ---------------------------------------------------------------- options */
+#define KMEANS2_PRECISION_FP32 0      /* FP32 CUDA-core distances + FP64 recheck */
+#define KMEANS2_PRECISION_BF16 1      /* BF16 tensor-core cross term + FP64 recheck */
+#define KMEANS2_PRECISION_AUTO 2      /* BF16 where d >= 32, else FP32 */
+
+/* Optional per-call measurement, filled by the library when options->profile
+   is set.  A profiled call runs each stage loop from the host (no graph) and
+   brackets every launch of the fused distance kernel with CUDA events on the
+   call's stream. */
+typedef struct kmeans2_profile {
+    int64_t kernel_launches;    /* kernels of this library launched by the call */
+    int64_t assign_launches;    /* launches of the fused distance kernel */
+    double assign_ms;           /* their summed CUDA-event time */
+    double assign_flops;        /* algorithmic 2*N*k*d summed over those launches */
+    double assign_bytes;        /* algorithmic 4*N*d (one read of X) summed */
+} kmeans2_profile;
+
+typedef struct kmeans2_options {
+    int32_t precision;          /* KMEANS2_PRECISION_*; default FP32 */
+    int32_t deterministic;      /* accepted for interface stability; every mode is
+                                   deterministic (exact integer cluster sums) */
+    double tol_fast;            /* stop tolerance of the fast stage; <= 0: use tol.
+                                   Section 5 uses 1e-3 fast / 1e-6 slow. */
+    const double* init_centers; /* k*d FP64 starting centers (host or device), or
+                                   NULL for the random draw of the Algorithm */
+    int32_t start_stage;        /* with init_centers: 0 = run both stages from them,
+                                   1 = skip the fast stage (resume a slow stage) */
+    int32_t use_graph;          /* 1 (default when options are NULL): run each stage
+                                   loop as one CUDA graph with a device-side while
+                                   loop; 0: one host round trip per iteration */
+    void* stream;               /* cudaStream_t, NULL = legacy default stream */
+    /* Optional HOST arrays of capacity max_iter receiving one value per
+       iteration (Figs. 4-11 and Table 1 track exactly these trajectories). */
+    double* traj_J_fast;
+    double* traj_shift_fast;
+    double* traj_J_slow;
+    double* traj_shift_slow;
+    kmeans2_profile* profile;   /* optional HOST struct, see kmeans2_profile */
+} kmeans2_options;
+
+/* Fill *opt with the defaults (FP32, tol_fast = tol, random init, graph loop). */
+KMEANS2_API void kmeans2_default_options(kmeans2_options* opt);
+
+typedef struct kmeans2_result {
+    double J;                   /* objective of the returned labels against the
+                                   centers they were assigned to (Eq. 3) */
+    int32_t iters_fast;         /* Q_f: fast-stage iterations, the detecting one counted */
+    int32_t iters_slow;         /* Q_s: slow-stage iterations */
+    int32_t converged_fast;     /* 1 if the fast stage met its tolerance */
+    int32_t converged_slow;     /* 1 if the slow stage met tol */
+    int32_t empty_clusters;     /* clusters left without points in the last iteration */
+    int32_t precision_used;     /* KMEANS2_PRECISION_FP32 or _BF16 */
+    int64_t subset_size;        /* m = |S_s| */
+    int64_t rechecked_points;   /* points re-evaluated in FP64, summed over iterations */
+    int64_t distance_evals;     /* K Q_f m + K Q_s n (Section 3 cost model) */
+    double shift_fast;          /* last fast-stage max center movement */
+    double shift_slow;          /* last slow-stage max center movement */
+    double seconds;             /* wall time of the call */
+} kmeans2_result;
+
+/* ---------------------------------------------------------------- entry points */
+
+/*
+ * kmeans2_fit -- the whole two-stage method (Section 2, Algorithm).
+ *
+ *  X             n*d FP32 points S_n (host or device).
+ *  subset_fraction  per, in (0, 1]; m = min(n, max(k, ceil(per*n))) points form S_s.
+ *  seed          drives both random draws (see kmeans2_sample).
+ *  tol           slow-stage stop tolerance on max_j ||c_j' - c_j||_2 (absolute);
+ *                the fast stage uses options->tol_fast when > 0.
+ *  max_iter      per-stage iteration cap (>= 1).
+ *  centers_out   k*d FP64 (host or device): the slow stage's last updated centers.
+ *  labels_out    n int32 (host or device): the last slow-stage assignment,
+ *                made against the centers before that last update.
+ *  res           host struct, may be NULL.
+ *  opt           may be NULL (defaults).
+ * Errors: KMEANS2_ERR_INVALID (n < 1, d < 1, k < 1, k > n, per outside (0, 1],
+ * tol < 0 or NaN, max_iter < 1, NULL X/centers_out/labels_out, limits above),
+ * KMEANS2_ERR_NONFINITE, KMEANS2_ERR_NOMEM, KMEANS2_ERR_CUDA.
+ */
+KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_fraction,
+                uint64_t seed, double tol, int32_t max_iter, double* centers_out,
+                int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt);
+
+/*
+ * kmeans_step -- one Lloyd iteration (Section 4.1; the loop body of the
+ * Algorithm) from given centers.
+ *
+ *  centers_in    k*d FP64 (host or device), the centers the points are assigned to.
+ *  centers_out   k*d FP64 (host or device): cluster means; an empty cluster
+ *                keeps its center.  May equal centers_in.
+ *  labels_out    n int32 (host or device).
+ *  J_out         host, may be NULL: J of this assignment against centers_in (Eq. 3).
+ *  shift_out     host, may be NULL: max_j ||c_j' - c_j||_2.
+ *  empty_out     host, may be NULL: number of empty clusters.
+ * Errors as kmeans2_fit.
+ */
+KMEANS2_API int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, const double* centers_in,
+                double* centers_out, int32_t* labels_out, double* J_out, double* shift_out,
+                int32_t* empty_out, const kmeans2_options* opt);
+
+/*
+ * kmeans2_subset_size -- m = min(n, max(k, ceil(per*n))), the size of S_s
+ * (Algorithm: "S_n = per% of S_n"; at least k points so that k distinct
+ * initial centers exist).  Host only; returns -1 on invalid arguments.
+ */
+KMEANS2_API int64_t kmeans2_subset_size(int64_t n, int32_t k, double subset_fraction);
+
+/*
+ * kmeans2_sample -- the random draws of the Algorithm ("S_n = per% of S_n",
+ * "Select X_c from S_n randomly"), computed on the GPU.
+ *
+ * SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) is used as a counter-based
+ * generator: key_i = mix64(seed + (i+1) * 0x9E3779B97F4A7C15).  S_s is the set
+ * of the m indices i in [0, n) with the smallest key_i, written ascending to
+ * subset_out (m int64).  The initial centers are the k positions p in [0, m)
+ * with the smallest key_{n+p}, written in increasing key order to
+ * init_pos_out (k int64): center j is X[subset_out[init_pos_out[j]]].
+ * Both outputs may be host or device pointers.
+ */
+KMEANS2_API int kmeans2_sample(int64_t n, int32_t k, double subset_fraction, uint64_t seed,
+                   int64_t* subset_out, int64_t* init_pos_out, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+KMEANS2_API const char* kmeans2_strerror(int status);
+
+/* Detail of the last failure on the calling thread (the failing CUDA call and
+   its error string), or "" if none.  Thread-local storage, valid until the
+   thread's next failing call. */
+KMEANS2_API const char* kmeans2_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+KMEANS2_API int32_t kmeans2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMEANS2_H */

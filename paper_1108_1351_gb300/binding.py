@@ -1,0 +1,308 @@
+"""ctypes binding of libkmeans2 (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts torch
+tensors / numpy arrays to pointers, picks torch's current stream and wraps the
+results.  It never falls back to another implementation: if the shared object
+is missing it raises, telling the caller to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkmeans2.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "kmeans2.h")
+
+PRECISION = {"fp32": 0, "bf16": 1, "auto": 2}
+_lock = threading.Lock()
+_lib = None
+
+
+class KMeans2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.kmeans2_strerror(status).decode()
+        detail = lib.kmeans2_last_error().decode()
+        super().__init__(f"{where}: {msg} (status {status})" + (f" [{detail}]" if detail else ""))
+        self.status = status
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("kernel_launches", ctypes.c_int64),
+        ("assign_launches", ctypes.c_int64),
+        ("assign_ms", ctypes.c_double),
+        ("assign_flops", ctypes.c_double),
+        ("assign_bytes", ctypes.c_double),
+    ]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("deterministic", ctypes.c_int32),
+        ("tol_fast", ctypes.c_double),
+        ("init_centers", ctypes.c_void_p),
+        ("start_stage", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("traj_J_fast", ctypes.c_void_p),
+        ("traj_shift_fast", ctypes.c_void_p),
+        ("traj_J_slow", ctypes.c_void_p),
+        ("traj_shift_slow", ctypes.c_void_p),
+        ("profile", ctypes.c_void_p),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("J", ctypes.c_double),
+        ("iters_fast", ctypes.c_int32),
+        ("iters_slow", ctypes.c_int32),
+        ("converged_fast", ctypes.c_int32),
+        ("converged_slow", ctypes.c_int32),
+        ("empty_clusters", ctypes.c_int32),
+        ("precision_used", ctypes.c_int32),
+        ("subset_size", ctypes.c_int64),
+        ("rechecked_points", ctypes.c_int64),
+        ("distance_evals", ctypes.c_int64),
+        ("shift_fast", ctypes.c_double),
+        ("shift_slow", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+
+def load():
+    """Load libkmeans2.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u64, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                 ctypes.c_uint64, ctypes.c_double)
+        lib.kmeans2_default_options.restype = None
+        lib.kmeans2_default_options.argtypes = [ctypes.POINTER(Options)]
+        lib.kmeans2_fit.restype = ctypes.c_int
+        lib.kmeans2_fit.argtypes = [P, i64, i32, i32, f64, u64, f64, i32, P, P,
+                                    ctypes.POINTER(Result), ctypes.POINTER(Options)]
+        lib.kmeans_step.restype = ctypes.c_int
+        lib.kmeans_step.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, ctypes.POINTER(Options)]
+        lib.kmeans2_subset_size.restype = i64
+        lib.kmeans2_subset_size.argtypes = [i64, i32, f64]
+        lib.kmeans2_sample.restype = ctypes.c_int
+        lib.kmeans2_sample.argtypes = [i64, i32, f64, u64, P, P, P]
+        lib.kmeans2_strerror.restype = ctypes.c_char_p
+        lib.kmeans2_strerror.argtypes = [ctypes.c_int]
+        lib.kmeans2_last_error.restype = ctypes.c_char_p
+        lib.kmeans2_last_error.argtypes = []
+        lib.kmeans2_version.restype = i32
+        lib.kmeans2_version.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    """Names of the entry points declared in include/kmeans2.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"KMEANS2_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)))
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _is_torch(a) -> bool:
+    return isinstance(a, torch.Tensor)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _as_points(X):
+    if _is_torch(X):
+        if X.dtype != torch.float32 or X.dim() != 2:
+            raise TypeError("X must be a 2-D float32 tensor")
+        return X.contiguous()
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    if X.ndim != 2:
+        raise TypeError("X must be 2-D")
+    return X
+
+
+def _as_centers(C, like):
+    if C is None:
+        return None
+    if _is_torch(C):
+        return C.to(dtype=torch.float64).contiguous()
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    if _is_torch(like) and like.is_cuda:
+        return torch.as_tensor(C, device=like.device)
+    return C
+
+
+def _empty(like, shape, kind):
+    if _is_torch(like):
+        dt = {"f64": torch.float64, "i32": torch.int32, "i64": torch.int64}[kind]
+        return torch.empty(shape, dtype=dt, device=like.device)
+    dt = {"f64": np.float64, "i32": np.int32, "i64": np.int64}[kind]
+    return np.empty(shape, dtype=dt)
+
+
+def _stream_of(X, stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    if _is_torch(X) and X.is_cuda:
+        return torch.cuda.current_stream(X.device).cuda_stream
+    return None
+
+
+class _device_of:
+    """Make X's device current for the call (the library uses the current device)."""
+
+    def __init__(self, X):
+        self.dev = X.device if (_is_torch(X) and X.is_cuda) else None
+
+    def __enter__(self):
+        self.ctx = torch.cuda.device(self.dev) if self.dev is not None else None
+        if self.ctx is not None:
+            self.ctx.__enter__()
+
+    def __exit__(self, *a):
+        if self.ctx is not None:
+            self.ctx.__exit__(*a)
+
+
+@dataclass
+class FitResult:
+    centers: object
+    labels: object
+    J: float
+    iters_fast: int
+    iters_slow: int
+    converged_fast: bool
+    converged_slow: bool
+    empty_clusters: int
+    subset_size: int
+    rechecked_points: int
+    distance_evals: int
+    shift_fast: float
+    shift_slow: float
+    seconds: float
+    precision_used: str
+    traj: dict = field(default_factory=dict)
+
+
+def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int, *,
+        tol_fast: float = 0.0, precision: str = "fp32", init_centers=None, start_stage: int = 0,
+        use_graph: bool = True, stream=None, trajectories: bool = False, centers_out=None,
+        labels_out=None, profile: "Profile | None" = None) -> FitResult:
+    """Two-stage k-means (kmeans2_fit).  Outputs live where X lives (device
+    tensors for a CUDA tensor, host arrays otherwise) unless given."""
+    lib = load()
+    X = _as_points(X)
+    n, d = X.shape
+    C0 = _as_centers(init_centers, X)
+    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
+    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    opt = Options()
+    lib.kmeans2_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION[precision]
+    opt.tol_fast = tol_fast
+    opt.init_centers = _ptr(C0)
+    opt.start_stage = start_stage
+    opt.use_graph = 1 if use_graph else 0
+    opt.stream = _stream_of(X, stream)
+    opt.profile = ctypes.addressof(profile) if profile is not None else None
+    traj = {}
+    if trajectories:
+        for key in ("J_fast", "shift_fast", "J_slow", "shift_slow"):
+            traj[key] = np.zeros(max_iter, dtype=np.float64)
+            setattr(opt, "traj_" + key, traj[key].ctypes.data)
+    res = Result()
+    with _device_of(X):
+        rc = lib.kmeans2_fit(_ptr(X), n, d, k, subset_fraction, seed & (2**64 - 1), tol, max_iter,
+                             _ptr(cen), _ptr(lab), ctypes.byref(res), ctypes.byref(opt))
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans2_fit")
+    if trajectories:
+        traj = {"J_fast": traj["J_fast"][:res.iters_fast], "shift_fast": traj["shift_fast"][:res.iters_fast],
+                "J_slow": traj["J_slow"][:res.iters_slow], "shift_slow": traj["shift_slow"][:res.iters_slow]}
+    return FitResult(centers=cen, labels=lab, J=res.J, iters_fast=res.iters_fast,
+                     iters_slow=res.iters_slow, converged_fast=bool(res.converged_fast),
+                     converged_slow=bool(res.converged_slow), empty_clusters=res.empty_clusters,
+                     subset_size=res.subset_size, rechecked_points=res.rechecked_points,
+                     distance_evals=res.distance_evals, shift_fast=res.shift_fast,
+                     shift_slow=res.shift_slow, seconds=res.seconds,
+                     precision_used={0: "fp32", 1: "bf16"}.get(res.precision_used, "?"), traj=traj)
+
+
+def step(X, centers, *, precision: str = "fp32", stream=None, centers_out=None, labels_out=None,
+         profile: "Profile | None" = None):
+    """One Lloyd iteration (kmeans_step): returns (centers', labels, J, shift, empty)."""
+    lib = load()
+    X = _as_points(X)
+    n, d = X.shape
+    C = _as_centers(centers, X)
+    k = C.shape[0]
+    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
+    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    J = ctypes.c_double()
+    sh = ctypes.c_double()
+    em = ctypes.c_int32()
+    opt = Options()
+    lib.kmeans2_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION[precision]
+    opt.stream = _stream_of(X, stream)
+    opt.profile = ctypes.addressof(profile) if profile is not None else None
+    with _device_of(X):
+        rc = lib.kmeans_step(_ptr(X), n, d, k, _ptr(C), _ptr(cen), _ptr(lab), ctypes.addressof(J),
+                             ctypes.addressof(sh), ctypes.addressof(em), ctypes.byref(opt))
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans_step")
+    return cen, lab, J.value, sh.value, em.value
+
+
+def subset_size(n: int, k: int, subset_fraction: float) -> int:
+    return int(load().kmeans2_subset_size(n, k, subset_fraction))
+
+
+def sample(n: int, k: int, subset_fraction: float, seed: int, device="cuda", stream=None):
+    """GPU draw of S_s and of the initial-center positions (kmeans2_sample)."""
+    lib = load()
+    m = subset_size(n, k, subset_fraction)
+    if m < 0:
+        raise ValueError("invalid sampling arguments")
+    dev = torch.device(device)
+    sub = torch.empty(m, dtype=torch.int64, device=dev)
+    pos = torch.empty(k, dtype=torch.int64, device=dev)
+    s = _stream_of(sub, stream)
+    with _device_of(sub):
+        rc = lib.kmeans2_sample(n, k, subset_fraction, seed & (2**64 - 1), sub.data_ptr(),
+                                pos.data_ptr(), s)
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans2_sample")
+    return sub, pos
+
+
+def strerror(status: int) -> str:
+    return load().kmeans2_strerror(status).decode()
+
+
+def version() -> tuple[int, int]:
+    v = int(load().kmeans2_version())
+    return v >> 16, v & 0xFFFF

@@ -1,0 +1,532 @@
+// api.cu -- the C ABI of libkmeans2 and the host-side orchestration of the
+// two-stage method (Section 2, Algorithm): draw S_s and the initial centers,
+// run the Lloyd loop on S_s (fast stage), then on S_n from the fast stage's
+// final centers (slow stage).
+//
+// One stage = stage_init, then per iteration: assign (fused distance, argmin,
+// exact sums) -> recheck (FP64 near ties) -> finalize (means, movement, J,
+// loop control).  With use_graph the iteration body is captured once into the
+// body of a CUDA-graph WHILE node whose condition finalize sets on the device,
+// so a whole stage is one graph launch with no host round trip per iteration.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace km2 {
+
+thread_local long long g_launches = 0;
+
+namespace {
+thread_local char g_last_error[512] = "";
+}
+
+void set_last_error(const char* where, cudaError_t e)
+{
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e),
+                  (int)e);
+}
+
+void set_last_error_text(const char* text)
+{
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s", text);
+}
+
+const char* last_error() { return g_last_error; }
+
+DeviceScratch::DeviceScratch(cudaStream_t s) : stream(s)
+{
+    cudaGetDevice(&device);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (sm_count < 1) sm_count = 1;
+}
+
+DeviceScratch::~DeviceScratch()
+{
+    for (void* p : ptrs) cudaFreeAsync(p, stream);
+}
+
+int DeviceScratch::alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        set_last_error("cudaMallocAsync", e);
+        cudaGetLastError();
+        *p = nullptr;
+        return KMEANS2_ERR_NOMEM;
+    }
+    ptrs.push_back(*p);
+    return KMEANS2_OK;
+}
+
+namespace {
+
+__global__ void fill_f32_kernel(float* p, long long count, float v)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+int fill_f32(float* p, long long count, float v, cudaStream_t s)
+{
+    if (count <= 0) return KMEANS2_OK;
+    int grid = (int)((count + 255) / 256);
+    if (grid > 1024) grid = 1024;
+    ++g_launches;
+    fill_f32_kernel<<<grid, 256, 0, s>>>(p, count, v);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+// True if p is memory the current device addresses as device memory.
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A private blocking stream per thread and device, used when the caller passes
+// the legacy default stream (which cannot be captured into a graph).
+cudaStream_t private_stream(int device)
+{
+    static thread_local cudaStream_t streams[64] = {};
+    if (device < 0 || device >= 64) return nullptr;
+    if (!streams[device]) cudaStreamCreate(&streams[device]);
+    return streams[device];
+}
+
+struct Workspace {
+    Centers c{};
+    Accum acc{};
+    StageState* st = nullptr;
+    int* list = nullptr;
+    double* clus = nullptr;
+    double* traj_J = nullptr;      // max_iter
+    double* traj_shift = nullptr;  // max_iter
+    int max_iter = 0;
+};
+
+int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, int d,
+                    int max_iter, cudaStream_t s)
+{
+    w.c.k = k;
+    w.c.d = d;
+    w.c.kpad = (k + 127) / 128 * 128;
+    w.c.dpad = (d + 7) / 8 * 8;
+    w.max_iter = max_iter;
+    size_t kd = (size_t)k * d;
+    KM2_TRY(ws.alloc((void**)&w.c.c64, kd * sizeof(double), s));
+    KM2_TRY(ws.alloc((void**)&w.c.c32, kd * sizeof(float), s));
+    KM2_TRY(ws.alloc((void**)&w.c.c32t, (size_t)w.c.dpad * w.c.kpad * sizeof(float), s));
+    KM2_TRY(ws.alloc((void**)&w.c.cnorm, (size_t)w.c.kpad * sizeof(float), s));
+    KM2_TRY(ws.alloc((void**)&w.acc.s_lo, kd * 8, s));
+    KM2_TRY(ws.alloc((void**)&w.acc.s_hi, kd * 8, s));
+    KM2_TRY(ws.alloc((void**)&w.acc.cnt, (size_t)k * 8, s));
+    KM2_TRY(ws.alloc((void**)&w.st, sizeof(StageState), s));
+    KM2_TRY(ws.alloc((void**)&w.list, (size_t)(list_cap > 0 ? list_cap : 1) * sizeof(int), s));
+    KM2_TRY(ws.alloc((void**)&w.clus, (size_t)4 * k * sizeof(double), s));
+    KM2_TRY(ws.alloc((void**)&w.traj_J, (size_t)max_iter * sizeof(double), s));
+    KM2_TRY(ws.alloc((void**)&w.traj_shift, (size_t)max_iter * sizeof(double), s));
+    KM2_CUDA(cudaMemsetAsync(w.c.c32t, 0, (size_t)w.c.dpad * w.c.kpad * sizeof(float), s));
+    KM2_TRY(fill_f32(w.c.cnorm, w.c.kpad, INFINITY, s));
+    return KMEANS2_OK;
+}
+
+// One Lloyd iteration: assign -> recheck -> finalize.
+int launch_iteration(const float* X, long long n, int d, Workspace& w, int* labels,
+                     unsigned long long handle, int use_cond, cudaStream_t s, int sm_count)
+{
+    KM2_TRY(launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count));
+    KM2_TRY(launch_recheck(X, d, w.c, labels, w.list, w.st, w.acc, s, sm_count));
+    KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, handle, use_cond,
+                            s));
+    return KMEANS2_OK;
+}
+
+// The stage loop as one graph: a WHILE conditional node whose body is one iteration.
+int run_loop_graph(const float* X, long long n, int d, Workspace& w, int* labels, cudaStream_t s,
+                   int sm_count)
+{
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = KMEANS2_OK;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) { set_last_error("cudaGraphCreate", e); return KMEANS2_ERR_CUDA; }
+    do {
+        cudaGraphConditionalHandle handle;
+        e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { set_last_error("cudaGraphConditionalHandleCreate", e); rc = KMEANS2_ERR_CUDA; break; }
+        // cudaGraphNodeParams has no default constructor: build it zeroed in raw storage.
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+        std::memset(raw, 0, sizeof(raw));
+        cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(raw);
+        p->type = cudaGraphNodeTypeConditional;
+        p->conditional.handle = handle;
+        p->conditional.type = cudaGraphCondTypeWhile;
+        p->conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, p);
+        if (e != cudaSuccess) { set_last_error("cudaGraphAddNode", e); rc = KMEANS2_ERR_CUDA; break; }
+        cudaGraph_t body = p->conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { set_last_error("cudaStreamBeginCaptureToGraph", e); rc = KMEANS2_ERR_CUDA; break; }
+        rc = launch_iteration(X, n, d, w, labels, (unsigned long long)handle, 1, s, sm_count);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(s, &captured);
+        if (rc != KMEANS2_OK) break;
+        if (e != cudaSuccess) { set_last_error("cudaStreamEndCapture", e); rc = KMEANS2_ERR_CUDA; break; }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) { set_last_error("cudaGraphInstantiate", e); rc = KMEANS2_ERR_CUDA; break; }
+        e = cudaGraphLaunch(exec, s);
+        if (e != cudaSuccess) { set_last_error("cudaGraphLaunch", e); rc = KMEANS2_ERR_CUDA; break; }
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_last_error("cudaStreamSynchronize", e); rc = KMEANS2_ERR_CUDA; break; }
+        int iters = 0;
+        e = cudaMemcpy(&iters, &w.st->iter, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { set_last_error("cudaMemcpy", e); rc = KMEANS2_ERR_CUDA; break; }
+        g_launches += 3ll * (iters > 1 ? iters - 1 : 0);   // body kernels per executed iteration
+    } while (0);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
+// Host-driven loop; with a profile, CUDA events bracket each distance-kernel launch.
+int run_loop_host(const float* X, long long n, int d, Workspace& w, int* labels, int max_iter,
+                  cudaStream_t s, int sm_count, kmeans2_profile* prof)
+{
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (prof) {
+        KM2_CUDA(cudaEventCreate(&ev0));
+        KM2_CUDA(cudaEventCreate(&ev1));
+    }
+    int rc = KMEANS2_OK;
+    for (int it = 0; it < max_iter && rc == KMEANS2_OK; ++it) {
+        if (prof) {
+            cudaEventRecord(ev0, s);
+            rc = launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
+            cudaEventRecord(ev1, s);
+            if (rc == KMEANS2_OK)
+                rc = launch_recheck(X, d, w.c, labels, w.list, w.st, w.acc, s, sm_count);
+            if (rc == KMEANS2_OK)
+                rc = launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, 0ull, 0, s);
+        } else {
+            rc = launch_iteration(X, n, d, w, labels, 0ull, 0, s, sm_count);
+        }
+        if (rc != KMEANS2_OK) break;
+        int done = 0;
+        cudaError_t e = cudaMemcpyAsync(&done, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_last_error("stage loop", e); rc = KMEANS2_ERR_CUDA; break; }
+        if (prof) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            prof->assign_launches += 1;
+            prof->assign_ms += ms;
+            prof->assign_flops += 2.0 * (double)n * w.c.k * d;
+            prof->assign_bytes += 4.0 * (double)n * d;
+        }
+        if (done) break;
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    return rc;
+}
+
+int map_stage_error(int err)
+{
+    if (err == kErrNonFinite) {
+        set_last_error_text("X holds a NaN or an infinity");
+        return KMEANS2_ERR_NONFINITE;
+    }
+    set_last_error_text("max|x| >= 2^50 is outside the supported range");
+    return KMEANS2_ERR_UNSUPPORTED;
+}
+
+// Run one stage on device-resident X (n x d) from the centers in w.c (FP64
+// master already set).  The caller has zeroed w.st and recorded max|x| in it.
+int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, double tol,
+              int max_iter, bool use_graph, cudaStream_t s, int sm_count, StageState& out,
+              double* traj_J_host, double* traj_shift_host, kmeans2_profile* prof)
+{
+    size_t kd = (size_t)w.c.k * d;
+    KM2_CUDA(cudaMemsetAsync(w.acc.s_lo, 0, kd * 8, s));
+    KM2_CUDA(cudaMemsetAsync(w.acc.s_hi, 0, kd * 8, s));
+    KM2_CUDA(cudaMemsetAsync(w.acc.cnt, 0, (size_t)w.c.k * 8, s));
+    KM2_TRY(launch_center_prep(w.c, w.st, s));
+    KM2_TRY(launch_stage_init(w.st, d, tol, max_iter, s));
+    if (use_graph && !prof)
+        KM2_TRY(run_loop_graph(X, n, d, w, labels, s, sm_count));
+    else
+        KM2_TRY(run_loop_host(X, n, d, w, labels, max_iter, s, sm_count, prof));
+    KM2_CUDA(cudaMemcpyAsync(&out, w.st, sizeof(StageState), cudaMemcpyDeviceToHost, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    if (out.error) return map_stage_error(out.error);
+    if (traj_J_host && out.iter > 0)
+        KM2_CUDA(cudaMemcpyAsync(traj_J_host, w.traj_J, sizeof(double) * out.iter,
+                                 cudaMemcpyDeviceToHost, s));
+    if (traj_shift_host && out.iter > 0)
+        KM2_CUDA(cudaMemcpyAsync(traj_shift_host, w.traj_shift, sizeof(double) * out.iter,
+                                 cudaMemcpyDeviceToHost, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    return KMEANS2_OK;
+}
+
+bool valid_shape(long long n, int d, int k)
+{
+    return n >= 1 && d >= 1 && d <= 4096 && k >= 1 && k <= n && n < (1ll << 31) &&
+           (long long)k * d <= (1ll << 24);
+}
+
+// Device-resident, 16-byte aligned view of X (staged through scratch when needed).
+int device_view(const float* X, long long count, const float** out, DeviceScratch& ws,
+                cudaStream_t s)
+{
+    bool dev = is_device_ptr(X);
+    if (dev && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+        *out = X;
+        return KMEANS2_OK;
+    }
+    float* buf = nullptr;
+    KM2_TRY(ws.alloc((void**)&buf, (size_t)count * sizeof(float), s));
+    KM2_CUDA(cudaMemcpyAsync(buf, X, (size_t)count * sizeof(float),
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    *out = buf;
+    return KMEANS2_OK;
+}
+
+struct Resolved {
+    cudaStream_t stream;
+    kmeans2_options opt;
+};
+
+Resolved resolve_options(const kmeans2_options* opt)
+{
+    Resolved r;
+    kmeans2_default_options(&r.opt);
+    if (opt) r.opt = *opt;
+    r.stream = static_cast<cudaStream_t>(r.opt.stream);
+    if (!r.stream) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        r.stream = private_stream(dev);
+    }
+    return r;
+}
+
+}  // namespace
+
+}  // namespace km2
+
+using namespace km2;
+
+extern "C" {
+
+void kmeans2_default_options(kmeans2_options* opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = KMEANS2_PRECISION_FP32;
+    opt->deterministic = 1;
+    opt->use_graph = 1;
+}
+
+int64_t kmeans2_subset_size(int64_t n, int32_t k, double f)
+{
+    if (n < 1 || k < 1 || k > n || !(f > 0.0 && f <= 1.0)) return -1;
+    double want = std::ceil(f * (double)n);
+    int64_t m = (int64_t)want;
+    if (m < k) m = k;
+    if (m > n) m = n;
+    return m;
+}
+
+const char* kmeans2_strerror(int status)
+{
+    switch (status) {
+        case KMEANS2_OK: return "ok";
+        case KMEANS2_ERR_INVALID: return "invalid argument";
+        case KMEANS2_ERR_NOMEM: return "out of memory";
+        case KMEANS2_ERR_CUDA: return "CUDA error";
+        case KMEANS2_ERR_NONFINITE: return "input holds NaN or infinity";
+        case KMEANS2_ERR_TIMEOUT: return "device wait timed out";
+        case KMEANS2_ERR_ADMISSION: return "admission refused";
+        case KMEANS2_ERR_UNSUPPORTED: return "unsupported shape or mode";
+        default: return "unknown status";
+    }
+}
+
+const char* kmeans2_last_error(void) { return km2::last_error(); }
+
+int32_t kmeans2_version(void) { return (1 << 16) | 0; }
+
+int kmeans2_sample(int64_t n, int32_t k, double f, uint64_t seed, int64_t* subset_out,
+                   int64_t* init_pos_out, void* stream)
+{
+    int64_t m = kmeans2_subset_size(n, k, f);
+    if (m < 0 || !subset_out || !init_pos_out || n >= (1ll << 40)) return KMEANS2_ERR_INVALID;
+    kmeans2_options o;
+    kmeans2_default_options(&o);
+    o.stream = stream;
+    Resolved r = resolve_options(&o);
+    cudaStream_t s = r.stream;
+    DeviceScratch ws(s);
+    bool sub_dev = is_device_ptr(subset_out), pos_dev = is_device_ptr(init_pos_out);
+    long long* sub = sub_dev ? (long long*)subset_out : nullptr;
+    long long* pos = pos_dev ? (long long*)init_pos_out : nullptr;
+    if (!sub) KM2_TRY(ws.alloc((void**)&sub, sizeof(long long) * (size_t)m, s));
+    if (!pos) KM2_TRY(ws.alloc((void**)&pos, sizeof(long long) * (size_t)k, s));
+    KM2_TRY(sample_device(n, k, m, seed, sub, pos, s, ws));
+    if (!sub_dev)
+        KM2_CUDA(cudaMemcpyAsync(subset_out, sub, sizeof(long long) * (size_t)m,
+                                 cudaMemcpyDeviceToHost, s));
+    if (!pos_dev)
+        KM2_CUDA(cudaMemcpyAsync(init_pos_out, pos, sizeof(long long) * (size_t)k,
+                                 cudaMemcpyDeviceToHost, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    return KMEANS2_OK;
+}
+
+int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, const double* centers_in,
+                double* centers_out, int32_t* labels_out, double* J_out, double* shift_out,
+                int32_t* empty_out, const kmeans2_options* opt)
+{
+    if (!X || !centers_in || !centers_out || !labels_out || !valid_shape(n, d, k))
+        return KMEANS2_ERR_INVALID;
+    Resolved r = resolve_options(opt);
+    if (r.opt.precision != KMEANS2_PRECISION_FP32 && r.opt.precision != KMEANS2_PRECISION_AUTO)
+        return KMEANS2_ERR_UNSUPPORTED;
+    const long long launches0 = g_launches;
+    cudaStream_t s = r.stream;
+    DeviceScratch ws(s);
+    const float* Xd = nullptr;
+    KM2_TRY(device_view(X, (long long)n * d, &Xd, ws, s));
+    Workspace w;
+    KM2_TRY(alloc_workspace(w, ws, n, k, d, 1, s));
+    bool lab_dev = is_device_ptr(labels_out) && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
+    int* labels = lab_dev ? labels_out : nullptr;
+    if (!labels) KM2_TRY(ws.alloc((void**)&labels, sizeof(int) * (size_t)n, s));
+    KM2_CUDA(cudaMemcpyAsync(w.c.c64, centers_in, sizeof(double) * (size_t)k * d,
+                             is_device_ptr(centers_in) ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice, s));
+    KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
+    KM2_TRY(launch_maxabs(Xd, (long long)n * d, w.st, s, ws.sm_count));
+    StageState out;
+    KM2_TRY(run_stage(Xd, n, d, w, labels, 0.0, 1, false, s, ws.sm_count, out, nullptr, nullptr,
+                      r.opt.profile));
+    KM2_CUDA(cudaMemcpyAsync(centers_out, w.c.c64, sizeof(double) * (size_t)k * d,
+                             is_device_ptr(centers_out) ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyDeviceToHost, s));
+    if (!lab_dev)
+        KM2_CUDA(cudaMemcpyAsync(labels_out, labels, sizeof(int) * (size_t)n,
+                                 is_device_ptr(labels_out) ? cudaMemcpyDeviceToDevice
+                                                           : cudaMemcpyDeviceToHost, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    if (J_out) *J_out = out.J;
+    if (shift_out) *shift_out = out.shift;
+    if (empty_out) *empty_out = out.empty;
+    if (r.opt.profile) r.opt.profile->kernel_launches += g_launches - launches0;
+    return KMEANS2_OK;
+}
+
+int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_fraction,
+                uint64_t seed, double tol, int32_t max_iter, double* centers_out,
+                int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = g_launches;
+    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) ||
+        !(subset_fraction > 0.0 && subset_fraction <= 1.0) || !(tol >= 0.0) || max_iter < 1)
+        return KMEANS2_ERR_INVALID;
+    Resolved r = resolve_options(opt);
+    const kmeans2_options& o = r.opt;
+    if (o.precision != KMEANS2_PRECISION_FP32 && o.precision != KMEANS2_PRECISION_AUTO)
+        return KMEANS2_ERR_UNSUPPORTED;
+    if (o.start_stage != 0 && o.start_stage != 1) return KMEANS2_ERR_INVALID;
+    if (o.start_stage == 1 && !o.init_centers) return KMEANS2_ERR_INVALID;
+    const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
+    const bool use_graph = o.use_graph != 0;
+    cudaStream_t s = r.stream;
+    DeviceScratch ws(s);
+
+    const long long m = kmeans2_subset_size(n, k, subset_fraction);
+    const float* Xd = nullptr;
+    KM2_TRY(device_view(X, (long long)n * d, &Xd, ws, s));
+    Workspace w;
+    KM2_TRY(alloc_workspace(w, ws, n, k, d, max_iter, s));
+    bool lab_dev = is_device_ptr(labels_out) && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
+    int* labels = lab_dev ? labels_out : nullptr;
+    if (!labels) KM2_TRY(ws.alloc((void**)&labels, sizeof(int) * (size_t)n, s));
+
+    kmeans2_result rr;
+    std::memset(&rr, 0, sizeof(rr));
+    rr.precision_used = KMEANS2_PRECISION_FP32;
+    rr.subset_size = m;
+    StageState fs;
+    std::memset(&fs, 0, sizeof(fs));
+
+    if (o.init_centers) {
+        KM2_CUDA(cudaMemcpyAsync(w.c.c64, o.init_centers, sizeof(double) * (size_t)k * d,
+                                 is_device_ptr(o.init_centers) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice, s));
+    }
+    if (o.start_stage == 0) {
+        // fast stage on S_s (Algorithm: "S_n = per% of S_n", "Select X_c from S_n randomly")
+        long long* subset = nullptr;
+        long long* pos = nullptr;
+        float* Xs = nullptr;
+        int* labels_s = nullptr;
+        KM2_TRY(ws.alloc((void**)&subset, sizeof(long long) * (size_t)m, s));
+        KM2_TRY(ws.alloc((void**)&pos, sizeof(long long) * (size_t)k, s));
+        KM2_TRY(ws.alloc((void**)&Xs, sizeof(float) * (size_t)m * d, s));
+        KM2_TRY(ws.alloc((void**)&labels_s, sizeof(int) * (size_t)m, s));
+        KM2_TRY(sample_device(n, k, m, seed, subset, pos, s, ws));
+        KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
+        KM2_TRY(launch_gather(Xd, d, subset, m, Xs, w.st, s, ws.sm_count));
+        if (!o.init_centers) KM2_TRY(launch_init_centers(Xs, d, pos, k, w.c.c64, s));
+        KM2_TRY(run_stage(Xs, m, d, w, labels_s, tol_fast, max_iter, use_graph, s, ws.sm_count,
+                          fs, o.traj_J_fast, o.traj_shift_fast, o.profile));
+        rr.iters_fast = fs.iter;
+        rr.converged_fast = fs.converged;
+        rr.shift_fast = fs.shift;
+        rr.rechecked_points += fs.rechecked_total;
+    }
+    // slow stage on S_n from the fast stage's final centers (Section 2; Section 5)
+    KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
+    KM2_TRY(launch_maxabs(Xd, (long long)n * d, w.st, s, ws.sm_count));
+    StageState ss;
+    KM2_TRY(run_stage(Xd, n, d, w, labels, tol, max_iter, use_graph, s, ws.sm_count, ss,
+                      o.traj_J_slow, o.traj_shift_slow, o.profile));
+    rr.iters_slow = ss.iter;
+    rr.converged_slow = ss.converged;
+    rr.shift_slow = ss.shift;
+    rr.J = ss.J;
+    rr.empty_clusters = ss.empty;
+    rr.rechecked_points += ss.rechecked_total;
+    rr.distance_evals = (int64_t)rr.iters_fast * m * k + (int64_t)rr.iters_slow * n * k;
+
+    KM2_CUDA(cudaMemcpyAsync(centers_out, w.c.c64, sizeof(double) * (size_t)k * d,
+                             is_device_ptr(centers_out) ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyDeviceToHost, s));
+    if (!lab_dev)
+        KM2_CUDA(cudaMemcpyAsync(labels_out, labels, sizeof(int) * (size_t)n,
+                                 is_device_ptr(labels_out) ? cudaMemcpyDeviceToDevice
+                                                           : cudaMemcpyDeviceToHost, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    rr.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = rr;
+    if (o.profile) o.profile->kernel_launches += g_launches - launches0;
+    return KMEANS2_OK;
+}
+
+}  // extern "C"

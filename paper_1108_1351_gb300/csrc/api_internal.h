@@ -1,0 +1,78 @@
+// api_internal.h -- host-side plumbing shared by the translation units of libkmeans2.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/kmeans2.h"
+#include "common.cuh"
+
+namespace km2 {
+
+// Kernels launched by the calling thread (every launch site increments it).
+extern thread_local long long g_launches;
+
+// Thread-local text of the last CUDA failure, returned by kmeans2_last_error().
+void set_last_error(const char* where, cudaError_t e);
+void set_last_error_text(const char* text);
+
+#define KM2_CUDA(call)                                                     \
+    do {                                                                   \
+        cudaError_t km2_e_ = (call);                                       \
+        if (km2_e_ != cudaSuccess) {                                       \
+            ::km2::set_last_error(#call, km2_e_);                          \
+            return (km2_e_ == cudaErrorMemoryAllocation) ? KMEANS2_ERR_NOMEM \
+                                                         : KMEANS2_ERR_CUDA; \
+        }                                                                  \
+    } while (0)
+
+#define KM2_TRY(expr)                        \
+    do {                                     \
+        int km2_rc_ = (expr);                \
+        if (km2_rc_ != KMEANS2_OK) return km2_rc_; \
+    } while (0)
+
+// Stream-ordered scratch: every allocation is released (cudaFreeAsync on the
+// same stream) when the object goes out of scope.
+struct DeviceScratch {
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int device = 0;
+    std::vector<void*> ptrs;
+
+    explicit DeviceScratch(cudaStream_t s);
+    ~DeviceScratch();
+    int alloc(void** p, size_t bytes, cudaStream_t s);
+    DeviceScratch(const DeviceScratch&) = delete;
+    DeviceScratch& operator=(const DeviceScratch&) = delete;
+};
+
+// sample.cu
+int sample_device(long long n, int k, long long m, unsigned long long seed, long long* subset,
+                  long long* init_pos, cudaStream_t s, DeviceScratch& ws);
+
+// prep.cu
+int launch_maxabs(const float* X, long long count, StageState* st, cudaStream_t s, int sm_count);
+int launch_gather(const float* X, int d, const long long* subset, long long m, float* Xs,
+                  StageState* st, cudaStream_t s, int sm_count);
+int launch_init_centers(const float* Xs, int d, const long long* pos, int k, double* c64,
+                        cudaStream_t s);
+int launch_center_prep(const Centers& c, StageState* st, cudaStream_t s);
+int launch_stage_init(StageState* st, int d, double tol, int max_iter, cudaStream_t s);
+// clus: 4*k doubles of scratch.
+int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* traj_J,
+                    double* traj_shift, double* clus, unsigned long long cond_handle,
+                    int use_cond, cudaStream_t s);
+int launch_recheck(const float* X, int d, const Centers& c, int* labels, const int* list,
+                   StageState* st, const Accum& acc, cudaStream_t s, int sm_count);
+
+// assign_fp32.cu
+int assign_fp32_supported(int d, int k);
+int launch_assign_fp32(const float* X, long long n, int d, const Centers& c, int* labels,
+                       StageState* st, const Accum& acc, int* list, cudaStream_t s,
+                       int sm_count);
+
+}  // namespace km2

@@ -1,0 +1,474 @@
+// assign_fp32.cu -- fused distance + nearest-center + cluster-sum kernels, FP32 on
+// the CUDA cores (the hot loop of the Algorithm: "Calculate the modified
+// distance", "Find minimum of d", "Assign the cluster number"; the sums feed the
+// mean step of Lloyd's method, Section 4.1).
+//
+// The argmin needs only D_j = ||c_j||^2 - 2 x.c_j (||x||^2 is common to all
+// centers).  Each kernel keeps the best and second-best D per point; when the
+// gap between them is below the rounding-error bound (tie_kappa) the point is
+// appended to a recheck list and decided in FP64 by recheck_kernel; otherwise
+// the FP32 argmin is provably the FP64 argmin.
+//
+// Cluster sums are exact fixed-point integers (common.cuh).  In the first
+// iteration of a stage (kModeFull) every point adds its coordinates; in later
+// iterations (kModeDelta) only a point whose label changed moves its
+// coordinates from the old cluster to the new one.  Integer sums make this
+// incremental update exact, so later Lloyd iterations cost almost nothing
+// beyond the distances.
+//
+// Two forms:
+//  assign_small<D, P>  d <= 16.  Each thread owns P points in registers; the
+//                      k centers (pre-scaled by -2, with ||c||^2) sit in shared
+//                      memory and are read as broadcast 128-bit loads.  Per-CTA
+//                      int64 partial sums in shared memory, flushed to the
+//                      global split accumulators every <= 2^16 points.
+//  assign_large        any d.  128 points x 128 centers register-blocked tiles
+//                      (8 x 8 per thread) over 8-dimension slices staged in
+//                      shared memory; per-thread top-2 merged across the 16
+//                      threads of a half-warp with shuffles.  Sums go to the
+//                      global accumulators directly.
+#include <cfloat>
+#include <cstdint>
+
+#include "api_internal.h"
+
+namespace km2 {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSmallSmemCap = 200 * 1024;   // dynamic shared memory of assign_small, at most
+
+__device__ __forceinline__ void top2_push(float v, int j, float& b1, float& b2, int& bi)
+{
+    if (v < b1) {
+        b2 = b1;
+        b1 = v;
+        bi = j;
+    } else {
+        b2 = fminf(b2, v);
+    }
+}
+
+// Merge another (best, second, index) triple; symmetric, lowest index on equal bests.
+__device__ __forceinline__ void top2_merge(float& b1, float& b2, int& bi, float o1, float o2,
+                                           int oi)
+{
+    if (o1 < b1 || (o1 == b1 && oi < bi)) {
+        b2 = fminf(b1, o2);
+        b1 = o1;
+        bi = oi;
+    } else {
+        b2 = fminf(b2, o1);
+    }
+}
+
+template <int D>
+struct SmallCfg {
+    static constexpr int DS = (D + 1 + 3) & ~3;   // floats per center in shared memory
+    static constexpr int P = D <= 8 ? 4 : 2;      // points per thread
+};
+
+template <int D>
+__device__ __forceinline__ void load_point(const float* __restrict__ X, long long i, float* x)
+{
+    const float* src = X + i * D;
+    if constexpr (D % 4 == 0) {
+#pragma unroll
+        for (int t = 0; t < D; t += 4) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(src + t));
+            x[t] = v.x; x[t + 1] = v.y; x[t + 2] = v.z; x[t + 3] = v.w;
+        }
+    } else if constexpr (D % 2 == 0) {
+#pragma unroll
+        for (int t = 0; t < D; t += 2) {
+            float2 v = __ldg(reinterpret_cast<const float2*>(src + t));
+            x[t] = v.x; x[t + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < D; ++t) x[t] = __ldg(src + t);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads)
+assign_small(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
+             StageState* st, Accum acc, int* __restrict__ list, float kappa)
+{
+    constexpr int DS = SmallCfg<D>::DS;
+    constexpr int P = SmallCfg<D>::P;
+    extern __shared__ __align__(16) float smem[];
+    const int k = c.k;
+    float* sc = smem;                                                   // k * DS
+    long long* sacc = reinterpret_cast<long long*>(smem + (size_t)k * DS);  // k * D
+    int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);               // k
+    __shared__ unsigned long long sq;
+    __shared__ int s_pts;
+
+    if (st->error) return;
+    const int mode = st->mode;
+    const float scaleF = st->scaleF;
+    const float scaleG = st->scaleG;
+    const float c2x2 = 2.0f * st->cmax2;
+    const int tid = threadIdx.x;
+
+    for (int e = tid; e < k * DS; e += kThreads) {
+        int j = e / DS, t = e - j * DS;
+        float v = 0.0f;
+        if (t < D) v = -2.0f * c.c32[(long long)j * D + t];
+        else if (t == D) v = c.cnorm[j];
+        sc[e] = v;
+    }
+    for (int e = tid; e < k * D; e += kThreads) sacc[e] = 0;
+    for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
+    if (tid == 0) { sq = 0; s_pts = 0; }
+    __syncthreads();
+
+    long long qloc = 0;
+    const long long tile_pts = (long long)kThreads * P;
+    const long long ntiles = (n + tile_pts - 1) / tile_pts;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long base = tile * tile_pts;
+        float x[P][D];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            long long i = base + (long long)p * kThreads + tid;
+            if (i < n) {
+                load_point<D>(X, i, x[p]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < D; ++t) x[p][t] = 0.0f;
+            }
+        }
+        float b1[P], b2[P];
+        int bi[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) { b1[p] = FLT_MAX; b2[p] = FLT_MAX; bi[p] = 0; }
+#pragma unroll 2
+        for (int j = 0; j < k; ++j) {
+            float cv[DS];
+            const float4* cj = reinterpret_cast<const float4*>(sc + j * DS);
+#pragma unroll
+            for (int q = 0; q < DS / 4; ++q) {
+                float4 v = cj[q];
+                cv[4 * q] = v.x; cv[4 * q + 1] = v.y; cv[4 * q + 2] = v.z; cv[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float dd = cv[D];
+#pragma unroll
+                for (int t = 0; t < D; ++t) dd = fmaf(x[p][t], cv[t], dd);
+                top2_push(dd, j, b1[p], b2[p], bi[p]);
+            }
+        }
+        int touched = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const long long i = base + (long long)p * kThreads + tid;
+            const bool valid = i < n;
+            float xn2 = 0.0f;
+#pragma unroll
+            for (int t = 0; t < D; ++t) xn2 = fmaf(x[p][t], x[p][t], xn2);
+            const bool flag = valid && (b2[p] - b1[p] <= kappa * (c2x2 + xn2));
+            if (mode == kModeFull && valid) {
+#pragma unroll
+                for (int t = 0; t < D; ++t) qloc += sq_fixed(x[p][t], scaleG);
+                ++touched;
+            }
+            recheck_append(flag, (int)i, list, &st->recheck_count);
+            if (valid && !flag) {
+                const int lab = bi[p];
+                const int old = (mode == kModeDelta) ? labels[i] : -1;
+                if (lab != old) {
+#pragma unroll
+                    for (int t = 0; t < D; ++t) {
+                        long long v = to_fixed(x[p][t], scaleF);
+                        atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * D + t),
+                                  (unsigned long long)v);
+                        if (old >= 0)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + t),
+                                      (unsigned long long)(-v));
+                    }
+                    atomicAdd(scnt + lab, 1);
+                    if (old >= 0) atomicAdd(scnt + old, -1);
+                    labels[i] = lab;
+                    if (mode == kModeDelta) ++touched;
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) touched += __shfl_xor_sync(0xffffffffu, touched, o);
+        if ((tid & 31) == 0 && touched) atomicAdd(&s_pts, touched);
+        __syncthreads();
+        const bool last = tile + gridDim.x >= ntiles;
+        const bool do_flush = s_pts > kFlushPoints - tile_pts || last;
+        __syncthreads();   // every thread has read s_pts before it changes again
+        if (do_flush) {
+            if (qloc) atomicAdd(&sq, (unsigned long long)qloc);
+            qloc = 0;
+            __syncthreads();
+            for (int e = tid; e < k * D; e += kThreads) {
+                long long v = sacc[e];
+                if (v) {
+                    split_add(acc.s_lo + e, acc.s_hi + e, v);
+                    sacc[e] = 0;
+                }
+            }
+            for (int e = tid; e < k; e += kThreads) {
+                int v = scnt[e];
+                if (v) {
+                    atomicAdd(acc.cnt + e, (unsigned long long)(long long)v);
+                    scnt[e] = 0;
+                }
+            }
+            if (tid == 0) {
+                if (sq) split_add(&st->q_lo, &st->q_hi, (long long)sq);
+                sq = 0;
+                s_pts = 0;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- large d
+
+constexpr int BM = 128, BN = 128, BK = 8;
+
+__global__ void __launch_bounds__(kThreads)
+assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __restrict__ labels,
+             StageState* st, Accum acc, int* __restrict__ list, float kappa, int vec4)
+{
+    __shared__ __align__(16) float Xs[2][BK][BM];
+    __shared__ __align__(16) float Cs[2][BK][BN];
+    if (st->error) return;
+    const int mode = st->mode;
+    const float scaleF = st->scaleF;
+    const float scaleG = st->scaleG;
+    const float c2x2 = 2.0f * st->cmax2;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int lane = tid & 31;
+    const int kpad = c.kpad;
+    const int nct = kpad / BN;
+    const int nks = c.dpad / BK;
+    const long long ntiles = (n + BM - 1) / BM;
+    // loader roles
+    const int xl_pt = tid >> 1, xl_d = (tid & 1) * 4;     // X: point, first of 4 dims
+    const int cl_row = tid >> 5, cl_col = (tid & 31) * 4;  // C: dim row, first of 4 centers
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long base = tile * BM;
+        float b1[8], b2[8], xn2[8];
+        int bi[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) { b1[r] = FLT_MAX; b2[r] = FLT_MAX; bi[r] = 0; xn2[r] = 0.f; }
+
+        for (int ct = 0; ct < nct; ++ct) {
+            float accm[8][8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) accm[r][q] = 0.0f;
+
+            auto load_x = [&](int ks, float* xv) {
+                const long long i = base + xl_pt;
+                const int t0 = ks * BK + xl_d;
+                if (i < n) {
+                    const float* src = X + i * d + t0;
+                    if (vec4 && t0 + 3 < d) {
+                        float4 v = __ldg(reinterpret_cast<const float4*>(src));
+                        xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) xv[q] = (t0 + q < d) ? __ldg(src + q) : 0.0f;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) xv[q] = 0.0f;
+                }
+            };
+            auto load_c = [&](int ks) -> float4 {
+                return __ldg(reinterpret_cast<const float4*>(
+                    c.c32t + (long long)(ks * BK + cl_row) * kpad + ct * BN + cl_col));
+            };
+            float xv[4];
+            load_x(0, xv);
+            float4 cv4 = load_c(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Xs[0][xl_d + q][xl_pt] = xv[q];
+            *reinterpret_cast<float4*>(&Cs[0][cl_row][cl_col]) = cv4;
+            __syncthreads();
+            for (int ks = 0; ks < nks; ++ks) {
+                const int buf = ks & 1;
+                if (ks + 1 < nks) {
+                    load_x(ks + 1, xv);
+                    cv4 = load_c(ks + 1);
+                }
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    float a[8], b[8];
+                    float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 4]);
+                    float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][kk][64 + ty * 4]);
+                    float4 b0 = *reinterpret_cast<const float4*>(&Cs[buf][kk][tx * 4]);
+                    float4 b1v = *reinterpret_cast<const float4*>(&Cs[buf][kk][64 + tx * 4]);
+                    a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+                    a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+                    b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+                    b[4] = b1v.x; b[5] = b1v.y; b[6] = b1v.z; b[7] = b1v.w;
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) accm[r][q] = fmaf(a[r], b[q], accm[r][q]);
+                    if (ct == 0) {
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) xn2[r] = fmaf(a[r], a[r], xn2[r]);
+                    }
+                }
+                if (ks + 1 < nks) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) Xs[buf ^ 1][xl_d + q][xl_pt] = xv[q];
+                    *reinterpret_cast<float4*>(&Cs[buf ^ 1][cl_row][cl_col]) = cv4;
+                }
+                __syncthreads();
+            }
+            // epilogue of this center tile: D = ||c||^2 - 2 x.c, running top-2
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int col = ct * BN + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4));
+                const float cn = __ldg(c.cnorm + col);
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    top2_push(fmaf(-2.0f, accm[r][q], cn), col, b1[r], b2[r], bi[r]);
+            }
+        }
+        // merge the 16 column groups of each row (half-warp butterfly)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                float o1 = __shfl_xor_sync(0xffffffffu, b1[r], o);
+                float o2 = __shfl_xor_sync(0xffffffffu, b2[r], o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi[r], o);
+                top2_merge(b1[r], b2[r], bi[r], o1, o2, oi);
+            }
+        }
+        long long qloc = 0;
+        int olds[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const long long i = base + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+            olds[r] = (mode == kModeDelta && i < n) ? labels[i] : -1;
+        }
+        __syncwarp();   // all lanes hold the old labels before lane tx == 0 rewrites them
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const long long i = base + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+            const bool valid = i < n;
+            const bool flag = valid && (b2[r] - b1[r] <= kappa * (c2x2 + xn2[r]));
+            recheck_append(flag && tx == 0, (int)i, list, &st->recheck_count);
+            if (!valid) continue;
+            const float* xr = X + i * d;
+            if (mode == kModeFull)
+                for (int t = tx; t < d; t += 16) qloc += sq_fixed(__ldg(xr + t), scaleG);
+            if (flag) continue;
+            const int lab = bi[r];
+            const int old = olds[r];
+            if (lab == old) continue;
+            for (int t = tx; t < d; t += 16) {
+                long long v = to_fixed(__ldg(xr + t), scaleF);
+                split_add(acc.s_lo + (long long)lab * d + t, acc.s_hi + (long long)lab * d + t, v);
+                if (old >= 0)
+                    split_add(acc.s_lo + (long long)old * d + t, acc.s_hi + (long long)old * d + t,
+                              -v);
+            }
+            if (tx == 0) {
+                atomicAdd(acc.cnt + lab, 1ull);
+                if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                labels[i] = lab;
+            }
+        }
+        if (mode == kModeFull) {
+            for (int o = 16; o; o >>= 1) qloc += __shfl_xor_sync(0xffffffffu, qloc, o);
+            if (lane == 0 && qloc) split_add(&st->q_lo, &st->q_hi, qloc);
+        }
+    }
+}
+
+template <int D>
+size_t small_smem(int k)
+{
+    return (size_t)k * SmallCfg<D>::DS * sizeof(float) + (size_t)k * D * sizeof(long long) +
+           (size_t)k * sizeof(int);
+}
+
+template <int D>
+int launch_small(const float* X, long long n, const Centers& c, int* labels, StageState* st,
+                 const Accum& acc, int* list, cudaStream_t s, int sm_count)
+{
+    size_t sm = small_smem<D>(c.k);
+    static thread_local int configured_for = -1;
+    int dev = 0;
+    KM2_CUDA(cudaGetDevice(&dev));
+    if (sm > 48 * 1024 && configured_for != dev) {
+        KM2_CUDA(cudaFuncSetAttribute(assign_small<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSmallSmemCap));
+        configured_for = dev;
+    }
+    int per_sm = 0;
+    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assign_small<D>, kThreads, sm));
+    if (per_sm < 1) return KMEANS2_ERR_UNSUPPORTED;
+    long long tiles = (n + (long long)kThreads * SmallCfg<D>::P - 1) / ((long long)kThreads * SmallCfg<D>::P);
+    long long grid = (long long)sm_count * per_sm;
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) grid = 1;
+    ++g_launches;
+    assign_small<D><<<(int)grid, kThreads, sm, s>>>(X, n, c, labels, st, acc, list, tie_kappa(D));
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+}  // namespace
+
+static size_t small_smem_any(int d, int k)
+{
+    size_t ds = (size_t)((d + 1 + 3) & ~3);
+    return (size_t)k * ds * 4 + (size_t)k * d * 8 + (size_t)k * 4;
+}
+
+int assign_fp32_supported(int d, int k)
+{
+    (void)d;
+    (void)k;
+    return 1;
+}
+
+int launch_assign_fp32(const float* X, long long n, int d, const Centers& c, int* labels,
+                       StageState* st, const Accum& acc, int* list, cudaStream_t s, int sm_count)
+{
+    if (d <= 16 && small_smem_any(d, c.k) <= (size_t)kSmallSmemCap) {
+        switch (d) {
+#define KM2_CASE(DD) \
+    case DD: return launch_small<DD>(X, n, c, labels, st, acc, list, s, sm_count);
+            KM2_CASE(1) KM2_CASE(2) KM2_CASE(3) KM2_CASE(4) KM2_CASE(5) KM2_CASE(6) KM2_CASE(7)
+            KM2_CASE(8) KM2_CASE(9) KM2_CASE(10) KM2_CASE(11) KM2_CASE(12) KM2_CASE(13)
+            KM2_CASE(14) KM2_CASE(15) KM2_CASE(16)
+#undef KM2_CASE
+            default: break;
+        }
+    }
+    int per_sm = 0;
+    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assign_large, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    long long tiles = (n + BM - 1) / BM;
+    long long grid = (long long)sm_count * per_sm;
+    if (grid > tiles) grid = tiles;
+    int vec4 = (d % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
+    ++g_launches;
+    assign_large<<<(int)grid, kThreads, 0, s>>>(X, n, d, c, labels, st, acc, list, tie_kappa(d),
+                                                vec4);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+}  // namespace km2

@@ -1,0 +1,132 @@
+// common.cuh -- definitions shared by the kernels of libkmeans2 (not by the oracle).
+//
+// Exact cluster sums.  Each FP32 coordinate x enters the sums as the integer
+// round(x * 2^F).  The per-stage exponent F = 46 - E, with max|x| < 2^E, keeps
+// one value below 2^46 in magnitude, so an int64 partial over at most
+// kFlushPoints = 2^16 points cannot overflow.  Global sums are kept as two
+// 64-bit words: `lo` accumulates the low 32 bits of every contribution
+// (unsigned) and `hi` the arithmetic high part, so that the exact sum is
+// (int128)hi * 2^32 + lo for any number of contributions below 2^31.  Integer
+// addition is associative, so the sums, the centers and J do not depend on the
+// order in which threads add: every mode is deterministic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace km2 {
+
+constexpr int kFlushPoints = 1 << 16;   // max points folded into one int64 partial
+constexpr int kModeFull = 0;            // first iteration of a stage: sums from scratch
+constexpr int kModeDelta = 1;           // later iterations: only points whose label changed
+
+// Per-stage device state, one instance per stage run, read by every kernel of
+// the loop.  Written only by the single-thread / single-CTA kernels
+// (stage_init, finalize) except for the atomically updated counters.
+struct StageState {
+    // fixed-point scales (stage_init)
+    int F, G;                     // exponents of the x and ||x||^2 fixed points
+    float scaleF, scaleG;         // 2^F, 2^G
+    double inv_scaleF, inv_scaleG;
+    unsigned int maxabs_bits;     // max |x| as float bits (atomicMax; NaN/inf sort above)
+    int error;                    // nonzero: stage aborted (see kErr*)
+    // loop control
+    int mode;                     // kModeFull / kModeDelta
+    int iter;                     // iterations completed
+    int done;                     // converged or iter == max_iter
+    int converged;
+    int max_iter;
+    int empty;                    // empty clusters after the last update
+    double tol;
+    // per iteration
+    float cmax2;                  // >= max_j ||c_j||^2, rounded up to FP32
+    int recheck_count;            // entries in the recheck list this iteration
+    long long rechecked_total;
+    double J;                     // objective of the last assignment
+    double shift;                 // last max center movement
+    double Qtot;                  // sum_i ||x_i||^2 of the stage's points
+    unsigned long long q_lo, q_hi;  // exact fixed-point sum of ||x||^2 (scale 2^G)
+};
+
+constexpr int kErrNonFinite = 1;
+
+// Accumulator arrays of one stage (device, zeroed by the host before a full pass).
+struct Accum {
+    unsigned long long* s_lo;     // k*d
+    unsigned long long* s_hi;     // k*d
+    unsigned long long* cnt;      // k (two's complement int64)
+};
+
+// Center copies derived from the FP64 master by center_prep / finalize.
+struct Centers {
+    double* c64;                  // k*d   FP64 master (row-major)
+    float* c32;                   // k*d   FP32 copy (row-major)
+    float* c32t;                  // dpad*kpad FP32 copy, transposed (dims x centers)
+    float* cnorm;                 // kpad  FP32 of ||c_j||^2; +inf for padding
+    int k, d, kpad, dpad;
+};
+
+__device__ __forceinline__ long long to_fixed(float x, float scale)
+{
+    return __float2ll_rn(x * scale);
+}
+
+// Add an int64 contribution to a split (lo, hi) global accumulator.
+__device__ __forceinline__ void split_add(unsigned long long* lo, unsigned long long* hi,
+                                          long long v)
+{
+    unsigned long long l = (unsigned long long)v & 0xffffffffull;
+    long long h = v >> 32;
+    if (l) atomicAdd(lo, l);
+    if (h) atomicAdd(hi, (unsigned long long)h);
+}
+
+// Exact value of a split accumulator, times 2^-F, as FP64.
+__device__ __forceinline__ double split_value(unsigned long long lo, unsigned long long hi,
+                                              double inv_scale)
+{
+    __int128 v = (__int128)(long long)hi * (__int128)4294967296LL + (__int128)lo;
+    return (double)v * inv_scale;
+}
+
+// ||x||^2 contribution of one coordinate as exact fixed point: x*x = p + e
+// exactly (p = fl(x*x), e = fma(x, x, -p)), each part rounded to the 2^-G grid.
+__device__ __forceinline__ long long sq_fixed(float x, float scaleG)
+{
+    float p = x * x;
+    float e = fmaf(x, x, -p);
+    return __float2ll_rn(p * scaleG) + __float2ll_rn(e * scaleG);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Append point i to the recheck list (warp-aggregated; all lanes must call).
+__device__ __forceinline__ void recheck_append(bool flag, int i, int* list, int* count)
+{
+    unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) list[base + __popc(mask & lanemask_lt())] = i;
+}
+
+// Near-tie threshold on the FP32 gap between the best and second-best
+// expanded distances ||c||^2 - 2 x.c (derivation in the design notes):
+// |D_fp32 - D_exact| <= (d+1) u (||c||^2 + 2 ||x|| ||c||) <= (d+1) u (2 C2 + X2)
+// per distance, u = 2^-24, C2 = max_j ||c_j||^2, X2 = ||x||^2.  Two distances,
+// the FP32 rounding of the gap and of X2, and the oracle's own FP64 rounding
+// are covered by kappa = 2 (d + 3) 2^-24 * 1.0625.
+__host__ __device__ inline float tie_kappa(int d)
+{
+    return 2.0f * (float)(d + 3) * 5.9604644775390625e-8f * 1.0625f;
+}
+
+}  // namespace km2

@@ -1,0 +1,391 @@
+// prep.cu -- the small kernels around the distance kernels:
+//   maxabs      max |x| over a stage's data (fixed-point scale, finiteness check)
+//   gather      X_s = rows of X at the subset indices (Algorithm, "per% of S_n")
+//   init        initial centers = chosen points of X_s (Algorithm, "Select X_c")
+//   center_prep FP32 / transposed copies of the FP64 centers and ||c||^2
+//   stage_init  fixed-point scales and loop state of one stage
+//   finalize    new centers = cluster means (Lloyd's method, Section 4.1), the
+//               largest movement (stop test, Sections 5-6), J (Eq. 3)
+//   recheck     FP64 re-evaluation of near-tie points (ties -> lowest index)
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include "api_internal.h"
+
+namespace km2 {
+
+namespace {
+
+constexpr int kErrRange = 2;   // max|x| >= 2^50: FP32 squares could overflow
+
+__device__ __forceinline__ unsigned int abs_bits(float v)
+{
+    return __float_as_uint(v) & 0x7fffffffu;   // NaN keeps a payload above +inf
+}
+
+__device__ __forceinline__ unsigned int warp_max_u32(unsigned int v)
+{
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void maxabs_kernel(const float* __restrict__ X, long long count, int vec4,
+                              StageState* st)
+{
+    unsigned int m = 0;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long done = 0;
+    if (vec4) {
+        const float4* X4 = reinterpret_cast<const float4*>(X);
+        long long n4 = count >> 2;
+        for (long long i = tid; i < n4; i += stride) {
+            float4 v = __ldg(X4 + i);
+            m = max(m, max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w))));
+        }
+        done = n4 << 2;
+    }
+    for (long long i = done + tid; i < count; i += stride) m = max(m, abs_bits(__ldg(X + i)));
+    m = warp_max_u32(m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&st->maxabs_bits, m);
+}
+
+__global__ void gather_kernel(const float* __restrict__ X, int d,
+                              const long long* __restrict__ subset, long long m,
+                              float* __restrict__ Xs, StageState* st)
+{
+    unsigned int mx = 0;
+    long long total = m * (long long)d;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        long long p = e / d;
+        int t = (int)(e - p * d);
+        float v = X[subset[p] * (long long)d + t];
+        Xs[e] = v;
+        mx = max(mx, abs_bits(v));
+    }
+    mx = warp_max_u32(mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxabs_bits, mx);
+}
+
+__global__ void init_centers_kernel(const float* __restrict__ Xs, int d,
+                                    const long long* __restrict__ pos, int k,
+                                    double* __restrict__ c64)
+{
+    long long total = (long long)k * d;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long j = e / d;
+        int t = (int)(e - j * d);
+        c64[e] = (double)Xs[pos[j] * (long long)d + t];
+    }
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP32 copies and ||c_j||^2 of every center; st->cmax2 = max_j ||c_j||^2 rounded up.
+// One CTA; warps stride over centers; fixed reduction order.
+__global__ void center_prep_kernel(Centers c, StageState* st)
+{
+    __shared__ double red[1024];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double mx = 0.0;
+    for (int j = warp; j < c.k; j += nw) {
+        double nn = 0.0;
+        for (int t = lane; t < c.d; t += 32) {
+            double v = c.c64[(long long)j * c.d + t];
+            nn = fma(v, v, nn);
+            c.c32[(long long)j * c.d + t] = (float)v;
+            c.c32t[(long long)t * c.kpad + j] = (float)v;
+        }
+        nn = warp_sum_f64(nn);
+        if (lane == 0) c.cnorm[j] = (float)nn;
+        mx = fmax(mx, nn);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st->cmax2 = __double2float_ru(red[0]);
+}
+
+__global__ void stage_init_kernel(StageState* st, int d, double tol, int max_iter)
+{
+    unsigned int b = st->maxabs_bits;
+    st->mode = kModeFull;
+    st->iter = 0;
+    st->done = 0;
+    st->converged = 0;
+    st->max_iter = max_iter;
+    st->tol = tol;
+    st->recheck_count = 0;
+    st->rechecked_total = 0;
+    st->q_lo = 0;
+    st->q_hi = 0;
+    st->J = 0.0;
+    st->shift = 0.0;
+    st->Qtot = 0.0;
+    st->empty = 0;
+    st->error = 0;
+    if (b >= 0x7f800000u) {
+        st->error = kErrNonFinite;
+        st->done = 1;
+        return;
+    }
+    float mx = __uint_as_float(b);
+    int E = -126;
+    if (mx > 0.0f) frexpf(mx, &E);          // mx < 2^E
+    if (E > 50) {
+        st->error = kErrRange;
+        st->done = 1;
+        return;
+    }
+    int lg = 0;
+    while ((1 << lg) < d) ++lg;
+    int F = min(120, max(-100, 46 - E));
+    int G = min(120, max(-100, 62 - 2 * E - 16 - lg));
+    st->F = F;
+    st->G = G;
+    st->scaleF = ldexpf(1.0f, F);
+    st->scaleG = ldexpf(1.0f, G);
+    st->inv_scaleF = ldexp(1.0, -F);
+    st->inv_scaleG = ldexp(1.0, -G);
+}
+
+// One CTA.  New centers, movement, J; loop control for the next iteration.
+__global__ void __launch_bounds__(1024) finalize_kernel(Accum acc, Centers c, StageState* st,
+                                                        double* traj_J, double* traj_shift,
+                                                        double* clus, unsigned long long handle,
+                                                        int use_cond)
+{
+    __shared__ double r_shift[1024];
+    __shared__ double r_J[1024];
+    __shared__ double r_nn[1024];
+    __shared__ int r_empty[1024];
+    __shared__ double s_Qtot;
+    const int k = c.k, d = c.d;
+    if (st->error) {
+        if (threadIdx.x == 0) {
+            st->done = 1;
+            if (use_cond) cudaGraphSetConditional(handle, 0u);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        double Q = st->Qtot;
+        if (st->mode == kModeFull) {
+            Q = split_value(st->q_lo, st->q_hi, st->inv_scaleG);
+            st->Qtot = Q;
+        }
+        s_Qtot = Q;
+    }
+    const double inv = st->inv_scaleF;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < k; j += nw) {
+        long long N = (long long)acc.cnt[j];
+        double diff2 = 0.0, cS = 0.0, cc = 0.0, nn = 0.0;
+        for (int t = lane; t < d; t += 32) {
+            long long e = (long long)j * d + t;
+            double S = split_value(acc.s_lo[e], acc.s_hi[e], inv);
+            double cv = c.c64[e];
+            double cn = N > 0 ? S / (double)N : cv;
+            double df = cn - cv;
+            diff2 = fma(df, df, diff2);
+            cS = fma(cv, S, cS);
+            cc = fma(cv, cv, cc);
+            nn = fma(cn, cn, nn);
+            c.c64[e] = cn;
+            c.c32[e] = (float)cn;
+            c.c32t[(long long)t * c.kpad + j] = (float)cn;
+        }
+        diff2 = warp_sum_f64(diff2);
+        cS = warp_sum_f64(cS);
+        cc = warp_sum_f64(cc);
+        nn = warp_sum_f64(nn);
+        if (lane == 0) {
+            clus[j] = diff2;
+            clus[k + j] = 2.0 * cS - (double)N * cc;
+            clus[2 * k + j] = nn;
+            clus[3 * k + j] = (N == 0) ? 1.0 : 0.0;
+            c.cnorm[j] = (float)nn;
+        }
+    }
+    __syncthreads();
+    double sh = 0.0, jj = 0.0, mx = 0.0;
+    int em = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        sh = fmax(sh, clus[j]);
+        jj += clus[k + j];
+        mx = fmax(mx, clus[2 * k + j]);
+        em += (int)clus[3 * k + j];
+    }
+    r_shift[threadIdx.x] = sh;
+    r_J[threadIdx.x] = jj;
+    r_nn[threadIdx.x] = mx;
+    r_empty[threadIdx.x] = em;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            r_shift[threadIdx.x] = fmax(r_shift[threadIdx.x], r_shift[threadIdx.x + s]);
+            r_J[threadIdx.x] += r_J[threadIdx.x + s];
+            r_nn[threadIdx.x] = fmax(r_nn[threadIdx.x], r_nn[threadIdx.x + s]);
+            r_empty[threadIdx.x] += r_empty[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double J = s_Qtot - r_J[0];
+        double shift = sqrt(r_shift[0]);
+        int it = st->iter;
+        if (traj_J) traj_J[it] = J;
+        if (traj_shift) traj_shift[it] = shift;
+        st->J = J;
+        st->shift = shift;
+        st->empty = r_empty[0];
+        st->cmax2 = __double2float_ru(r_nn[0]);
+        st->iter = it + 1;
+        int conv = shift <= st->tol;
+        st->converged = conv;
+        st->done = conv || (it + 1 >= st->max_iter);
+        st->mode = kModeDelta;
+        st->rechecked_total += st->recheck_count;
+        st->recheck_count = 0;
+        if (use_cond) cudaGraphSetConditional(handle, st->done ? 0u : 1u);
+    }
+}
+
+// One warp per listed point: exact FP64 distances in the oracle's form
+// (sum_t fma(x_t - c_t, x_t - c_t, acc), t ascending), lowest index on ties.
+__global__ void recheck_kernel(const float* __restrict__ X, int d, Centers c,
+                               int* __restrict__ labels, const int* __restrict__ list,
+                               StageState* st, Accum acc)
+{
+    if (st->error) return;
+    const int count = st->recheck_count;
+    const int mode = st->mode;
+    const float scaleF = st->scaleF;
+    const int k = c.k;
+    int lane = threadIdx.x & 31;
+    long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = gw; w < count; w += nw) {
+        int i = list[w];
+        const float* x = X + (long long)i * d;
+        double best = DBL_MAX;
+        int bj = INT_MAX;
+        for (int j = lane; j < k; j += 32) {
+            const double* cj = c.c64 + (long long)j * d;
+            double a2 = 0.0;
+            for (int t = 0; t < d; ++t) {
+                double a = (double)__ldg(x + t) - cj[t];
+                a2 = fma(a, a, a2);
+            }
+            if (a2 < best) { best = a2; bj = j; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        }
+        int old = (mode == kModeDelta) ? labels[i] : -1;
+        __syncwarp();   // every lane has read the old label before lane 0 rewrites it
+        if (bj != old) {
+            for (int t = lane; t < d; t += 32) {
+                long long v = to_fixed(__ldg(x + t), scaleF);
+                split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, v);
+                if (old >= 0)
+                    split_add(acc.s_lo + (long long)old * d + t, acc.s_hi + (long long)old * d + t, -v);
+            }
+            if (lane == 0) {
+                atomicAdd(acc.cnt + bj, 1ull);
+                if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                labels[i] = bj;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+static int grid_for(long long work, int threads, int sm_count, int per_sm)
+{
+    long long g = (work + threads - 1) / threads;
+    long long cap = (long long)sm_count * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+int launch_maxabs(const float* X, long long count, StageState* st, cudaStream_t s, int sm_count)
+{
+    int vec4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
+    ++g_launches;
+    maxabs_kernel<<<grid_for(count / 4 + 1, 256, sm_count, 8), 256, 0, s>>>(X, count, vec4, st);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_gather(const float* X, int d, const long long* subset, long long m, float* Xs,
+                  StageState* st, cudaStream_t s, int sm_count)
+{
+    ++g_launches;
+    gather_kernel<<<grid_for(m * d, 256, sm_count, 8), 256, 0, s>>>(X, d, subset, m, Xs, st);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_init_centers(const float* Xs, int d, const long long* pos, int k, double* c64,
+                        cudaStream_t s)
+{
+    long long total = (long long)k * d;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    ++g_launches;
+    init_centers_kernel<<<grid, 256, 0, s>>>(Xs, d, pos, k, c64);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_center_prep(const Centers& c, StageState* st, cudaStream_t s)
+{
+    ++g_launches;
+    center_prep_kernel<<<1, 1024, 0, s>>>(c, st);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_stage_init(StageState* st, int d, double tol, int max_iter, cudaStream_t s)
+{
+    ++g_launches;
+    stage_init_kernel<<<1, 1, 0, s>>>(st, d, tol, max_iter);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* traj_J,
+                    double* traj_shift, double* clus, unsigned long long cond_handle,
+                    int use_cond, cudaStream_t s)
+{
+    ++g_launches;
+    finalize_kernel<<<1, 1024, 0, s>>>(acc, c, st, traj_J, traj_shift, clus, cond_handle, use_cond);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_recheck(const float* X, int d, const Centers& c, int* labels, const int* list,
+                   StageState* st, const Accum& acc, cudaStream_t s, int sm_count)
+{
+    ++g_launches;
+    recheck_kernel<<<sm_count * 4, 256, 0, s>>>(X, d, c, labels, list, st, acc);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+}  // namespace km2

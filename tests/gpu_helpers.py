@@ -1,0 +1,42 @@
+"""Shared checks for the GPU parity tests (tolerances derived in the design notes).
+
+* Labels: bit-exact (the library decides near ties in the oracle's own FP64 form).
+* Centers: |c_gpu - c_oracle| <= 1e-10 * max_t |c_oracle[j, t]| + 2^(E - 46) per
+  coordinate, where 2^E > max|x|: the second term is the documented
+  fixed-point grid of the exact cluster sums.
+* J: |J_gpu - J_oracle| <= 1e-9 * J_oracle + 1e-13 * sum_i ||x_i||^2; the
+  library forms J as sum ||x||^2 - sum_j (2 c_j.S_j - N_j ||c_j||^2), whose FP64
+  rounding is relative to sum ||x||^2.
+"""
+import math
+
+import numpy as np
+
+
+def grid_term(X) -> float:
+    mx = float(np.max(np.abs(X))) if X.size else 0.0
+    if mx == 0.0:
+        return 0.0
+    E = math.frexp(mx)[1]
+    return 2.0 ** (E - 46)
+
+
+def assert_centers_close(got, want, X, rel=1e-10):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape
+    scale = np.max(np.abs(want), axis=1, keepdims=True)
+    tol = rel * scale + grid_term(X)
+    bad = np.abs(got - want) > tol
+    assert not bad.any(), f"{bad.sum()} center coordinates off; worst {np.max(np.abs(got - want) - tol)}"
+
+
+def assert_J_close(got, want, X, rel=1e-9):
+    q = float(np.sum(np.asarray(X, dtype=np.float64) ** 2))
+    assert abs(got - want) <= rel * abs(want) + 1e-13 * q, (got, want)
+
+
+def to_np(a):
+    if hasattr(a, "detach"):
+        return a.detach().cpu().numpy()
+    return np.asarray(a)

@@ -1,0 +1,205 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1108_1351_gb300 as km
+from paper_1108_1351_gb300 import synth
+from tests.gpu_helpers import assert_centers_close, assert_J_close, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1351_gb300 import build
+    build.build()
+    oracle.build()
+    km.load()
+
+
+DEV = "cuda:0"
+NT = max(1, oracle.max_threads())
+
+
+def _mixture(n, d, k, seed, spread=8.0):
+    rng = np.random.default_rng(seed)
+    means = rng.normal(size=(k, d)) * spread
+    X = means[rng.integers(0, k, n)] + rng.normal(size=(n, d))
+    return X.astype(np.float32)
+
+
+def _centers_from(X, k, seed, jitter=0.0):
+    rng = np.random.default_rng(seed + 99)
+    idx = rng.choice(len(X), size=k, replace=False)
+    C = X[idx].astype(np.float64)
+    if jitter:
+        C = C + jitter * rng.normal(size=C.shape)
+    return C
+
+
+def _step_both(X, C):
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, shift, empty = km.step(Xd, torch.as_tensor(C, device=DEV))
+    ocn, olab, oJ, oshift, oempty = oracle.lloyd_step(X, C, nthreads=NT)
+    return (to_np(cn), to_np(lab), J, shift, empty), (ocn, olab, oJ, oshift, oempty)
+
+
+STEP_SHAPES = [
+    # (n, d, k): small-d kernel (d <= 16) and large-d kernel; several tiles + ragged tails
+    (5000, 1, 3), (20000, 2, 4), (10001, 3, 7), (9999, 5, 16), (70001, 8, 32), (12345, 13, 50),
+    (30000, 16, 256), (5000, 17, 5), (20000, 32, 64), (10000, 64, 200), (4099, 128, 1024),
+    (3000, 300, 10),
+]
+
+
+@pytest.mark.parametrize("n,d,k", STEP_SHAPES)
+def test_step_matches_oracle(n, d, k):
+    X = _mixture(n, d, k, seed=n + d + k)
+    C = _centers_from(X, k, seed=d, jitter=0.3)
+    (cn, lab, J, sh, em), (ocn, olab, oJ, osh, oem) = _step_both(X, C)
+    assert np.array_equal(lab, olab)
+    assert_centers_close(cn, ocn, X)
+    assert_J_close(J, oJ, X)
+    assert abs(sh - osh) <= 1e-10 * max(osh, 1.0)
+    assert em == oem
+
+
+def test_step_exact_ties_duplicates_and_empty_cluster():
+    rng = np.random.default_rng(5)
+    base = rng.normal(size=(50, 4)).astype(np.float32)
+    X = np.repeat(base, 40, axis=0)                      # every point 40 times
+    C = np.concatenate([base[:6], base[:6], [[1e4] * 4]]).astype(np.float64)   # duplicated centers
+    (cn, lab, J, sh, em), (ocn, olab, oJ, osh, oem) = _step_both(X, C)
+    assert np.array_equal(lab, olab)
+    assert lab.max() < 6                                  # ties go to the lowest index
+    assert em == oem and em >= 7
+    assert_centers_close(cn, ocn, X)
+    assert_J_close(J, oJ, X)
+
+
+def test_step_far_from_origin_forces_rechecks():
+    rng = np.random.default_rng(6)
+    X = (1000.0 + rng.normal(size=(40000, 3)) * 0.01).astype(np.float32)
+    C = 1000.0 + rng.normal(size=(8, 3)) * 0.01
+    (cn, lab, J, sh, em), (ocn, olab, oJ, osh, oem) = _step_both(X, C)
+    assert np.array_equal(lab, olab)
+    assert_centers_close(cn, ocn, X)
+    assert_J_close(J, oJ, X)
+
+
+def test_step_k_equals_n_and_k_one():
+    X = _mixture(64, 3, 4, seed=7)
+    C = X.astype(np.float64)
+    (cn, lab, J, sh, em), (ocn, olab, oJ, osh, oem) = _step_both(X, C)
+    assert np.array_equal(lab, olab) and np.array_equal(lab, np.arange(64))
+    assert oJ == 0.0 and abs(J) <= 1e-13 * float(np.sum(X.astype(np.float64) ** 2))
+    X = _mixture(3000, 6, 3, seed=8)
+    C = X[:1].astype(np.float64)
+    (cn, lab, J, sh, em), (ocn, olab, oJ, osh, oem) = _step_both(X, C)
+    assert np.array_equal(lab, olab) and lab.max() == 0
+    assert_centers_close(cn, ocn, X)
+
+
+def test_step_host_buffers_match_device_buffers():
+    X = _mixture(20000, 8, 16, seed=9)
+    C = _centers_from(X, 16, seed=1)
+    a = km.step(X, C)                                     # numpy in, numpy out (host staging)
+    b = km.step(torch.as_tensor(X, device=DEV), torch.as_tensor(C, device=DEV))
+    assert np.array_equal(a[1], to_np(b[1]))
+    assert np.array_equal(a[0], to_np(b[0]))
+    assert a[2] == b[2] and a[3] == b[3]
+
+
+@pytest.mark.parametrize("n,k,f,seed", [(20000, 4, 0.1, 0), (1_000_000, 32, 0.01, 3),
+                                        (1000, 256, 0.1, 5), (50, 50, 1.0, 1), (12345, 7, 0.37, 2**63 + 11)])
+def test_sample_matches_oracle(n, k, f, seed):
+    sub, pos = km.sample(n, k, f, seed, device=DEV)
+    osub, opos = oracle.sample(n, k, f, seed)
+    assert np.array_equal(to_np(sub), osub)
+    assert np.array_equal(to_np(pos), opos)
+
+
+def _fit_both(X, k, f, seed, tol, max_iter, tol_fast=0.0, **kw):
+    Xd = torch.as_tensor(X, device=DEV)
+    r = km.fit(Xd, k, f, seed, tol, max_iter, tol_fast=tol_fast, trajectories=True, **kw)
+    o = oracle.fit(X, k, f, seed, tol, max_iter, tol_fast=tol_fast, nthreads=NT)
+    return r, o
+
+
+def _assert_fit_equal(r, o, X):
+    assert (r.iters_fast, r.iters_slow) == (o["iters_fast"], o["iters_slow"])
+    assert (r.converged_fast, r.converged_slow) == (o["converged_fast"], o["converged_slow"])
+    assert np.array_equal(to_np(r.labels), o["labels"])
+    assert_centers_close(to_np(r.centers), o["centers"], X)
+    assert_J_close(r.J, o["J"], X)
+    assert r.subset_size == o["subset_size"] and r.distance_evals == o["distance_evals"]
+    assert r.empty_clusters == o["empty_clusters"]
+    for key in ("J_fast", "J_slow"):
+        for g, w in zip(r.traj[key], o["traj_" + key]):
+            assert_J_close(g, w, X)
+    for key in ("shift_fast", "shift_slow"):
+        assert np.allclose(r.traj[key], o["traj_" + key], rtol=1e-9, atol=1e-10)
+
+
+def test_fit_small_gaussian_config():
+    """n = 20,000, d = 2, k = 4, isotropic Gaussians, 10% subset, tol 1e-6, seed 0."""
+    X = to_np(synth.iso_gaussian_mixture(20000, 2, 4, seed=0))
+    r, o = _fit_both(X, 4, 0.1, 0, 1e-6, 100)
+    _assert_fit_equal(r, o, X)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fit_aniso_noise_d8_k32(use_graph):
+    X = to_np(synth.aniso_gaussian_noise(200_000, 8, 32, seed=1))
+    r, o = _fit_both(X, 32, 0.01, 1, 1e-5, 50, use_graph=use_graph)
+    _assert_fit_equal(r, o, X)
+
+
+def test_fit_vmf_d32_k64():
+    X = to_np(synth.vmf_mixture(30000, 32, 64, seed=2))
+    r, o = _fit_both(X, 64, 0.05, 2, 1e-6, 40, tol_fast=1e-3)
+    _assert_fit_equal(r, o, X)
+
+
+def test_fit_full_subset_theorem():
+    """Section 4.1 Theorem: with the whole set as S_s, the slow stage takes one
+    iteration without movement."""
+    X = _mixture(30000, 3, 5, seed=11)
+    r, o = _fit_both(X, 5, 1.0, 4, 0.0, 300)
+    _assert_fit_equal(r, o, X)
+    assert r.iters_slow == 1 and r.traj["shift_slow"].tolist() == [0.0]
+
+
+def test_fit_host_buffers_and_resume():
+    X = _mixture(40000, 4, 6, seed=12)
+    a = km.fit(X, 6, 0.1, 5, 1e-7, 60)                    # host in / host out
+    b = km.fit(torch.as_tensor(X, device=DEV), 6, 0.1, 5, 1e-7, 60)
+    assert np.array_equal(a.labels, to_np(b.labels)) and np.array_equal(a.centers, to_np(b.centers))
+    assert a.J == b.J
+    # resume the slow stage from given centers == oracle stage loop from them
+    C0 = _centers_from(X, 6, seed=3)
+    r = km.fit(X, 6, 0.1, 5, 1e-7, 60, init_centers=C0, start_stage=1)
+    o = oracle.lloyd_stage(X, C0, 1e-7, 60, nthreads=NT)
+    assert r.iters_fast == 0 and r.iters_slow == o["iters"]
+    assert np.array_equal(r.labels, o["labels"])
+    assert_centers_close(r.centers, o["centers"], X)
+    assert_J_close(r.J, o["J"], X)
+
+
+def test_fit_is_deterministic():
+    X = torch.as_tensor(synth.aniso_gaussian_noise(300_000, 8, 32, seed=4), device=DEV)
+    a = km.fit(X, 32, 0.02, 7, 1e-6, 30)
+    b = km.fit(X, 32, 0.02, 7, 1e-6, 30)
+    assert torch.equal(a.labels, b.labels) and torch.equal(a.centers, b.centers) and a.J == b.J
+
+
+def test_nonfinite_input_is_rejected():
+    X = _mixture(1000, 4, 3, seed=13)
+    X[17, 2] = np.nan
+    with pytest.raises(km.KMeans2Error) as e:
+        km.fit(torch.as_tensor(X, device=DEV), 3, 0.5, 0, 1e-6, 10)
+    assert e.value.status == -4
