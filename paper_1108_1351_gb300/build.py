@@ -9,6 +9,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 
@@ -45,6 +46,16 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
     """Compile and link the library; returns the path of the shared object."""
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
+    # objects built on another host architecture (x86 here, aarch64 on the GPU
+    # hosts) must not be linked: rebuild everything when the stamp differs
+    stamp = os.path.join(OBJ, "host_arch.txt")
+    arch = platform.machine()
+    try:
+        with open(stamp) as fh:
+            if fh.read().strip() != arch:
+                force = True
+    except OSError:
+        force = True
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = _headers()
     jobs = []
@@ -77,6 +88,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
             print(p.stdout)
             raise RuntimeError("linking libkmeans2.so failed")
         os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(arch)
     return LIB
 
 
