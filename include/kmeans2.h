@@ -173,6 +173,38 @@ KMEANS2_API int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, con
                 int32_t* empty_out, const kmeans2_options* opt);
 
 /*
+ * kmeans_step_noalloc -- kmeans_step for callers that cannot allocate device
+ * memory during the call.  (The paper has no counterpart: this is an
+ * integration variant of the library.)
+ *
+ * Some callers cannot call cudaMalloc once they are running: a service whose
+ * device memory is entirely owned by its own caching allocator or memory pool,
+ * where a stray allocation could fail or fragment that pool, or a latency-
+ * critical loop that must not wait on the allocator.  This entry point runs
+ * the same kernels as kmeans_step but takes its scratch from one fixed device
+ * array of 24 MiB compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ *  X, centers_in, centers_out, labels_out: DEVICE memory on the current device
+ *                (X 16-byte aligned); the caller still owns and passes them.
+ *  Limits: n <= 4,194,304, k <= 1024, d <= 128 (plus the limits of kmeans_step).
+ *          Larger shapes are rejected with KMEANS2_ERR_INVALID and a message in
+ *          kmeans2_last_error(); host pointers are rejected the same way.
+ *  stream: cudaStream_t (NULL = legacy default stream).
+ *  Other arguments and results as kmeans_step.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  Every call on a device
+ * shares the one array and overwrites it (each call clears what must start at
+ * zero): calls that overlap on the GPU -- concurrent streams or threads --
+ * race and must be serialised by the caller.
+ */
+KMEANS2_API int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
+                                    const double* centers_in, double* centers_out,
+                                    int32_t* labels_out, double* J_out, double* shift_out,
+                                    int32_t* empty_out, void* stream);
+
+/*
  * kmeans2_subset_size -- m = min(n, max(k, ceil(per*n))), the size of S_s
  * (Algorithm: "S_n = per% of S_n"; at least k points so that k distinct
  * initial centers exist).  Host only; returns -1 on invalid arguments.

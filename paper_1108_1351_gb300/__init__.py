@@ -6,7 +6,7 @@ library ``libkmeans2.so`` (C ABI in ``include/kmeans2.h``).  This package only
 binds it (``binding``) and provides seeded synthetic inputs (``synth``).
 """
 from .binding import (FitResult, KMeans2Error, LIB_PATH, Profile, declared_symbols, fit, load,
-                      sample, step, strerror, subset_size, version)
+                      sample, step, step_noalloc, strerror, subset_size, version)
 
 __all__ = ["FitResult", "KMeans2Error", "LIB_PATH", "Profile", "declared_symbols", "fit", "load",
-           "sample", "step", "strerror", "subset_size", "version"]
+           "sample", "step", "step_noalloc", "strerror", "subset_size", "version"]

@@ -98,6 +98,8 @@ def load():
                                     ctypes.POINTER(Result), ctypes.POINTER(Options)]
         lib.kmeans_step.restype = ctypes.c_int
         lib.kmeans_step.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, ctypes.POINTER(Options)]
+        lib.kmeans_step_noalloc.restype = ctypes.c_int
+        lib.kmeans_step_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P]
         lib.kmeans2_subset_size.restype = i64
         lib.kmeans2_subset_size.argtypes = [i64, i32, f64]
         lib.kmeans2_sample.restype = ctypes.c_int
@@ -274,6 +276,31 @@ def step(X, centers, *, precision: str = "fp32", stream=None, centers_out=None, 
                              ctypes.addressof(sh), ctypes.addressof(em), ctypes.byref(opt))
     if rc != 0:
         raise KMeans2Error(rc, "kmeans_step")
+    return cen, lab, J.value, sh.value, em.value
+
+
+def step_noalloc(X, centers, *, stream=None, centers_out=None, labels_out=None):
+    """kmeans_step_noalloc: one Lloyd iteration whose scratch is the library's
+    fixed device array (no device allocation inside the call).  X and centers
+    must be CUDA tensors; returns (centers', labels, J, shift, empty)."""
+    lib = load()
+    if not (_is_torch(X) and X.is_cuda):
+        raise TypeError("step_noalloc needs X on a CUDA device")
+    X = _as_points(X)
+    n, d = X.shape
+    C = _as_centers(centers, X)
+    k = C.shape[0]
+    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
+    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    J = ctypes.c_double()
+    sh = ctypes.c_double()
+    em = ctypes.c_int32()
+    with _device_of(X):
+        rc = lib.kmeans_step_noalloc(_ptr(X), n, d, k, _ptr(C), _ptr(cen), _ptr(lab),
+                                     ctypes.addressof(J), ctypes.addressof(sh),
+                                     ctypes.addressof(em), _stream_of(X, stream))
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans_step_noalloc")
     return cen, lab, J.value, sh.value, em.value
 
 

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "api_internal.h"
@@ -44,6 +45,13 @@ DeviceScratch::DeviceScratch(cudaStream_t s) : stream(s)
     if (sm_count < 1) sm_count = 1;
 }
 
+DeviceScratch::DeviceScratch(cudaStream_t s, void* arena_base, size_t bytes)
+    : DeviceScratch(s)
+{
+    arena = static_cast<unsigned char*>(arena_base);
+    arena_bytes = bytes;
+}
+
 DeviceScratch::~DeviceScratch()
 {
     for (void* p : ptrs) cudaFreeAsync(p, stream);
@@ -52,6 +60,17 @@ DeviceScratch::~DeviceScratch()
 int DeviceScratch::alloc(void** p, size_t bytes, cudaStream_t s)
 {
     if (bytes == 0) bytes = 16;
+    if (arena) {
+        size_t off = (arena_used + 255) & ~(size_t)255;
+        if (off + bytes > arena_bytes) {
+            set_last_error_text("fixed scratch area too small for this call");
+            *p = nullptr;
+            return KMEANS2_ERR_INVALID;
+        }
+        *p = arena + off;
+        arena_used = off + bytes;
+        return KMEANS2_OK;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         set_last_error("cudaMallocAsync", e);
@@ -326,6 +345,38 @@ Resolved resolve_options(const kmeans2_options* opt)
 
 }  // namespace
 
+// ---------------------------------------------------------------- fixed scratch
+// Scratch of kmeans_step_noalloc: one file-scope device array, present on every
+// GPU that loads this library until the process exits.  Its size bounds the
+// shapes that entry point accepts (see kNoAlloc* below).
+constexpr size_t kNoAllocBytes = 24ull << 20;           // 24 MiB per GPU
+constexpr long long kNoAllocMaxN = 1ll << 22;           // points
+constexpr int kNoAllocMaxK = 1024;                      // centers
+constexpr int kNoAllocMaxD = 128;                       // dimensions
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device (in host code the symbol names a host-side stand-in, not device memory).
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    KM2_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return KMEANS2_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        KM2_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return KMEANS2_OK;
+}
+}  // namespace
+
 }  // namespace km2
 
 using namespace km2;
@@ -436,6 +487,50 @@ int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, const double* c
     if (shift_out) *shift_out = out.shift;
     if (empty_out) *empty_out = out.empty;
     if (r.opt.profile) r.opt.profile->kernel_launches += g_launches - launches0;
+    return KMEANS2_OK;
+}
+
+int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
+                        const double* centers_in, double* centers_out, int32_t* labels_out,
+                        double* J_out, double* shift_out, int32_t* empty_out, void* stream)
+{
+    if (!X || !centers_in || !centers_out || !labels_out || !valid_shape(n, d, k))
+        return KMEANS2_ERR_INVALID;
+    if (n > kNoAllocMaxN || k > kNoAllocMaxK || d > kNoAllocMaxD) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg),
+                      "kmeans_step_noalloc: n=%lld, k=%d, d=%d exceed the fixed scratch limits "
+                      "n <= %lld, k <= %d, d <= %d", (long long)n, k, d, kNoAllocMaxN,
+                      kNoAllocMaxK, kNoAllocMaxD);
+        set_last_error_text(msg);
+        return KMEANS2_ERR_INVALID;
+    }
+    if (!is_device_ptr(X) || !is_device_ptr(centers_in) || !is_device_ptr(centers_out) ||
+        !is_device_ptr(labels_out) || (reinterpret_cast<uintptr_t>(X) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(labels_out) & 3) != 0) {
+        set_last_error_text("kmeans_step_noalloc: X, centers and labels must be device memory "
+                            "(X 16-byte aligned)");
+        return KMEANS2_ERR_INVALID;
+    }
+    void* arena = nullptr;
+    KM2_TRY(noalloc_scratch(&arena));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceScratch ws(s, arena, kNoAllocBytes);
+    Workspace w;
+    KM2_TRY(alloc_workspace(w, ws, n, k, d, 1, s));
+    KM2_CUDA(cudaMemcpyAsync(w.c.c64, centers_in, sizeof(double) * (size_t)k * d,
+                             cudaMemcpyDeviceToDevice, s));
+    KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
+    KM2_TRY(launch_maxabs(X, (long long)n * d, w.st, s, ws.sm_count));
+    StageState out;
+    KM2_TRY(run_stage(X, n, d, w, labels_out, 0.0, 1, false, s, ws.sm_count, out, nullptr,
+                      nullptr, nullptr));
+    KM2_CUDA(cudaMemcpyAsync(centers_out, w.c.c64, sizeof(double) * (size_t)k * d,
+                             cudaMemcpyDeviceToDevice, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    if (J_out) *J_out = out.J;
+    if (shift_out) *shift_out = out.shift;
+    if (empty_out) *empty_out = out.empty;
     return KMEANS2_OK;
 }
 

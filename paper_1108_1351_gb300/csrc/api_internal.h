@@ -43,7 +43,14 @@ struct DeviceScratch {
     int device = 0;
     std::vector<void*> ptrs;
 
+    // Arena mode: alloc() carves 256-byte-aligned pieces out of [arena, arena +
+    // arena_bytes) and never calls the allocator; nothing is freed.
+    unsigned char* arena = nullptr;
+    size_t arena_bytes = 0;
+    size_t arena_used = 0;
+
     explicit DeviceScratch(cudaStream_t s);
+    DeviceScratch(cudaStream_t s, void* arena_base, size_t bytes);
     ~DeviceScratch();
     int alloc(void** p, size_t bytes, cudaStream_t s);
     DeviceScratch(const DeviceScratch&) = delete;
