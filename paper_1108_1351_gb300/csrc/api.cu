@@ -471,7 +471,7 @@ int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, const double* c
                              is_device_ptr(centers_in) ? cudaMemcpyDeviceToDevice
                                                        : cudaMemcpyHostToDevice, s));
     KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
-    KM2_TRY(launch_maxabs(Xd, (long long)n * d, w.st, s, ws.sm_count));
+    KM2_TRY(launch_maxabs(Xd, n, d, w.st, s, ws.sm_count));
     StageState out;
     KM2_TRY(run_stage(Xd, n, d, w, labels, 0.0, 1, false, s, ws.sm_count, out, nullptr, nullptr,
                       r.opt.profile));
@@ -521,7 +521,7 @@ int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
     KM2_CUDA(cudaMemcpyAsync(w.c.c64, centers_in, sizeof(double) * (size_t)k * d,
                              cudaMemcpyDeviceToDevice, s));
     KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
-    KM2_TRY(launch_maxabs(X, (long long)n * d, w.st, s, ws.sm_count));
+    KM2_TRY(launch_maxabs(X, n, d, w.st, s, ws.sm_count));
     StageState out;
     KM2_TRY(run_stage(X, n, d, w, labels_out, 0.0, 1, false, s, ws.sm_count, out, nullptr,
                       nullptr, nullptr));
@@ -598,7 +598,7 @@ int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_f
     }
     // slow stage on S_n from the fast stage's final centers (Section 2; Section 5)
     KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
-    KM2_TRY(launch_maxabs(Xd, (long long)n * d, w.st, s, ws.sm_count));
+    KM2_TRY(launch_maxabs(Xd, n, d, w.st, s, ws.sm_count));
     StageState ss;
     KM2_TRY(run_stage(Xd, n, d, w, labels, tol, max_iter, use_graph, s, ws.sm_count, ss,
                       o.traj_J_slow, o.traj_shift_slow, o.profile));

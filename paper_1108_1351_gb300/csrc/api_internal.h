@@ -62,7 +62,9 @@ int sample_device(long long n, int k, long long m, unsigned long long seed, long
                   long long* init_pos, cudaStream_t s, DeviceScratch& ws);
 
 // prep.cu
-int launch_maxabs(const float* X, long long count, StageState* st, cudaStream_t s, int sm_count);
+// max |x| of n rows of d values, into st->maxabs_bits.
+int launch_maxabs(const float* X, long long n, int d, StageState* st, cudaStream_t s,
+                  int sm_count);
 int launch_gather(const float* X, int d, const long long* subset, long long m, float* Xs,
                   StageState* st, cudaStream_t s, int sm_count);
 int launch_init_centers(const float* Xs, int d, const long long* pos, int k, double* c64,

@@ -17,11 +17,13 @@
 // beyond the distances.
 //
 // Two forms:
-//  assign_small<D, P>  d <= 16.  Each thread owns P points in registers; the
-//                      k centers (pre-scaled by -2, with ||c||^2) sit in shared
-//                      memory and are read as broadcast 128-bit loads.  Per-CTA
-//                      int64 partial sums in shared memory, flushed to the
-//                      global split accumulators every <= 2^16 points.
+//  assign_small<D>     d <= 16.  Each thread owns P points in registers and
+//                      prefetches its next tile with cp.async; the k centers
+//                      (pre-scaled by -2, with ||c||^2) sit in shared memory
+//                      and are read as broadcast 128-bit loads, two at a time;
+//                      the top-2 runs on packed keys (index in the low mantissa
+//                      bits).  Per-CTA int64 partial sums in shared memory,
+//                      flushed to the global split accumulators every 2^16 points.
 //  assign_large        any d.  128 points x 128 centers register-blocked tiles
 //                      (8 x 8 per thread) over 8-dimension slices staged in
 //                      shared memory; per-thread top-2 merged across the 16
@@ -65,170 +67,270 @@ __device__ __forceinline__ void top2_merge(float& b1, float& b2, int& bi, float 
 
 template <int D>
 struct SmallCfg {
-    static constexpr int DS = (D + 1 + 3) & ~3;   // floats per center in shared memory
+    static constexpr int DS = (D + 3) & ~3;       // floats per center (-2c) in shared memory
     static constexpr int P = D <= 8 ? 4 : 2;      // points per thread
+    static constexpr int V = (D % 4 == 0) ? 4 : ((D % 2 == 0) ? 2 : 1);   // copy width (floats)
+    static constexpr int NV = D / V;              // copies per point
+    static constexpr int TILE = kThreads * P;     // points per tile
+    static constexpr int FLUSH_TILES = kFlushPoints / TILE;
 };
 
-template <int D>
-__device__ __forceinline__ void load_point(const float* __restrict__ X, long long i, float* x)
+// Packed key: the float v with its 5 low mantissa bits replaced by j (0..31).
+// Compared as floats, keys order like the values up to 2^-18 |v|; which of two
+// near-equal keys wins does not matter, since such points are rechecked.
+__device__ __forceinline__ float pack_key(float v, unsigned j)
 {
-    const float* src = X + i * D;
-    if constexpr (D % 4 == 0) {
+    return __uint_as_float((__float_as_uint(v) & ~31u) | j);
+}
+
+template <int D>
+__device__ __forceinline__ void copy_point_async(float* sx, const float* src, int p, int tid)
+{
+    using C = SmallCfg<D>;
 #pragma unroll
-        for (int t = 0; t < D; t += 4) {
-            float4 v = __ldg(reinterpret_cast<const float4*>(src + t));
-            x[t] = v.x; x[t + 1] = v.y; x[t + 2] = v.z; x[t + 3] = v.w;
-        }
-    } else if constexpr (D % 2 == 0) {
-#pragma unroll
-        for (int t = 0; t < D; t += 2) {
-            float2 v = __ldg(reinterpret_cast<const float2*>(src + t));
-            x[t] = v.x; x[t + 1] = v.y;
-        }
-    } else {
-#pragma unroll
-        for (int t = 0; t < D; ++t) x[t] = __ldg(src + t);
+    for (int q = 0; q < C::NV; ++q) {
+        float* dst = sx + ((size_t)(p * C::NV + q) * kThreads + tid) * C::V;
+        if constexpr (C::V == 4) cp_async16(dst, src + 4 * q);
+        else if constexpr (C::V == 2) cp_async8(dst, src + 2 * q);
+        else cp_async4(dst, src + q);
     }
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads)
-assign_small(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
-             StageState* st, Accum acc, int* __restrict__ list, float kappa)
+__device__ __forceinline__ void read_point(const float* sx, int p, int tid, float* x)
 {
-    constexpr int DS = SmallCfg<D>::DS;
-    constexpr int P = SmallCfg<D>::P;
+    using C = SmallCfg<D>;
+#pragma unroll
+    for (int q = 0; q < C::NV; ++q) {
+        const float* src = sx + ((size_t)(p * C::NV + q) * kThreads + tid) * C::V;
+        if constexpr (C::V == 4) {
+            float4 v = *reinterpret_cast<const float4*>(src);
+            x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+        } else if constexpr (C::V == 2) {
+            float2 v = *reinterpret_cast<const float2*>(src);
+            x[2 * q] = v.x; x[2 * q + 1] = v.y;
+        } else {
+            x[q] = src[0];
+        }
+    }
+}
+
+// Points are owned by threads (tile point p * 256 + tid); each thread prefetches
+// its own next-tile points (and old labels) with cp.async into its own shared
+// slots while it computes the current tile, so no thread waits on another.
+// Centers are walked in chunks of 32 and in pairs; the running top-2 of packed
+// keys costs 2.5 min/max operations per distance (3-input min).
+template <int D>
+__global__ void __launch_bounds__(kThreads, 2)
+assign_small(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
+             StageState* st, Accum acc, int* __restrict__ list, float kappa, float kpack,
+             int use_sacc)
+{
+    using C = SmallCfg<D>;
+    constexpr int DS = C::DS;
+    constexpr int P = C::P;
     extern __shared__ __align__(16) float smem[];
     const int k = c.k;
-    float* sc = smem;                                                   // k * DS
-    long long* sacc = reinterpret_cast<long long*>(smem + (size_t)k * DS);  // k * D
-    int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);               // k
+    const int kc = (k + 31) & ~31;
+    const int nchunks = kc >> 5;
+    float* sc = smem;                                          // kc * DS: -2 c_j
+    float* ss = sc + (size_t)kc * DS;                          // kc: ||c_j||^2
+    float* sx = ss + kc;                                       // TILE * D (thread-major)
+    int* sl = reinterpret_cast<int*>(sx + (size_t)C::TILE * D);  // TILE old labels
+    long long* sacc = reinterpret_cast<long long*>(sl + C::TILE);  // k * D (if use_sacc)
+    int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);       // k (if use_sacc)
     __shared__ unsigned long long sq;
-    __shared__ int s_pts;
 
     if (st->error) return;
     const int mode = st->mode;
     const float scaleF = st->scaleF;
     const float scaleG = st->scaleG;
-    const float c2x2 = 2.0f * st->cmax2;
+    const float thr_base = 2.0f * st->cmax2;
     const int tid = threadIdx.x;
 
-    for (int e = tid; e < k * DS; e += kThreads) {
+    for (int e = tid; e < kc * DS; e += kThreads) {
         int j = e / DS, t = e - j * DS;
-        float v = 0.0f;
-        if (t < D) v = -2.0f * c.c32[(long long)j * D + t];
-        else if (t == D) v = c.cnorm[j];
-        sc[e] = v;
+        sc[e] = (j < k && t < D) ? -2.0f * c.c32[(long long)j * D + t] : 0.0f;
     }
-    for (int e = tid; e < k * D; e += kThreads) sacc[e] = 0;
-    for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
-    if (tid == 0) { sq = 0; s_pts = 0; }
+    for (int j = tid; j < kc; j += kThreads)
+        ss[j] = (j < k) ? c.cnorm[j] : FLT_MAX;   // padding center: never the best
+    if (use_sacc) {
+        for (int e = tid; e < k * D; e += kThreads) sacc[e] = 0;
+        for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
+    }
+    if (tid == 0) sq = 0;
     __syncthreads();
 
-    long long qloc = 0;
-    const long long tile_pts = (long long)kThreads * P;
-    const long long ntiles = (n + tile_pts - 1) / tile_pts;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long base = tile * tile_pts;
-        float x[P][D];
+    const long long ntiles = (n + C::TILE - 1) / C::TILE;
+    auto prefetch = [&](long long tile, unsigned dep) {
+        // `dep` is computed from this thread's reads of the slots about to be
+        // refilled: consuming it here orders those reads before the copies.
+        asm volatile("" ::"r"(dep) : "memory");
+        const long long base = tile * C::TILE;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            long long i = base + (long long)p * kThreads + tid;
+            const long long i = base + (long long)p * kThreads + tid;
             if (i < n) {
-                load_point<D>(X, i, x[p]);
+                copy_point_async<D>(sx, X + i * D, p, tid);
+                if (mode == kModeDelta) cp_async4(sl + p * kThreads + tid, labels + i);
+            }
+        }
+        cp_async_commit();
+    };
+    if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0u);
+
+    long long qloc = 0;
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const long long base = tile * C::TILE;
+        cp_async_wait_all();
+        float x[P][D];
+        int oldl[P];
+        float xn2[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const long long i = base + (long long)p * kThreads + tid;
+            if (i < n) {
+                read_point<D>(sx, p, tid, x[p]);
+                oldl[p] = (mode == kModeDelta) ? sl[p * kThreads + tid] : -1;
             } else {
 #pragma unroll
                 for (int t = 0; t < D; ++t) x[p][t] = 0.0f;
+                oldl[p] = -1;
             }
+            float s2 = 0.0f;
+#pragma unroll
+            for (int t = 0; t < D; ++t) s2 = fmaf(x[p][t], x[p][t], s2);
+            xn2[p] = s2;
         }
-        float b1[P], b2[P];
-        int bi[P];
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) {
+            unsigned dep = __float_as_uint(xn2[0]);
 #pragma unroll
-        for (int p = 0; p < P; ++p) { b1[p] = FLT_MAX; b2[p] = FLT_MAX; bi[p] = 0; }
-#pragma unroll 2
-        for (int j = 0; j < k; ++j) {
-            float cv[DS];
-            const float4* cj = reinterpret_cast<const float4*>(sc + j * DS);
+            for (int p = 1; p < P; ++p) dep ^= __float_as_uint(xn2[p]);
+            prefetch(next, dep);
+        }
+
+        float B1[P], B2[P];
+        int BI[P];
 #pragma unroll
-            for (int q = 0; q < DS / 4; ++q) {
-                float4 v = cj[q];
-                cv[4 * q] = v.x; cv[4 * q + 1] = v.y; cv[4 * q + 2] = v.z; cv[4 * q + 3] = v.w;
+        for (int p = 0; p < P; ++p) { B1[p] = INFINITY; B2[p] = INFINITY; BI[p] = 0; }
+        for (int ch = 0; ch < nchunks; ++ch) {
+            float b1[P], b2[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) { b1[p] = INFINITY; b2[p] = INFINITY; }
+            const float* cbase = sc + (size_t)(ch << 5) * DS;
+            const float* sbase = ss + (ch << 5);
+#pragma unroll 4
+            for (unsigned jj = 0; jj < 32; jj += 2) {
+                float c0[DS], c1[DS];
+                const float4* q0 = reinterpret_cast<const float4*>(cbase + jj * DS);
+                const float4* q1 = reinterpret_cast<const float4*>(cbase + (jj + 1) * DS);
+#pragma unroll
+                for (int q = 0; q < DS / 4; ++q) {
+                    float4 v0 = q0[q], v1 = q1[q];
+                    c0[4 * q] = v0.x; c0[4 * q + 1] = v0.y; c0[4 * q + 2] = v0.z; c0[4 * q + 3] = v0.w;
+                    c1[4 * q] = v1.x; c1[4 * q + 1] = v1.y; c1[4 * q + 2] = v1.z; c1[4 * q + 3] = v1.w;
+                }
+                const float2 st01 = *reinterpret_cast<const float2*>(sbase + jj);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float d0 = st01.x, d1 = st01.y;
+#pragma unroll
+                    for (int t = 0; t < D; ++t) {
+                        d0 = fmaf(x[p][t], c0[t], d0);
+                        d1 = fmaf(x[p][t], c1[t], d1);
+                    }
+                    const float k0 = pack_key(d0, jj), k1 = pack_key(d1, jj | 1u);
+                    const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+                    b2[p] = fmin3(b2[p], hi, fmaxf(b1[p], lo));
+                    b1[p] = fminf(b1[p], lo);
+                }
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float dd = cv[D];
-#pragma unroll
-                for (int t = 0; t < D; ++t) dd = fmaf(x[p][t], cv[t], dd);
-                top2_push(dd, j, b1[p], b2[p], bi[p]);
+                if (b1[p] < B1[p]) {
+                    B2[p] = fminf(B1[p], b2[p]);
+                    B1[p] = b1[p];
+                    BI[p] = (ch << 5) | (int)(__float_as_uint(b1[p]) & 31u);
+                } else {
+                    B2[p] = fminf(B2[p], b1[p]);
+                }
             }
         }
-        int touched = 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const long long i = base + (long long)p * kThreads + tid;
             const bool valid = i < n;
-            float xn2 = 0.0f;
-#pragma unroll
-            for (int t = 0; t < D; ++t) xn2 = fmaf(x[p][t], x[p][t], xn2);
-            const bool flag = valid && (b2[p] - b1[p] <= kappa * (c2x2 + xn2));
+            const float thr = kappa * (thr_base + xn2[p]) + kpack * (fabsf(B1[p]) + fabsf(B2[p]));
+            const bool flag = valid && (B2[p] - B1[p] <= thr);
             if (mode == kModeFull && valid) {
 #pragma unroll
                 for (int t = 0; t < D; ++t) qloc += sq_fixed(x[p][t], scaleG);
-                ++touched;
             }
             recheck_append(flag, (int)i, list, &st->recheck_count);
             if (valid && !flag) {
-                const int lab = bi[p];
-                const int old = (mode == kModeDelta) ? labels[i] : -1;
+                const int lab = BI[p];
+                const int old = oldl[p];
                 if (lab != old) {
 #pragma unroll
                     for (int t = 0; t < D; ++t) {
-                        long long v = to_fixed(x[p][t], scaleF);
-                        atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * D + t),
-                                  (unsigned long long)v);
-                        if (old >= 0)
-                            atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + t),
-                                      (unsigned long long)(-v));
+                        const long long v = to_fixed(x[p][t], scaleF);
+                        if (use_sacc) {
+                            atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * D + t),
+                                      (unsigned long long)v);
+                            if (old >= 0)
+                                atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + t),
+                                          (unsigned long long)(-v));
+                        } else {
+                            split_add(acc.s_lo + (long long)lab * D + t,
+                                      acc.s_hi + (long long)lab * D + t, v);
+                            if (old >= 0)
+                                split_add(acc.s_lo + (long long)old * D + t,
+                                          acc.s_hi + (long long)old * D + t, -v);
+                        }
                     }
-                    atomicAdd(scnt + lab, 1);
-                    if (old >= 0) atomicAdd(scnt + old, -1);
+                    if (use_sacc) {
+                        atomicAdd(scnt + lab, 1);
+                        if (old >= 0) atomicAdd(scnt + old, -1);
+                    } else {
+                        atomicAdd(acc.cnt + lab, 1ull);
+                        if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                    }
                     labels[i] = lab;
-                    if (mode == kModeDelta) ++touched;
                 }
             }
         }
-        for (int o = 16; o; o >>= 1) touched += __shfl_xor_sync(0xffffffffu, touched, o);
-        if ((tid & 31) == 0 && touched) atomicAdd(&s_pts, touched);
-        __syncthreads();
+        // Static flush schedule: at most FLUSH_TILES tiles (2^16 points) per partial.
         const bool last = tile + gridDim.x >= ntiles;
-        const bool do_flush = s_pts > kFlushPoints - tile_pts || last;
-        __syncthreads();   // every thread has read s_pts before it changes again
-        if (do_flush) {
+        if ((it + 1) % C::FLUSH_TILES == 0 || last) {
             if (qloc) atomicAdd(&sq, (unsigned long long)qloc);
             qloc = 0;
             __syncthreads();
-            for (int e = tid; e < k * D; e += kThreads) {
-                long long v = sacc[e];
-                if (v) {
-                    split_add(acc.s_lo + e, acc.s_hi + e, v);
-                    sacc[e] = 0;
+            if (use_sacc) {
+                for (int e = tid; e < k * D; e += kThreads) {
+                    const long long v = sacc[e];
+                    if (v) {
+                        split_add(acc.s_lo + e, acc.s_hi + e, v);
+                        sacc[e] = 0;
+                    }
                 }
-            }
-            for (int e = tid; e < k; e += kThreads) {
-                int v = scnt[e];
-                if (v) {
-                    atomicAdd(acc.cnt + e, (unsigned long long)(long long)v);
-                    scnt[e] = 0;
+                for (int e = tid; e < k; e += kThreads) {
+                    const int v = scnt[e];
+                    if (v) {
+                        atomicAdd(acc.cnt + e, (unsigned long long)(long long)v);
+                        scnt[e] = 0;
+                    }
                 }
             }
             if (tid == 0) {
                 if (sq) split_add(&st->q_lo, &st->q_hi, (long long)sq);
                 sq = 0;
-                s_pts = 0;
             }
             __syncthreads();
         }
     }
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------- large d
@@ -396,21 +498,27 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
 }
 
 template <int D>
-size_t small_smem(int k)
+size_t small_smem(int k, bool with_acc)
 {
-    return (size_t)k * SmallCfg<D>::DS * sizeof(float) + (size_t)k * D * sizeof(long long) +
-           (size_t)k * sizeof(int);
+    using C = SmallCfg<D>;
+    size_t kc = (size_t)((k + 31) & ~31);
+    size_t bytes = kc * (C::DS + 1) * sizeof(float) + (size_t)C::TILE * D * sizeof(float) +
+                   (size_t)C::TILE * sizeof(int);
+    if (with_acc) bytes += (size_t)k * D * sizeof(long long) + (size_t)k * sizeof(int);
+    return bytes;
 }
 
 template <int D>
 int launch_small(const float* X, long long n, const Centers& c, int* labels, StageState* st,
                  const Accum& acc, int* list, cudaStream_t s, int sm_count)
 {
-    size_t sm = small_smem<D>(c.k);
+    const bool with_acc = small_smem<D>(c.k, true) <= (size_t)kSmallSmemCap;
+    const size_t sm = small_smem<D>(c.k, with_acc);
+    if (sm > (size_t)kSmallSmemCap) return KMEANS2_ERR_UNSUPPORTED;
     static thread_local int configured_for = -1;
     int dev = 0;
     KM2_CUDA(cudaGetDevice(&dev));
-    if (sm > 48 * 1024 && configured_for != dev) {
+    if (configured_for != dev) {
         KM2_CUDA(cudaFuncSetAttribute(assign_small<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kSmallSmemCap));
         configured_for = dev;
@@ -418,22 +526,25 @@ int launch_small(const float* X, long long n, const Centers& c, int* labels, Sta
     int per_sm = 0;
     KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assign_small<D>, kThreads, sm));
     if (per_sm < 1) return KMEANS2_ERR_UNSUPPORTED;
-    long long tiles = (n + (long long)kThreads * SmallCfg<D>::P - 1) / ((long long)kThreads * SmallCfg<D>::P);
+    const long long tiles = (n + SmallCfg<D>::TILE - 1) / SmallCfg<D>::TILE;
     long long grid = (long long)sm_count * per_sm;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
     ++g_launches;
-    assign_small<D><<<(int)grid, kThreads, sm, s>>>(X, n, c, labels, st, acc, list, tie_kappa(D));
+    assign_small<D><<<(int)grid, kThreads, sm, s>>>(X, n, c, labels, st, acc, list, tie_kappa(D),
+                                                    kPackSlack, with_acc ? 1 : 0);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
 
 }  // namespace
 
-static size_t small_smem_any(int d, int k)
+// Shared memory of assign_small without per-CTA accumulators (the smallest form).
+static size_t small_smem_min(int d, int k)
 {
-    size_t ds = (size_t)((d + 1 + 3) & ~3);
-    return (size_t)k * ds * 4 + (size_t)k * d * 8 + (size_t)k * 4;
+    size_t ds = (size_t)((d + 3) & ~3) + 1;
+    size_t tile = (size_t)kThreads * (d <= 8 ? 4 : 2);
+    return (size_t)((k + 31) & ~31) * ds * 4 + tile * d * 4 + tile * 4;
 }
 
 int assign_fp32_supported(int d, int k)
@@ -446,7 +557,7 @@ int assign_fp32_supported(int d, int k)
 int launch_assign_fp32(const float* X, long long n, int d, const Centers& c, int* labels,
                        StageState* st, const Accum& acc, int* list, cudaStream_t s, int sm_count)
 {
-    if (d <= 16 && small_smem_any(d, c.k) <= (size_t)kSmallSmemCap) {
+    if (d <= 16 && small_smem_min(d, c.k) <= (size_t)kSmallSmemCap) {
         switch (d) {
 #define KM2_CASE(DD) \
     case DD: return launch_small<DD>(X, n, c, labels, st, acc, list, s, sm_count);

@@ -98,6 +98,45 @@ __device__ __forceinline__ long long sq_fixed(float x, float scaleG)
     return __float2ll_rn(p * scaleG) + __float2ll_rn(e * scaleG);
 }
 
+// 3-input minimum (sm_100+ PTX form).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Asynchronous global->shared copies of one thread's own data (Ampere-style
+// cp.async; completion is waited for by the same thread with cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;
@@ -128,5 +167,12 @@ __host__ __device__ inline float tie_kappa(int d)
 {
     return 2.0f * (float)(d + 3) * 5.9604644775390625e-8f * 1.0625f;
 }
+
+// The small-d kernel compares packed keys: D_j with the center's index within
+// its chunk of 32 written into the 5 low mantissa bits, compared as floats.  A
+// key differs from D_j by less than 2^-18 |D_j|, so the two keys of a point
+// add at most 2^-18 (|key_1| + |key_2|) (1 + 2^-17) to the gap error; the
+// threshold adds kPackSlack (|key_1| + |key_2|) to the FMA bound.
+constexpr float kPackSlack = 3.814697265625e-6f * 1.0625f;   // 2^-18 * 1.0625
 
 }  // namespace km2

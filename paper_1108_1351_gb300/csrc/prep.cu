@@ -323,8 +323,10 @@ static int grid_for(long long work, int threads, int sm_count, int per_sm)
     return (int)g;
 }
 
-int launch_maxabs(const float* X, long long count, StageState* st, cudaStream_t s, int sm_count)
+int launch_maxabs(const float* X, long long n, int d, StageState* st, cudaStream_t s,
+                  int sm_count)
 {
+    const long long count = n * d;
     int vec4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
     ++g_launches;
     maxabs_kernel<<<grid_for(count / 4 + 1, 256, sm_count, 8), 256, 0, s>>>(X, count, vec4, st);

@@ -53,6 +53,8 @@ STEP_SHAPES = [
     (5000, 1, 3), (20000, 2, 4), (10001, 3, 7), (9999, 5, 16), (70001, 8, 32), (12345, 13, 50),
     (30000, 16, 256), (5000, 17, 5), (20000, 32, 64), (10000, 64, 200), (4099, 128, 1024),
     (3000, 300, 10),
+    # large enough that every CTA of the persistent grid walks several tiles
+    (2_000_003, 8, 32), (1_500_001, 3, 7), (1_200_000, 16, 40), (700_001, 5, 100),
 ]
 
 
@@ -143,6 +145,13 @@ def _assert_fit_equal(r, o, X):
             assert_J_close(g, w, X)
     for key in ("shift_fast", "shift_slow"):
         assert np.allclose(r.traj[key], o["traj_" + key], rtol=1e-9, atol=1e-10)
+
+
+def test_fit_multi_tile_delta_iterations():
+    """Enough points for many tiles per CTA and many incremental iterations."""
+    X = to_np(synth.aniso_gaussian_noise(1_500_000, 8, 32, seed=21))
+    r, o = _fit_both(X, 32, 0.05, 9, 1e-4, 25)
+    _assert_fit_equal(r, o, X)
 
 
 def test_fit_small_gaussian_config():
