@@ -72,9 +72,15 @@ extern "C" {
 #define KMEANS2_ERR_UNSUPPORTED (-7)  /* shape or mode not available on this build */
 
 /* ---------------------------------------------------------------- options */
-#define KMEANS2_PRECISION_FP32 0      /* FP32 CUDA-core distances + FP64 recheck */
-#define KMEANS2_PRECISION_BF16 1      /* BF16 tensor-core cross term + FP64 recheck */
-#define KMEANS2_PRECISION_AUTO 2      /* BF16 where d >= 32, else FP32 */
+/* Forms of the distance kernel.  Every form returns the same labels (near
+   ties are re-decided in FP64); they differ in speed and in how many points
+   need that recheck. */
+#define KMEANS2_PRECISION_FP32 0      /* FP32 FMA chains on the CUDA cores (plain form) */
+#define KMEANS2_PRECISION_BF16 1      /* BF16 tensor-core cross term (not in this build) */
+#define KMEANS2_PRECISION_AUTO 2      /* fastest form measured for the shape (default) */
+#define KMEANS2_PRECISION_TF32X3 3    /* cross term on the tensor cores as three TF32
+                                         products of the exact hi/lo split of the FP32
+                                         operands; d in {4, 8, 16, 32}, k <= 256 */
 
 /* Optional per-call measurement, filled by the library when options->profile
    is set.  A profiled call runs each stage loop from the host (no graph) and
@@ -89,7 +95,7 @@ typedef struct kmeans2_profile {
 } kmeans2_profile;
 
 typedef struct kmeans2_options {
-    int32_t precision;          /* KMEANS2_PRECISION_*; default FP32 */
+    int32_t precision;          /* KMEANS2_PRECISION_*; default AUTO */
     int32_t deterministic;      /* accepted for interface stability; every mode is
                                    deterministic (exact integer cluster sums) */
     double tol_fast;            /* stop tolerance of the fast stage; <= 0: use tol.
@@ -111,7 +117,7 @@ typedef struct kmeans2_options {
     kmeans2_profile* profile;   /* optional HOST struct, see kmeans2_profile */
 } kmeans2_options;
 
-/* Fill *opt with the defaults (FP32, tol_fast = tol, random init, graph loop). */
+/* Fill *opt with the defaults (AUTO form, tol_fast = tol, random init, graph loop). */
 KMEANS2_API void kmeans2_default_options(kmeans2_options* opt);
 
 typedef struct kmeans2_result {
@@ -122,7 +128,7 @@ typedef struct kmeans2_result {
     int32_t converged_fast;     /* 1 if the fast stage met its tolerance */
     int32_t converged_slow;     /* 1 if the slow stage met tol */
     int32_t empty_clusters;     /* clusters left without points in the last iteration */
-    int32_t precision_used;     /* KMEANS2_PRECISION_FP32 or _BF16 */
+    int32_t precision_used;     /* the form that ran: KMEANS2_PRECISION_FP32 or _TF32X3 */
     int64_t subset_size;        /* m = |S_s| */
     int64_t rechecked_points;   /* points re-evaluated in FP64, summed over iterations */
     int64_t distance_evals;     /* K Q_f m + K Q_s n (Section 3 cost model) */
@@ -149,7 +155,9 @@ typedef struct kmeans2_result {
  *  opt           may be NULL (defaults).
  * Errors: KMEANS2_ERR_INVALID (n < 1, d < 1, k < 1, k > n, per outside (0, 1],
  * tol < 0 or NaN, max_iter < 1, NULL X/centers_out/labels_out, limits above),
- * KMEANS2_ERR_NONFINITE, KMEANS2_ERR_NOMEM, KMEANS2_ERR_CUDA.
+ * KMEANS2_ERR_UNSUPPORTED (a precision form the shape cannot run),
+ * KMEANS2_ERR_NONFINITE, KMEANS2_ERR_NOMEM, KMEANS2_ERR_CUDA,
+ * KMEANS2_ERR_TIMEOUT (a bounded wait inside a tensor-core kernel gave up).
  */
 KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_fraction,
                 uint64_t seed, double tol, int32_t max_iter, double* centers_out,

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkmeans2.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "kmeans2.h")
 
-PRECISION = {"fp32": 0, "bf16": 1, "auto": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "auto": 2, "tf32x3": 3}
 _lock = threading.Lock()
 _lib = None
 
@@ -210,7 +210,7 @@ class FitResult:
 
 
 def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int, *,
-        tol_fast: float = 0.0, precision: str = "fp32", init_centers=None, start_stage: int = 0,
+        tol_fast: float = 0.0, precision: str = "auto", init_centers=None, start_stage: int = 0,
         use_graph: bool = True, stream=None, trajectories: bool = False, centers_out=None,
         labels_out=None, profile: "Profile | None" = None) -> FitResult:
     """Two-stage k-means (kmeans2_fit).  Outputs live where X lives (device
@@ -250,10 +250,11 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                      subset_size=res.subset_size, rechecked_points=res.rechecked_points,
                      distance_evals=res.distance_evals, shift_fast=res.shift_fast,
                      shift_slow=res.shift_slow, seconds=res.seconds,
-                     precision_used={0: "fp32", 1: "bf16"}.get(res.precision_used, "?"), traj=traj)
+                     precision_used={0: "fp32", 1: "bf16", 3: "tf32x3"}.get(res.precision_used, "?"),
+                     traj=traj)
 
 
-def step(X, centers, *, precision: str = "fp32", stream=None, centers_out=None, labels_out=None,
+def step(X, centers, *, precision: str = "auto", stream=None, centers_out=None, labels_out=None,
          profile: "Profile | None" = None):
     """One Lloyd iteration (kmeans_step): returns (centers', labels, J, shift, empty)."""
     lib = load()

@@ -124,6 +124,7 @@ cudaStream_t private_stream(int device)
 }
 
 struct Workspace {
+    int form = KMEANS2_PRECISION_FP32;   // distance-kernel form used by this call
     Centers c{};
     Accum acc{};
     StageState* st = nullptr;
@@ -160,11 +161,45 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     return KMEANS2_OK;
 }
 
+// The fused distance kernel of the chosen form.
+int launch_assign(const float* X, long long n, int d, Workspace& w, int* labels, cudaStream_t s,
+                  int sm_count)
+{
+    if (w.form == KMEANS2_PRECISION_TF32X3)
+        return launch_assign_tc32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
+    return launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
+}
+
+// Resolve the requested precision to the form this shape runs in.
+int choose_form(int requested, int d, int k, const float* X, int* form)
+{
+    const bool tc = assign_tc32_supported(d, k, X) != 0;
+    switch (requested) {
+        case KMEANS2_PRECISION_FP32: *form = KMEANS2_PRECISION_FP32; return KMEANS2_OK;
+        case KMEANS2_PRECISION_TF32X3:
+            if (!tc) {
+                set_last_error_text("the 3xTF32 tensor-core form needs d in {4, 8, 16, 32}, "
+                                    "k <= 256 and 16-byte aligned X");
+                return KMEANS2_ERR_UNSUPPORTED;
+            }
+            *form = KMEANS2_PRECISION_TF32X3;
+            return KMEANS2_OK;
+        case KMEANS2_PRECISION_AUTO:
+            // For FP32 data with d <= 32 the CUDA-core form is as fast per launch and
+            // flags far fewer near ties than the 3xTF32 tensor-core form (measured).
+            *form = KMEANS2_PRECISION_FP32;
+            return KMEANS2_OK;
+        default:
+            set_last_error_text("precision form not available in this build");
+            return KMEANS2_ERR_UNSUPPORTED;
+    }
+}
+
 // One Lloyd iteration: assign -> recheck -> finalize.
 int launch_iteration(const float* X, long long n, int d, Workspace& w, int* labels,
                      unsigned long long handle, int use_cond, cudaStream_t s, int sm_count)
 {
-    KM2_TRY(launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count));
+    KM2_TRY(launch_assign(X, n, d, w, labels, s, sm_count));
     KM2_TRY(launch_recheck(X, d, w.c, labels, w.list, w.st, w.acc, s, sm_count));
     KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, handle, use_cond,
                             s));
@@ -233,7 +268,7 @@ int run_loop_host(const float* X, long long n, int d, Workspace& w, int* labels,
     for (int it = 0; it < max_iter && rc == KMEANS2_OK; ++it) {
         if (prof) {
             cudaEventRecord(ev0, s);
-            rc = launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
+            rc = launch_assign(X, n, d, w, labels, s, sm_count);
             cudaEventRecord(ev1, s);
             if (rc == KMEANS2_OK)
                 rc = launch_recheck(X, d, w.c, labels, w.list, w.st, w.acc, s, sm_count);
@@ -267,6 +302,10 @@ int map_stage_error(int err)
     if (err == kErrNonFinite) {
         set_last_error_text("X holds a NaN or an infinity");
         return KMEANS2_ERR_NONFINITE;
+    }
+    if (err == kErrTimeout) {
+        set_last_error_text("a device-side wait on the tensor-core pipeline timed out");
+        return KMEANS2_ERR_TIMEOUT;
     }
     set_last_error_text("max|x| >= 2^50 is outside the supported range");
     return KMEANS2_ERR_UNSUPPORTED;
@@ -387,7 +426,7 @@ void kmeans2_default_options(kmeans2_options* opt)
 {
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
-    opt->precision = KMEANS2_PRECISION_FP32;
+    opt->precision = KMEANS2_PRECISION_AUTO;
     opt->deterministic = 1;
     opt->use_graph = 1;
 }
@@ -455,14 +494,13 @@ int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, const double* c
     if (!X || !centers_in || !centers_out || !labels_out || !valid_shape(n, d, k))
         return KMEANS2_ERR_INVALID;
     Resolved r = resolve_options(opt);
-    if (r.opt.precision != KMEANS2_PRECISION_FP32 && r.opt.precision != KMEANS2_PRECISION_AUTO)
-        return KMEANS2_ERR_UNSUPPORTED;
     const long long launches0 = g_launches;
     cudaStream_t s = r.stream;
     DeviceScratch ws(s);
     const float* Xd = nullptr;
     KM2_TRY(device_view(X, (long long)n * d, &Xd, ws, s));
     Workspace w;
+    KM2_TRY(choose_form(r.opt.precision, d, k, Xd, &w.form));
     KM2_TRY(alloc_workspace(w, ws, n, k, d, 1, s));
     bool lab_dev = is_device_ptr(labels_out) && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
     int* labels = lab_dev ? labels_out : nullptr;
@@ -517,6 +555,7 @@ int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceScratch ws(s, arena, kNoAllocBytes);
     Workspace w;
+    KM2_TRY(choose_form(KMEANS2_PRECISION_AUTO, d, k, X, &w.form));
     KM2_TRY(alloc_workspace(w, ws, n, k, d, 1, s));
     KM2_CUDA(cudaMemcpyAsync(w.c.c64, centers_in, sizeof(double) * (size_t)k * d,
                              cudaMemcpyDeviceToDevice, s));
@@ -545,8 +584,6 @@ int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_f
         return KMEANS2_ERR_INVALID;
     Resolved r = resolve_options(opt);
     const kmeans2_options& o = r.opt;
-    if (o.precision != KMEANS2_PRECISION_FP32 && o.precision != KMEANS2_PRECISION_AUTO)
-        return KMEANS2_ERR_UNSUPPORTED;
     if (o.start_stage != 0 && o.start_stage != 1) return KMEANS2_ERR_INVALID;
     if (o.start_stage == 1 && !o.init_centers) return KMEANS2_ERR_INVALID;
     const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
@@ -558,6 +595,7 @@ int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_f
     const float* Xd = nullptr;
     KM2_TRY(device_view(X, (long long)n * d, &Xd, ws, s));
     Workspace w;
+    KM2_TRY(choose_form(o.precision, d, k, Xd, &w.form));
     KM2_TRY(alloc_workspace(w, ws, n, k, d, max_iter, s));
     bool lab_dev = is_device_ptr(labels_out) && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
     int* labels = lab_dev ? labels_out : nullptr;
@@ -565,7 +603,7 @@ int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_f
 
     kmeans2_result rr;
     std::memset(&rr, 0, sizeof(rr));
-    rr.precision_used = KMEANS2_PRECISION_FP32;
+    rr.precision_used = w.form;
     rr.subset_size = m;
     StageState fs;
     std::memset(&fs, 0, sizeof(fs));

@@ -78,6 +78,12 @@ int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* 
 int launch_recheck(const float* X, int d, const Centers& c, int* labels, const int* list,
                    StageState* st, const Accum& acc, cudaStream_t s, int sm_count);
 
+// assign_tc32.cu: tensor-core (3xTF32) form for FP32 data, d in {4, 8, 16, 32}, k <= 256
+int assign_tc32_supported(int d, int k, const float* X);
+int launch_assign_tc32(const float* X, long long n, int d, const Centers& c, int* labels,
+                       StageState* st, const Accum& acc, int* list, cudaStream_t s,
+                       int sm_count);
+
 // assign_fp32.cu
 int assign_fp32_supported(int d, int k);
 int launch_assign_fp32(const float* X, long long n, int d, const Centers& c, int* labels,

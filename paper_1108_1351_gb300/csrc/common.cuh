@@ -49,6 +49,8 @@ struct StageState {
 };
 
 constexpr int kErrNonFinite = 1;
+constexpr int kErrRange = 2;       // max|x| >= 2^50
+constexpr int kErrTimeout = 3;     // a bounded device-side wait gave up
 
 // Accumulator arrays of one stage (device, zeroed by the host before a full pass).
 struct Accum {

@@ -17,8 +17,6 @@ namespace km2 {
 
 namespace {
 
-constexpr int kErrRange = 2;   // max|x| >= 2^50: FP32 squares could overflow
-
 __device__ __forceinline__ unsigned int abs_bits(float v)
 {
     return __float_as_uint(v) & 0x7fffffffu;   // NaN keeps a payload above +inf
@@ -261,8 +259,12 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Accum acc, Centers c, St
     }
 }
 
-// One warp per listed point: exact FP64 distances in the oracle's form
-// (sum_t fma(x_t - c_t, x_t - c_t, acc), t ascending), lowest index on ties.
+// One warp per listed point.  Pass 1: FP32 D_j = ||c_j||^2 - 2 x.c_j for every
+// center on the CUDA cores (the FMA chain whose error tie_kappa bounds) and
+// their minimum b1.  Pass 2: every center with D_j <= b1 + tie_kappa (2 C2 + X2)
+// -- a set that provably holds the FP64 argmin -- is evaluated exactly in the
+// oracle's form (sum_t fma(x_t - c_t, x_t - c_t, acc), t ascending) and the
+// smallest wins, lowest index on ties.
 __global__ void recheck_kernel(const float* __restrict__ X, int d, Centers c,
                                int* __restrict__ labels, const int* __restrict__ list,
                                StageState* st, Accum acc)
@@ -271,6 +273,8 @@ __global__ void recheck_kernel(const float* __restrict__ X, int d, Centers c,
     const int count = st->recheck_count;
     const int mode = st->mode;
     const float scaleF = st->scaleF;
+    const float c2x2 = 2.0f * st->cmax2;
+    const float kap = tie_kappa(d);
     const int k = c.k;
     int lane = threadIdx.x & 31;
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -278,16 +282,33 @@ __global__ void recheck_kernel(const float* __restrict__ X, int d, Centers c,
     for (long long w = gw; w < count; w += nw) {
         int i = list[w];
         const float* x = X + (long long)i * d;
+        float x2 = 0.0f;
+        for (int t = lane; t < d; t += 32) { float v = __ldg(x + t); x2 = fmaf(v, v, x2); }
+        for (int o = 16; o; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+        float b1 = INFINITY;
+        for (int j = lane; j < k; j += 32) {
+            const float* cj = c.c32 + (long long)j * d;
+            float a = c.cnorm[j];
+            for (int t = 0; t < d; ++t) a = fmaf(__ldg(x + t), -2.0f * cj[t], a);
+            b1 = fminf(b1, a);
+        }
+        for (int o = 16; o; o >>= 1) b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+        const float lim = b1 + kap * (c2x2 + x2) * 1.0009765625f;
         double best = DBL_MAX;
         int bj = INT_MAX;
         for (int j = lane; j < k; j += 32) {
-            const double* cj = c.c64 + (long long)j * d;
-            double a2 = 0.0;
-            for (int t = 0; t < d; ++t) {
-                double a = (double)__ldg(x + t) - cj[t];
-                a2 = fma(a, a, a2);
+            const float* cj = c.c32 + (long long)j * d;
+            float a = c.cnorm[j];
+            for (int t = 0; t < d; ++t) a = fmaf(__ldg(x + t), -2.0f * cj[t], a);
+            if (a <= lim) {
+                const double* cj64 = c.c64 + (long long)j * d;
+                double a2 = 0.0;
+                for (int t = 0; t < d; ++t) {
+                    double e = (double)__ldg(x + t) - cj64[t];
+                    a2 = fma(e, e, a2);
+                }
+                if (a2 < best) { best = a2; bj = j; }
             }
-            if (a2 < best) { best = a2; bj = j; }
         }
         for (int o = 16; o; o >>= 1) {
             double ob = __shfl_xor_sync(0xffffffffu, best, o);

@@ -70,6 +70,42 @@ def test_step_matches_oracle(n, d, k):
     assert em == oem
 
 
+TC_SHAPES = [(70001, 8, 32), (2_000_003, 8, 32), (50000, 4, 7), (300_001, 16, 100),
+             (120_000, 32, 256), (33, 8, 1), (1000, 8, 256)]
+
+
+@pytest.mark.parametrize("form", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("n,d,k", TC_SHAPES)
+def test_step_each_form_matches_oracle(n, d, k, form):
+    """Both distance-kernel forms (CUDA-core FP32 and tensor-core 3xTF32)."""
+    X = _mixture(n, d, k, seed=3 * n + d + k)
+    C = _centers_from(X, k, seed=d + 1, jitter=0.3)
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision=form)
+    ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
+    assert np.array_equal(to_np(lab), olab)
+    assert_centers_close(to_np(cn), ocn, X)
+    assert_J_close(J, oJ, X)
+    assert em == oem
+
+
+@pytest.mark.parametrize("form", ["fp32", "tf32x3"])
+def test_fit_each_form_matches_oracle(form):
+    X = to_np(synth.aniso_gaussian_noise(1_000_000, 8, 32, seed=23))
+    Xd = torch.as_tensor(X, device=DEV)
+    r = km.fit(Xd, 32, 0.02, 4, 1e-5, 30, precision=form, trajectories=True)
+    o = oracle.fit(X, 32, 0.02, 4, 1e-5, 30, nthreads=NT)
+    assert r.precision_used == form
+    _assert_fit_equal(r, o, X)
+
+
+def test_tf32x3_rejects_unsupported_shape():
+    X = torch.zeros((100, 5), dtype=torch.float32, device=DEV)
+    with pytest.raises(km.KMeans2Error) as e:
+        km.step(X, torch.zeros((3, 5), dtype=torch.float64, device=DEV), precision="tf32x3")
+    assert e.value.status == -7
+
+
 def test_step_exact_ties_duplicates_and_empty_cluster():
     rng = np.random.default_rng(5)
     base = rng.normal(size=(50, 4)).astype(np.float32)
