@@ -50,7 +50,7 @@ def test_status_strings_and_version(lib):
 def test_default_options(lib):
     o = binding.Options()
     lib.kmeans2_default_options(ctypes.byref(o))
-    assert o.precision == 0 and o.use_graph == 1 and o.init_centers is None and o.stream is None
+    assert o.precision == 2 and o.use_graph == 1 and o.init_centers is None and o.stream is None
 
 
 def test_invalid_arguments_rejected_before_device_work(lib):
