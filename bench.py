@@ -220,7 +220,8 @@ def run_ours(args, cfg):
 
     def one(profile=None):
         return km.fit(X, k, cfg["f"], cfg["seed"] + rank, cfg["tol"], cfg["max_iter"],
-                      centers_out=centers, labels_out=labels, stream=stream, profile=profile)
+                      centers_out=centers, labels_out=labels, stream=stream, profile=profile,
+                      precision=args.precision)
 
     for _ in range(args.warmup):
         one()
@@ -266,7 +267,7 @@ def run_ours(args, cfg):
         del X
         torch.cuda.empty_cache()
         km.fit(Xh, k, cfg["f"], cfg["seed"] + rank, cfg["tol"], cfg["max_iter"], centers_out=ch,
-               labels_out=lh, stream=stream)
+               labels_out=lh, stream=stream, precision=args.precision)
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -274,7 +275,7 @@ def run_ours(args, cfg):
         e_evals = 0
         for _ in range(args.e2e_steps):
             r = km.fit(Xh, k, cfg["f"], cfg["seed"] + rank, cfg["tol"], cfg["max_iter"],
-                       centers_out=ch, labels_out=lh, stream=stream)
+                       centers_out=ch, labels_out=lh, stream=stream, precision=args.precision)
             e_evals += r.distance_evals
         torch.cuda.synchronize()
         te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
@@ -348,6 +349,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
+                    help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":

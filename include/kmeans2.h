@@ -76,8 +76,11 @@ extern "C" {
    ties are re-decided in FP64); they differ in speed and in how many points
    need that recheck. */
 #define KMEANS2_PRECISION_FP32 0      /* FP32 FMA chains on the CUDA cores (plain form) */
-#define KMEANS2_PRECISION_BF16 1      /* BF16 tensor-core cross term (not in this build) */
-#define KMEANS2_PRECISION_AUTO 2      /* fastest form measured for the shape (default) */
+#define KMEANS2_PRECISION_BF16 1      /* cross term on the tensor cores in BF16 (operands
+                                         split in two BF16 parts, three products, FP32
+                                         accumulation); d a multiple of 16 in [16, 128] */
+#define KMEANS2_PRECISION_AUTO 2      /* fastest form measured for the shape (default):
+                                         BF16 for d in {64, 80, ..., 128}, else FP32 */
 #define KMEANS2_PRECISION_TF32X3 3    /* cross term on the tensor cores as three TF32
                                          products of the exact hi/lo split of the FP32
                                          operands; d in {4, 8, 16, 32}, k <= 256 */
@@ -128,7 +131,7 @@ typedef struct kmeans2_result {
     int32_t converged_fast;     /* 1 if the fast stage met its tolerance */
     int32_t converged_slow;     /* 1 if the slow stage met tol */
     int32_t empty_clusters;     /* clusters left without points in the last iteration */
-    int32_t precision_used;     /* the form that ran: KMEANS2_PRECISION_FP32 or _TF32X3 */
+    int32_t precision_used;     /* the form that ran: KMEANS2_PRECISION_FP32, _BF16 or _TF32X3 */
     int64_t subset_size;        /* m = |S_s| */
     int64_t rechecked_points;   /* points re-evaluated in FP64, summed over iterations */
     int64_t distance_evals;     /* K Q_f m + K Q_s n (Section 3 cost model) */

@@ -8,6 +8,7 @@
 // loop control).  With use_graph the iteration body is captured once into the
 // body of a CUDA-graph WHILE node whose condition finalize sets on the device,
 // so a whole stage is one graph launch with no host round trip per iteration.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -133,6 +134,11 @@ struct Workspace {
     double* traj_J = nullptr;      // max_iter
     double* traj_shift = nullptr;  // max_iter
     int max_iter = 0;
+    DeviceScratch* ws = nullptr;   // the call's scratch (per-stage buffers)
+    // BF16 form: the stage's points as BF16 tiles, their ||x||^2, the centers' chunks
+    unsigned char* xt = nullptr;
+    float* xn2 = nullptr;
+    unsigned char* cb = nullptr;
 };
 
 int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, int d,
@@ -143,11 +149,13 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     w.c.kpad = (k + 127) / 128 * 128;
     w.c.dpad = (d + 7) / 8 * 8;
     w.max_iter = max_iter;
+    w.ws = &ws;
     size_t kd = (size_t)k * d;
     KM2_TRY(ws.alloc((void**)&w.c.c64, kd * sizeof(double), s));
     KM2_TRY(ws.alloc((void**)&w.c.c32, kd * sizeof(float), s));
     KM2_TRY(ws.alloc((void**)&w.c.c32t, (size_t)w.c.dpad * w.c.kpad * sizeof(float), s));
-    KM2_TRY(ws.alloc((void**)&w.c.cnorm, (size_t)w.c.kpad * sizeof(float), s));
+    const long long cn_len = std::max((long long)w.c.kpad, (long long)(k + 255) / 256 * 256);
+    KM2_TRY(ws.alloc((void**)&w.c.cnorm, (size_t)cn_len * sizeof(float), s));
     KM2_TRY(ws.alloc((void**)&w.acc.s_lo, kd * 8, s));
     KM2_TRY(ws.alloc((void**)&w.acc.s_hi, kd * 8, s));
     KM2_TRY(ws.alloc((void**)&w.acc.cnt, (size_t)k * 8, s));
@@ -157,8 +165,20 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     KM2_TRY(ws.alloc((void**)&w.traj_J, (size_t)max_iter * sizeof(double), s));
     KM2_TRY(ws.alloc((void**)&w.traj_shift, (size_t)max_iter * sizeof(double), s));
     KM2_CUDA(cudaMemsetAsync(w.c.c32t, 0, (size_t)w.c.dpad * w.c.kpad * sizeof(float), s));
-    KM2_TRY(fill_f32(w.c.cnorm, w.c.kpad, INFINITY, s));
+    KM2_TRY(fill_f32(w.c.cnorm, cn_len, INFINITY, s));
+    if (w.form == KMEANS2_PRECISION_BF16)
+        KM2_TRY(ws.alloc((void**)&w.cb, bf16_cb_bytes(d, k), s));
     return KMEANS2_OK;
+}
+
+// BF16 form: per-stage copy of the stage's points as BF16 tiles + ||x||^2.
+int prepare_stage_points(const float* X, long long n, int d, Workspace& w, DeviceScratch& ws,
+                         cudaStream_t s)
+{
+    if (w.form != KMEANS2_PRECISION_BF16) return KMEANS2_OK;
+    KM2_TRY(ws.alloc((void**)&w.xt, bf16_xt_bytes(n, d), s));
+    KM2_TRY(ws.alloc((void**)&w.xn2, (size_t)n * sizeof(float), s));
+    return launch_convert_x_bf16(X, n, d, w.xt, w.xn2, s, ws.sm_count);
 }
 
 // The fused distance kernel of the chosen form.
@@ -167,6 +187,9 @@ int launch_assign(const float* X, long long n, int d, Workspace& w, int* labels,
 {
     if (w.form == KMEANS2_PRECISION_TF32X3)
         return launch_assign_tc32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
+    if (w.form == KMEANS2_PRECISION_BF16)
+        return launch_assign_bf16(X, w.xt, w.xn2, w.cb, n, d, w.c, labels, w.st, w.acc, w.list, s,
+                                  sm_count);
     return launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
 }
 
@@ -174,8 +197,17 @@ int launch_assign(const float* X, long long n, int d, Workspace& w, int* labels,
 int choose_form(int requested, int d, int k, const float* X, int* form)
 {
     const bool tc = assign_tc32_supported(d, k, X) != 0;
+    const bool bf = assign_bf16_supported(d, k, X) != 0;
     switch (requested) {
         case KMEANS2_PRECISION_FP32: *form = KMEANS2_PRECISION_FP32; return KMEANS2_OK;
+        case KMEANS2_PRECISION_BF16:
+            if (!bf) {
+                set_last_error_text("the BF16 tensor-core form needs d a multiple of 16 in "
+                                    "[16, 128] and 16-byte aligned X");
+                return KMEANS2_ERR_UNSUPPORTED;
+            }
+            *form = KMEANS2_PRECISION_BF16;
+            return KMEANS2_OK;
         case KMEANS2_PRECISION_TF32X3:
             if (!tc) {
                 set_last_error_text("the 3xTF32 tensor-core form needs d in {4, 8, 16, 32}, "
@@ -185,9 +217,10 @@ int choose_form(int requested, int d, int k, const float* X, int* form)
             *form = KMEANS2_PRECISION_TF32X3;
             return KMEANS2_OK;
         case KMEANS2_PRECISION_AUTO:
-            // For FP32 data with d <= 32 the CUDA-core form is as fast per launch and
-            // flags far fewer near ties than the 3xTF32 tensor-core form (measured).
-            *form = KMEANS2_PRECISION_FP32;
+            // For d <= 32 the CUDA-core form is as fast per launch as the tensor-core
+            // forms and flags far fewer near ties (measured); from d = 64 on the
+            // d FFMAs per distance dominate and the BF16 tensor-core form wins.
+            *form = (bf && d >= 64) ? KMEANS2_PRECISION_BF16 : KMEANS2_PRECISION_FP32;
             return KMEANS2_OK;
         default:
             set_last_error_text("precision form not available in this build");
@@ -323,6 +356,7 @@ int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, dou
     KM2_CUDA(cudaMemsetAsync(w.acc.cnt, 0, (size_t)w.c.k * 8, s));
     KM2_TRY(launch_center_prep(w.c, w.st, s));
     KM2_TRY(launch_stage_init(w.st, d, tol, max_iter, s));
+    KM2_TRY(prepare_stage_points(X, n, d, w, *w.ws, s));
     if (use_graph && !prof)
         KM2_TRY(run_loop_graph(X, n, d, w, labels, s, sm_count));
     else

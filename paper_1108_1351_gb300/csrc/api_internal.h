@@ -84,6 +84,17 @@ int launch_assign_tc32(const float* X, long long n, int d, const Centers& c, int
                        StageState* st, const Accum& acc, int* list, cudaStream_t s,
                        int sm_count);
 
+// assign_bf16.cu: tensor-core split-BF16 form, d a multiple of 16 in [16, 128]
+int assign_bf16_supported(int d, int k, const float* X);
+size_t bf16_xt_bytes(long long n, int d);
+size_t bf16_cb_bytes(int d, int k);
+int launch_convert_x_bf16(const float* X, long long n, int d, unsigned char* Xt, float* xn2,
+                          cudaStream_t s, int sm_count);
+int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2,
+                       unsigned char* Cb, long long n, int d, const Centers& c, int* labels,
+                       StageState* st, const Accum& acc, int* list, cudaStream_t s,
+                       int sm_count);
+
 // assign_fp32.cu
 int assign_fp32_supported(int d, int k);
 int launch_assign_fp32(const float* X, long long n, int d, const Centers& c, int* labels,

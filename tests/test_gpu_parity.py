@@ -99,6 +99,34 @@ def test_fit_each_form_matches_oracle(form):
     _assert_fit_equal(r, o, X)
 
 
+BF16_SHAPES = [(20000, 16, 40), (50001, 64, 300), (30000, 128, 1024), (100_000, 128, 64),
+               (10000, 112, 100), (5000, 32, 5), (1_000_001, 64, 32), (300, 128, 1),
+               (200_003, 96, 777)]
+
+
+@pytest.mark.parametrize("n,d,k", BF16_SHAPES)
+def test_step_bf16_form_matches_oracle(n, d, k):
+    """BF16 tensor-core cross term + FP64 recheck: labels still bit-exact."""
+    X = _mixture(n, d, k, seed=5 * n + d + k, spread=3.0)
+    C = _centers_from(X, k, seed=d + 2, jitter=0.3)
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision="bf16")
+    ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
+    assert np.array_equal(to_np(lab), olab)
+    assert_centers_close(to_np(cn), ocn, X)
+    assert_J_close(J, oJ, X)
+    assert em == oem
+
+
+def test_fit_bf16_vmf_matches_oracle():
+    X = to_np(synth.vmf_mixture(60000, 128, 256, seed=7))
+    Xd = torch.as_tensor(X, device=DEV)
+    r = km.fit(Xd, 256, 0.05, 3, 1e-6, 15, precision="bf16", trajectories=True)
+    o = oracle.fit(X, 256, 0.05, 3, 1e-6, 15, nthreads=NT)
+    assert r.precision_used == "bf16"
+    _assert_fit_equal(r, o, X)
+
+
 def test_tf32x3_rejects_unsupported_shape():
     X = torch.zeros((100, 5), dtype=torch.float32, device=DEV)
     with pytest.raises(km.KMeans2Error) as e:
