@@ -166,6 +166,44 @@ KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, dou
                 uint64_t seed, double tol, int32_t max_iter, double* centers_out,
                 int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt);
 
+/* One independent clustering problem of a batch (kmeans2_fit_batched). */
+typedef struct kmeans2_job {
+    const float* X;             /* n*d FP32 points, DEVICE memory, 16-byte aligned */
+    int64_t n;
+    int32_t d;                  /* 1 <= d <= 64 */
+    int32_t k;                  /* 1 <= k <= min(n, 256) */
+    double subset_fraction;     /* per, in (0, 1] */
+    uint64_t seed;
+    double tol;                 /* slow-stage tolerance; options->tol_fast, when > 0,
+                                   is every job's fast-stage tolerance */
+    int32_t max_iter;           /* per stage, >= 1 */
+    int32_t reserved;
+    double* centers_out;        /* k*d FP64 (host or device) */
+    int32_t* labels_out;        /* n int32 (host or device) */
+} kmeans2_job;
+
+/*
+ * kmeans2_fit_batched -- the two-stage method of kmeans2_fit applied to `count`
+ * independent jobs at once (batched form).  All jobs advance together: every
+ * phase of an iteration (distances, recheck, update) is one launch over all
+ * jobs still running, each job carries its own stage (fast, slow, done) and
+ * convergence flag on the device, and the whole loop runs as one CUDA graph
+ * with a device-side while condition.  Work is cut into items of a number of
+ * 1024-point tiles chosen by a built-in autotuner (timed on the first call for
+ * each dimension class, then cached for the process).  Each job's result equals
+ * kmeans2_fit on that job alone.
+ *
+ *  jobs      count descriptors (host array).
+ *  results   count results (host array), may be NULL.
+ *  opt       may be NULL; precision must be FP32 or AUTO (the batched kernels
+ *            are the CUDA-core FP32 form).
+ * Errors: KMEANS2_ERR_INVALID (a job out of range; nothing is run),
+ * KMEANS2_ERR_NONFINITE (some job holds NaN / inf: the other jobs complete),
+ * KMEANS2_ERR_NOMEM, KMEANS2_ERR_CUDA.
+ */
+KMEANS2_API int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs,
+                                    kmeans2_result* results, const kmeans2_options* opt);
+
 /*
  * kmeans_step -- one Lloyd iteration (Section 4.1; the loop body of the
  * Algorithm) from given centers.

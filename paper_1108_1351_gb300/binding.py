@@ -61,6 +61,22 @@ class Options(ctypes.Structure):
     ]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [
+        ("X", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("subset_fraction", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("centers_out", ctypes.c_void_p),
+        ("labels_out", ctypes.c_void_p),
+    ]
+
+
 class Result(ctypes.Structure):
     _fields_ = [
         ("J", ctypes.c_double),
@@ -98,6 +114,9 @@ def load():
                                     ctypes.POINTER(Result), ctypes.POINTER(Options)]
         lib.kmeans_step.restype = ctypes.c_int
         lib.kmeans_step.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, ctypes.POINTER(Options)]
+        lib.kmeans2_fit_batched.restype = ctypes.c_int
+        lib.kmeans2_fit_batched.argtypes = [i32, ctypes.POINTER(Job), ctypes.POINTER(Result),
+                                            ctypes.POINTER(Options)]
         lib.kmeans_step_noalloc.restype = ctypes.c_int
         lib.kmeans_step_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P]
         lib.kmeans2_subset_size.restype = i64
@@ -252,6 +271,56 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                      shift_slow=res.shift_slow, seconds=res.seconds,
                      precision_used={0: "fp32", 1: "bf16", 3: "tf32x3"}.get(res.precision_used, "?"),
                      traj=traj)
+
+
+def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: float = 0.0,
+                stream=None, raise_on_error: bool = True):
+    """Batched two-stage fits (kmeans2_fit_batched) of independent problems.
+
+    Xs: list of 2-D float32 CUDA tensors; ks, seeds: per-job lists; the other
+    arguments are scalars or per-job lists.  Returns a list of FitResult (with
+    device centers and labels) and the status code."""
+    lib = load()
+    cnt = len(Xs)
+
+    def per_job(v):
+        return list(v) if isinstance(v, (list, tuple)) else [v] * cnt
+
+    fs, tols, its = per_job(subset_fraction), per_job(tol), per_job(max_iter)
+    jobs = (Job * cnt)()
+    outs = []
+    for j, X in enumerate(Xs):
+        if not (_is_torch(X) and X.is_cuda):
+            raise TypeError("fit_batched needs CUDA tensors")
+        X = _as_points(X)
+        n, d = X.shape
+        cen = _empty(X, (ks[j], d), "f64")
+        lab = _empty(X, (n,), "i32")
+        outs.append((X, cen, lab))
+        jobs[j] = Job(X=X.data_ptr(), n=n, d=d, k=int(ks[j]), subset_fraction=float(fs[j]),
+                      seed=int(seeds[j]) & (2**64 - 1), tol=float(tols[j]), max_iter=int(its[j]),
+                      reserved=0, centers_out=cen.data_ptr(), labels_out=lab.data_ptr())
+    res = (Result * cnt)()
+    opt = Options()
+    lib.kmeans2_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION["fp32"]
+    opt.tol_fast = tol_fast
+    opt.stream = _stream_of(Xs[0], stream)
+    with _device_of(Xs[0]):
+        rc = lib.kmeans2_fit_batched(cnt, jobs, res, ctypes.byref(opt))
+    if rc != 0 and raise_on_error:
+        raise KMeans2Error(rc, "kmeans2_fit_batched")
+    out = []
+    for j in range(cnt):
+        r = res[j]
+        out.append(FitResult(centers=outs[j][1], labels=outs[j][2], J=r.J, iters_fast=r.iters_fast,
+                             iters_slow=r.iters_slow, converged_fast=bool(r.converged_fast),
+                             converged_slow=bool(r.converged_slow),
+                             empty_clusters=r.empty_clusters, subset_size=r.subset_size,
+                             rechecked_points=r.rechecked_points,
+                             distance_evals=r.distance_evals, shift_fast=r.shift_fast,
+                             shift_slow=r.shift_slow, seconds=r.seconds, precision_used="fp32"))
+    return out, rc
 
 
 def step(X, centers, *, precision: str = "auto", stream=None, centers_out=None, labels_out=None,

@@ -39,6 +39,16 @@ void set_last_error_text(const char* text)
 
 const char* last_error() { return g_last_error; }
 
+// A private blocking stream per thread and device, used when the caller passes
+// the legacy default stream (which cannot be captured into a graph).
+cudaStream_t private_stream(int device)
+{
+    static thread_local cudaStream_t streams[64] = {};
+    if (device < 0 || device >= 64) return nullptr;
+    if (!streams[device]) cudaStreamCreate(&streams[device]);
+    return streams[device];
+}
+
 DeviceScratch::DeviceScratch(cudaStream_t s) : stream(s)
 {
     cudaGetDevice(&device);
@@ -112,16 +122,6 @@ bool is_device_ptr(const void* p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// A private blocking stream per thread and device, used when the caller passes
-// the legacy default stream (which cannot be captured into a graph).
-cudaStream_t private_stream(int device)
-{
-    static thread_local cudaStream_t streams[64] = {};
-    if (device < 0 || device >= 64) return nullptr;
-    if (!streams[device]) cudaStreamCreate(&streams[device]);
-    return streams[device];
 }
 
 struct Workspace {

@@ -35,6 +35,10 @@ void set_last_error_text(const char* text);
         if (km2_rc_ != KMEANS2_OK) return km2_rc_; \
     } while (0)
 
+// A private blocking stream of the calling thread for `device` (capturable,
+// unlike the legacy default stream).
+cudaStream_t private_stream(int device);
+
 // Stream-ordered scratch: every allocation is released (cudaFreeAsync on the
 // same stream) when the object goes out of scope.
 struct DeviceScratch {

@@ -1,0 +1,798 @@
+// batched.cu -- the batched form: many independent two-stage fits advancing
+// together.  Every job keeps its own stage (fast, slow, done), iteration count
+// and convergence flag in a device descriptor; one iteration of the whole
+// batch is
+//   batch_assign<DC>  one launch per dimension class over a list of work items
+//                     (job, first 1024-point tile, tile count); items of jobs
+//                     that are done, or beyond the current stage's points, are
+//                     skipped
+//   batch_recheck     one CTA per job: FP64 re-decision of its near ties
+//   batch_finalize    one CTA per job: means, movement, J, stop test, and the
+//                     switch from the fast to the slow stage (Section 2)
+//   batch_control     sets the graph's while condition: any job still running
+// and the loop is captured once as a CUDA graph with a device-side WHILE node.
+// The arithmetic of every step is the single-fit arithmetic (stage_dev.cuh,
+// the same packed-key top-2, bound and exact sums), so each job's result equals
+// kmeans2_fit on that job alone.
+//
+// Work items hold a number of tiles chosen per dimension class by an
+// autotuner: on the first call for a class it times the real first pass of
+// the batch for a few item sizes (resetting the sums between trials) and keeps
+// the fastest for the rest of the process.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "api_internal.h"
+#include "stage_dev.cuh"
+
+namespace km2 {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 1024;          // points per tile of a work item
+constexpr int kMaxK = 256;
+constexpr int kMaxD = 64;
+constexpr int kMaxTilesPerItem = kFlushPoints / kTile;   // keeps per-item partials < 2^62
+
+struct BatchInst {
+    const float* X;          // n x d (caller's, device)
+    float* Xs;               // m x d gathered subset
+    int* lab_fast;           // m
+    int* lab_slow;           // n
+    int* list;               // n (recheck list)
+    long long* subset;       // m
+    long long* pos;          // k
+    long long* seltmp;       // k
+    double* clus;            // 4 k
+    Centers c;
+    Accum acc;
+    StageState st;
+    long long n, m;
+    unsigned long long seed;
+    double tol_fast, tol_slow;
+    int d, k, max_iter;
+    int stage;               // 0 fast, 1 slow, 2 done
+    unsigned int maxabs_x;   // max |x| over X (scale of the slow stage)
+    int iters_fast, conv_fast, error;
+    double shift_fast;
+    long long rechecked;
+};
+
+struct WorkItem {
+    int inst;
+    int tile0;
+    int ntile;
+};
+
+__device__ __forceinline__ unsigned int abs_bits(float v)
+{
+    return __float_as_uint(v) & 0x7fffffffu;
+}
+
+// ---------------------------------------------------------------- sampling
+
+// Block-level exact radix select: ascending positions (relative to `off`) of
+// the `want` smallest keys splitmix64_at(seed, off + i), i in [0, count).
+__device__ void select_block(unsigned long long seed, unsigned long long off, long long count,
+                             long long want, long long* out)
+{
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned long long prefix;
+    __shared__ long long need;
+    __shared__ long long scan[kThreads + 1];
+    if (threadIdx.x == 0) { prefix = 0; need = want; }
+    __syncthreads();
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const unsigned long long pf = prefix;
+        for (long long i = threadIdx.x; i < count; i += blockDim.x) {
+            const unsigned long long key = splitmix64_at(seed, off + (unsigned long long)i);
+            const bool match = pass == 0 || (key >> (shift + 8)) == (pf >> (shift + 8));
+            if (match) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long acc = 0, nd = need;
+            for (int b = 0; b < 256; ++b) {
+                if (nd <= acc + (long long)hist[b]) {
+                    prefix = pf | ((unsigned long long)b << shift);
+                    need = nd - acc;
+                    break;
+                }
+                acc += hist[b];
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long T = prefix;     // the want-th smallest key (keys are distinct)
+    const long long per = (count + blockDim.x - 1) / blockDim.x;
+    const long long i0 = min(count, (long long)threadIdx.x * per), i1 = min(count, i0 + per);
+    long long c = 0;
+    for (long long i = i0; i < i1; ++i) c += splitmix64_at(seed, off + (unsigned long long)i) <= T;
+    scan[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) { const long long v = scan[t]; scan[t] = a; a += v; }
+    }
+    __syncthreads();
+    long long o = scan[threadIdx.x];
+    for (long long i = i0; i < i1; ++i)
+        if (splitmix64_at(seed, off + (unsigned long long)i) <= T) out[o++] = i;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) batch_sample_kernel(BatchInst* insts)
+{
+    BatchInst* I = insts + blockIdx.x;
+    select_block(I->seed, 0ull, I->n, I->m, I->subset);
+    select_block(I->seed, (unsigned long long)I->n, I->m, I->k, I->seltmp);
+    // initial centers: the k selected positions in increasing key order
+    for (int a = threadIdx.x; a < I->k; a += blockDim.x) {
+        const unsigned long long ka = splitmix64_at(I->seed, (unsigned long long)(I->n + I->seltmp[a]));
+        int rank = 0;
+        for (int b = 0; b < I->k; ++b)
+            rank += splitmix64_at(I->seed, (unsigned long long)(I->n + I->seltmp[b])) < ka;
+        I->pos[rank] = I->seltmp[a];
+    }
+}
+
+// Gather X_s, its max |x|, the initial centers, and max |x| over X.
+__global__ void __launch_bounds__(kThreads) batch_gather_kernel(BatchInst* insts)
+{
+    __shared__ unsigned int mx_s, mx_x;
+    BatchInst* I = insts + blockIdx.x;
+    const int d = I->d;
+    if (threadIdx.x == 0) { mx_s = 0; mx_x = 0; }
+    __syncthreads();
+    unsigned int a = 0;
+    const long long total = I->m * d;
+    for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+        const long long p = e / d;
+        const int t = (int)(e - p * d);
+        const float v = I->X[I->subset[p] * d + t];
+        I->Xs[e] = v;
+        a = max(a, abs_bits(v));
+    }
+    atomicMax(&mx_s, a);
+    unsigned int b = 0;
+    const long long all = I->n * d;
+    for (long long e = threadIdx.x; e < all; e += blockDim.x) b = max(b, abs_bits(__ldg(I->X + e)));
+    atomicMax(&mx_x, b);
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)I->k * d; e += blockDim.x) {
+        const long long j = e / d;
+        const int t = (int)(e - j * d);
+        I->c.c64[e] = (double)I->Xs[I->pos[j] * d + t];
+    }
+    if (threadIdx.x == 0) {
+        I->st.maxabs_bits = mx_s;
+        I->maxabs_x = mx_x;
+    }
+}
+
+// Fast-stage start: scales, loop state, center copies, zero sums.
+__global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchInst* insts)
+{
+    __shared__ double red[kThreads];
+    BatchInst* I = insts + blockIdx.x;
+    if (threadIdx.x == 0) {
+        stage_init_dev(&I->st, I->d, I->tol_fast, I->max_iter);
+        I->stage = I->st.error ? 2 : 0;
+        I->error = I->st.error;
+        I->rechecked = 0;
+        I->iters_fast = 0;
+        I->conv_fast = 0;
+        I->shift_fast = 0.0;
+    }
+    __syncthreads();
+    center_prep_block(I->c, &I->st, red);
+    const long long kd = (long long)I->k * I->d;
+    for (long long e = threadIdx.x; e < kd; e += blockDim.x) { I->acc.s_lo[e] = 0; I->acc.s_hi[e] = 0; }
+    for (int j = threadIdx.x; j < I->k; j += blockDim.x) I->acc.cnt[j] = 0;
+}
+
+// Back to the state of a stage's first pass (used between autotuning trials).
+__global__ void __launch_bounds__(kThreads) batch_reset_kernel(BatchInst* insts)
+{
+    BatchInst* I = insts + blockIdx.x;
+    const long long kd = (long long)I->k * I->d;
+    for (long long e = threadIdx.x; e < kd; e += blockDim.x) { I->acc.s_lo[e] = 0; I->acc.s_hi[e] = 0; }
+    for (int j = threadIdx.x; j < I->k; j += blockDim.x) I->acc.cnt[j] = 0;
+    if (threadIdx.x == 0) {
+        I->st.q_lo = 0;
+        I->st.q_hi = 0;
+        I->st.recheck_count = 0;
+    }
+}
+
+// ---------------------------------------------------------------- assign
+
+template <int DC>
+struct BCfg {
+    static constexpr int P = DC <= 16 ? 4 : (DC <= 32 ? 2 : 1);   // points per thread
+    static constexpr int SUB = kThreads * P;                      // points per sub-tile
+    static constexpr int NSUB = kTile / SUB;
+    static constexpr bool SACC = DC <= 32;                        // per-CTA partial sums
+};
+
+template <int DC>
+constexpr size_t batch_smem()
+{
+    return (size_t)kMaxK * DC * 4 + (size_t)kMaxK * 4 +
+           (BCfg<DC>::SACC ? (size_t)kMaxK * DC * 8 + (size_t)kMaxK * 4 : 0);
+}
+
+__device__ __forceinline__ float pack_key(float v, unsigned j)
+{
+    return __uint_as_float((__float_as_uint(v) & ~31u) | j);
+}
+
+template <int DC>
+__global__ void __launch_bounds__(kThreads, 2)
+batch_assign(BatchInst* insts, const WorkItem* items, int nitems)
+{
+    using C = BCfg<DC>;
+    constexpr int P = C::P;
+    extern __shared__ __align__(16) float smem[];
+    float* sc = smem;                                         // kMaxK * DC: -2 c
+    float* ss = sc + kMaxK * DC;                              // kMaxK: ||c||^2
+    long long* sacc = reinterpret_cast<long long*>(ss + kMaxK);
+    int* scnt = reinterpret_cast<int*>(sacc + kMaxK * DC);
+    __shared__ unsigned long long sq;
+    const int tid = threadIdx.x;
+
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        BatchInst* I = insts + w.inst;
+        const int stage = I->stage;
+        if (stage >= 2) continue;
+        const long long npts = stage == 0 ? I->m : I->n;
+        const long long tiles = (npts + kTile - 1) / kTile;
+        if (w.tile0 >= tiles) continue;
+        const float* X = stage == 0 ? I->Xs : I->X;
+        int* labels = stage == 0 ? I->lab_fast : I->lab_slow;
+        StageState* st = &I->st;
+        const int d = I->d, k = I->k;
+        const int kc = (k + 31) & ~31;
+        const int mode = st->mode;
+        const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float thr_base = 2.0f * st->cmax2;
+        const float kappa = tie_kappa(d);
+
+        __syncthreads();   // the previous item is done with shared memory
+        for (int e = tid; e < kc * DC; e += kThreads) {
+            const int j = e / DC, t = e - j * DC;
+            sc[e] = (j < k && t < d) ? -2.0f * I->c.c32[(long long)j * d + t] : 0.0f;
+        }
+        for (int j = tid; j < kc; j += kThreads) ss[j] = j < k ? I->c.cnorm[j] : FLT_MAX;
+        if (C::SACC) {
+            for (int e = tid; e < k * DC; e += kThreads) sacc[e] = 0;
+            for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
+        }
+        if (tid == 0) sq = 0;
+        __syncthreads();
+
+        long long qloc = 0;
+        const long long t_end = min(tiles, (long long)w.tile0 + w.ntile);
+        for (long long tile = w.tile0; tile < t_end; ++tile) {
+            for (int sub = 0; sub < C::NSUB; ++sub) {
+                const long long base = tile * kTile + (long long)sub * C::SUB;
+                float x[P][DC];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const long long i = base + (long long)p * kThreads + tid;
+#pragma unroll
+                    for (int t = 0; t < DC; ++t) x[p][t] = (i < npts && t < d) ? __ldg(X + i * d + t) : 0.0f;
+                }
+                float B1[P], B2[P];
+                int BI[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) { B1[p] = INFINITY; B2[p] = INFINITY; BI[p] = 0; }
+                for (int ch = 0; ch < kc; ch += 32) {
+                    float b1[P], b2[P];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) { b1[p] = INFINITY; b2[p] = INFINITY; }
+#pragma unroll 2
+                    for (unsigned jj = 0; jj < 32; jj += 2) {
+                        const float* c0 = sc + (ch + jj) * DC;
+                        const float* c1 = c0 + DC;
+                        const float s0 = ss[ch + jj], s1 = ss[ch + jj + 1];
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            float d0 = s0, d1 = s1;
+#pragma unroll
+                            for (int t = 0; t < DC; ++t) {
+                                d0 = fmaf(x[p][t], c0[t], d0);
+                                d1 = fmaf(x[p][t], c1[t], d1);
+                            }
+                            const float k0 = pack_key(d0, jj), k1 = pack_key(d1, jj | 1u);
+                            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+                            b2[p] = fmin3(b2[p], hi, fmaxf(b1[p], lo));
+                            b1[p] = fminf(b1[p], lo);
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        if (b1[p] < B1[p]) {
+                            B2[p] = fminf(B1[p], b2[p]);
+                            B1[p] = b1[p];
+                            BI[p] = ch | (int)(__float_as_uint(b1[p]) & 31u);
+                        } else {
+                            B2[p] = fminf(B2[p], b1[p]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const long long i = base + (long long)p * kThreads + tid;
+                    const bool valid = i < npts;
+                    float xn2 = 0.f;
+#pragma unroll
+                    for (int t = 0; t < DC; ++t) xn2 = fmaf(x[p][t], x[p][t], xn2);
+                    const float thr = kappa * (thr_base + xn2) + kPackSlack * (fabsf(B1[p]) + fabsf(B2[p]));
+                    const bool flag = valid && (B2[p] - B1[p] <= thr);
+                    if (mode == kModeFull && valid) {
+#pragma unroll
+                        for (int t = 0; t < DC; ++t)
+                            if (t < d) qloc += sq_fixed(x[p][t], scaleG);
+                    }
+                    recheck_append(flag, (int)i, I->list, &st->recheck_count);
+                    if (valid && !flag) {
+                        const int lab = BI[p];
+                        const int old = (mode == kModeDelta) ? labels[i] : -1;
+                        if (lab != old) {
+#pragma unroll
+                            for (int t = 0; t < DC; ++t) {
+                                if (t >= d) break;
+                                const long long v = to_fixed(x[p][t], scaleF);
+                                if (C::SACC) {
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * DC + t),
+                                              (unsigned long long)v);
+                                    if (old >= 0)
+                                        atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * DC + t),
+                                                  (unsigned long long)(-v));
+                                } else {
+                                    split_add(I->acc.s_lo + (long long)lab * d + t,
+                                              I->acc.s_hi + (long long)lab * d + t, v);
+                                    if (old >= 0)
+                                        split_add(I->acc.s_lo + (long long)old * d + t,
+                                                  I->acc.s_hi + (long long)old * d + t, -v);
+                                }
+                            }
+                            if (C::SACC) {
+                                atomicAdd(scnt + lab, 1);
+                                if (old >= 0) atomicAdd(scnt + old, -1);
+                            } else {
+                                atomicAdd(I->acc.cnt + lab, 1ull);
+                                if (old >= 0) atomicAdd(I->acc.cnt + old, ~0ull);
+                            }
+                            labels[i] = lab;
+                        }
+                    }
+                }
+            }
+        }
+        if (qloc) atomicAdd(&sq, (unsigned long long)qloc);
+        __syncthreads();
+        if (C::SACC) {
+            for (int e = tid; e < k * DC; e += kThreads) {
+                const int j = e / DC, t = e - j * DC;
+                const long long v = sacc[e];
+                if (v && t < d)
+                    split_add(I->acc.s_lo + (long long)j * d + t, I->acc.s_hi + (long long)j * d + t, v);
+            }
+            for (int j = tid; j < k; j += kThreads)
+                if (scnt[j]) atomicAdd(I->acc.cnt + j, (unsigned long long)(long long)scnt[j]);
+        }
+        if (tid == 0 && sq) split_add(&st->q_lo, &st->q_hi, (long long)sq);
+    }
+}
+
+// ---------------------------------------------------------------- recheck, finalize, control
+
+__global__ void __launch_bounds__(kThreads) batch_recheck_kernel(BatchInst* insts)
+{
+    BatchInst* I = insts + blockIdx.x;
+    if (I->stage >= 2 || I->st.error) return;
+    const float* X = I->stage == 0 ? I->Xs : I->X;
+    int* labels = I->stage == 0 ? I->lab_fast : I->lab_slow;
+    recheck_warps(X, I->d, I->c, labels, I->list, &I->st, I->acc, threadIdx.x >> 5,
+                  blockDim.x >> 5);
+}
+
+__global__ void __launch_bounds__(kThreads) batch_finalize_kernel(BatchInst* insts, int* active)
+{
+    __shared__ FinalizeSmem sm;
+    __shared__ int switched;
+    BatchInst* I = insts + blockIdx.x;
+    const int stage = I->stage;
+    if (stage >= 2) return;
+    if (I->st.error) {
+        if (threadIdx.x == 0) { I->stage = 2; I->error = I->st.error; }
+        return;
+    }
+    finalize_block(I->acc, I->c, &I->st, nullptr, nullptr, I->clus, sm);
+    if (threadIdx.x == 0) {
+        switched = 0;
+        if (I->st.done) {
+            I->rechecked += I->st.rechecked_total;
+            if (stage == 0) {
+                // slow stage on S_n from the fast stage's final centers (Section 2)
+                I->iters_fast = I->st.iter;
+                I->conv_fast = I->st.converged;
+                I->shift_fast = I->st.shift;
+                I->st.maxabs_bits = I->maxabs_x;
+                stage_init_dev(&I->st, I->d, I->tol_slow, I->max_iter);
+                if (I->st.error) {
+                    I->stage = 2;
+                    I->error = I->st.error;
+                } else {
+                    I->stage = 1;
+                    switched = 1;
+                }
+            } else {
+                I->stage = 2;
+            }
+        }
+        if (I->stage < 2) atomicAdd(active, 1);
+    }
+    __syncthreads();
+    if (switched) {
+        const long long kd = (long long)I->k * I->d;
+        for (long long e = threadIdx.x; e < kd; e += blockDim.x) { I->acc.s_lo[e] = 0; I->acc.s_hi[e] = 0; }
+        for (int j = threadIdx.x; j < I->k; j += blockDim.x) I->acc.cnt[j] = 0;
+    }
+}
+
+__global__ void batch_control_kernel(int* active, int* iter, int cap, unsigned long long handle)
+{
+    const int a = *active;
+    *active = 0;
+    const int it = ++*iter;
+    cudaGraphSetConditional(handle, (a > 0 && it < cap) ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------- host
+
+int dclass(int d)
+{
+    if (d <= 2) return 2;
+    if (d <= 4) return 4;
+    if (d <= 8) return 8;
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    return 64;
+}
+
+template <int DC>
+int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, cudaStream_t s,
+                        int sm_count)
+{
+    static thread_local int configured_for = -1;
+    int dev = 0;
+    KM2_CUDA(cudaGetDevice(&dev));
+    const size_t sm = batch_smem<DC>();
+    if (configured_for != dev) {
+        KM2_CUDA(cudaFuncSetAttribute(batch_assign<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm));
+        configured_for = dev;
+    }
+    int per_sm = 0;
+    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_assign<DC>, kThreads, sm));
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)sm_count * per_sm;
+    if (grid > nitems) grid = nitems;
+    if (grid < 1) grid = 1;
+    ++g_launches;
+    batch_assign<DC><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_class(int dc, BatchInst* insts, const WorkItem* items, int nitems, cudaStream_t s,
+                 int sm_count)
+{
+    switch (dc) {
+        case 2: return launch_batch_assign<2>(insts, items, nitems, s, sm_count);
+        case 4: return launch_batch_assign<4>(insts, items, nitems, s, sm_count);
+        case 8: return launch_batch_assign<8>(insts, items, nitems, s, sm_count);
+        case 16: return launch_batch_assign<16>(insts, items, nitems, s, sm_count);
+        case 32: return launch_batch_assign<32>(insts, items, nitems, s, sm_count);
+        default: return launch_batch_assign<64>(insts, items, nitems, s, sm_count);
+    }
+}
+
+std::mutex g_tune_mu;
+std::map<int, int> g_tuned;          // dimension class -> tiles per work item
+
+struct ClassItems {
+    int dc = 0;
+    int tpi = 0;
+    std::vector<WorkItem> host;
+    WorkItem* dev = nullptr;
+    int count = 0;
+};
+
+void build_items(ClassItems& ci, const std::vector<int>& members, const std::vector<long long>& n,
+                 int tpi)
+{
+    ci.host.clear();
+    for (int j : members) {
+        const long long tiles = (n[j] + kTile - 1) / kTile;
+        for (long long t = 0; t < tiles; t += tpi)
+            ci.host.push_back(WorkItem{j, (int)t, tpi});
+    }
+    ci.count = (int)ci.host.size();
+    ci.tpi = tpi;
+}
+
+}  // namespace
+
+}  // namespace km2
+
+using namespace km2;
+
+extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmeans2_result* results,
+                                   const kmeans2_options* opt)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (count < 1 || !jobs) return KMEANS2_ERR_INVALID;
+    kmeans2_options o;
+    kmeans2_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != KMEANS2_PRECISION_FP32 && o.precision != KMEANS2_PRECISION_AUTO) {
+        set_last_error_text("the batched form runs the FP32 CUDA-core kernels only");
+        return KMEANS2_ERR_UNSUPPORTED;
+    }
+    for (int j = 0; j < count; ++j) {
+        const kmeans2_job& J = jobs[j];
+        if (!J.X || !J.centers_out || !J.labels_out || J.n < 1 || J.n >= (1ll << 31) || J.d < 1 ||
+            J.d > kMaxD || J.k < 1 || J.k > kMaxK || J.k > J.n ||
+            !(J.subset_fraction > 0.0 && J.subset_fraction <= 1.0) || !(J.tol >= 0.0) ||
+            J.max_iter < 1 || (reinterpret_cast<uintptr_t>(J.X) & 15) != 0) {
+            char msg[160];
+            std::snprintf(msg, sizeof(msg), "kmeans2_fit_batched: job %d is out of range", j);
+            set_last_error_text(msg);
+            return KMEANS2_ERR_INVALID;
+        }
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, J.X) != cudaSuccess ||
+            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            set_last_error_text("kmeans2_fit_batched: X must be device memory");
+            return KMEANS2_ERR_INVALID;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+    int dev = 0;
+    KM2_CUDA(cudaGetDevice(&dev));
+    if (!s) s = private_stream(dev);
+    const long long launches0 = g_launches;
+    int rc = KMEANS2_OK;
+    {
+        DeviceScratch ws(s);
+        // ---- per-job layout in one arena
+        auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+        std::vector<BatchInst> hi(count);
+        std::vector<size_t> offs(count);
+        std::vector<long long> nvec(count);
+        size_t total = 0;
+        int max_iter_all = 1;
+        for (int j = 0; j < count; ++j) {
+            const kmeans2_job& J = jobs[j];
+            const long long m = kmeans2_subset_size(J.n, J.k, J.subset_fraction);
+            const int kpad = (J.k + 127) / 128 * 128, dpad = (J.d + 7) / 8 * 8;
+            const size_t kd = (size_t)J.k * J.d;
+            offs[j] = total;
+            total += up(m * J.d * 4) + up(m * 4) + up(J.n * 4) + up(J.n * 4) + up(m * 8) +
+                     3 * up((size_t)J.k * 8) + up(4 * (size_t)J.k * 8) + up(kd * 8) + up(kd * 4) +
+                     up((size_t)dpad * kpad * 4) + up((size_t)kpad * 4) + 2 * up(kd * 8) +
+                     up((size_t)J.k * 8);
+            nvec[j] = J.n;
+            max_iter_all = std::max(max_iter_all, J.max_iter);
+        }
+        unsigned char* arena = nullptr;
+        BatchInst* dinst = nullptr;
+        int* counters = nullptr;
+        KM2_TRY(ws.alloc((void**)&arena, total, s));
+        KM2_TRY(ws.alloc((void**)&dinst, sizeof(BatchInst) * (size_t)count, s));
+        KM2_TRY(ws.alloc((void**)&counters, 2 * sizeof(int), s));
+        for (int j = 0; j < count; ++j) {
+            const kmeans2_job& J = jobs[j];
+            BatchInst& I = hi[j];
+            std::memset(&I, 0, sizeof(I));
+            const long long m = kmeans2_subset_size(J.n, J.k, J.subset_fraction);
+            const int kpad = (J.k + 127) / 128 * 128, dpad = (J.d + 7) / 8 * 8;
+            const size_t kd = (size_t)J.k * J.d;
+            unsigned char* p = arena + offs[j];
+            auto take = [&](size_t b) { unsigned char* q = p; p += up(b); return q; };
+            I.X = J.X;
+            I.Xs = (float*)take(m * J.d * 4);
+            I.lab_fast = (int*)take(m * 4);
+            I.lab_slow = (int*)take(J.n * 4);
+            I.list = (int*)take(J.n * 4);
+            I.subset = (long long*)take(m * 8);
+            I.pos = (long long*)take((size_t)J.k * 8);
+            I.seltmp = (long long*)take((size_t)J.k * 8);
+            take((size_t)J.k * 8);
+            I.clus = (double*)take(4 * (size_t)J.k * 8);
+            I.c.c64 = (double*)take(kd * 8);
+            I.c.c32 = (float*)take(kd * 4);
+            I.c.c32t = (float*)take((size_t)dpad * kpad * 4);
+            I.c.cnorm = (float*)take((size_t)kpad * 4);
+            I.c.k = J.k;
+            I.c.d = J.d;
+            I.c.kpad = kpad;
+            I.c.dpad = dpad;
+            I.acc.s_lo = (unsigned long long*)take(kd * 8);
+            I.acc.s_hi = (unsigned long long*)take(kd * 8);
+            I.acc.cnt = (unsigned long long*)take((size_t)J.k * 8);
+            I.n = J.n;
+            I.m = m;
+            I.seed = J.seed;
+            I.tol_slow = J.tol;
+            I.tol_fast = o.tol_fast > 0.0 ? o.tol_fast : J.tol;
+            I.d = J.d;
+            I.k = J.k;
+            I.max_iter = J.max_iter;
+        }
+        KM2_CUDA(cudaMemcpyAsync(dinst, hi.data(), sizeof(BatchInst) * (size_t)count,
+                                 cudaMemcpyHostToDevice, s));
+        KM2_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
+        g_launches += 3;
+        batch_sample_kernel<<<count, kThreads, 0, s>>>(dinst);
+        batch_gather_kernel<<<count, kThreads, 0, s>>>(dinst);
+        batch_prep_kernel<<<count, kThreads, 0, s>>>(dinst);
+        KM2_CUDA(cudaGetLastError());
+
+        // ---- work items per dimension class, item size from the autotuner
+        std::map<int, std::vector<int>> members;
+        for (int j = 0; j < count; ++j) members[dclass(jobs[j].d)].push_back(j);
+        std::vector<ClassItems> classes;
+        for (auto& kv : members) {
+            ClassItems ci;
+            ci.dc = kv.first;
+            int tpi = 0;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                auto f = g_tuned.find(ci.dc);
+                if (f != g_tuned.end()) tpi = f->second;
+            }
+            if (tpi == 0) {
+                // time the real first pass for a few item sizes, resetting the sums between
+                const int cand[4] = {1, 4, 16, kMaxTilesPerItem};
+                float best_ms = 0.f;
+                cudaEvent_t e0, e1;
+                KM2_CUDA(cudaEventCreate(&e0));
+                KM2_CUDA(cudaEventCreate(&e1));
+                for (int c = 0; c < 4; ++c) {
+                    ClassItems trial;
+                    build_items(trial, kv.second, nvec, cand[c]);
+                    KM2_TRY(ws.alloc((void**)&trial.dev, sizeof(WorkItem) * (size_t)trial.count, s));
+                    KM2_CUDA(cudaMemcpyAsync(trial.dev, trial.host.data(),
+                                             sizeof(WorkItem) * (size_t)trial.count,
+                                             cudaMemcpyHostToDevice, s));
+                    KM2_CUDA(cudaEventRecord(e0, s));
+                    KM2_TRY(launch_class(ci.dc, dinst, trial.dev, trial.count, s, ws.sm_count));
+                    KM2_CUDA(cudaEventRecord(e1, s));
+                    ++g_launches;
+                    batch_reset_kernel<<<count, kThreads, 0, s>>>(dinst);
+                    KM2_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    KM2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (c == 0 || ms < best_ms) { best_ms = ms; tpi = cand[c]; }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                g_tuned[ci.dc] = tpi;
+            }
+            build_items(ci, kv.second, nvec, tpi);
+            KM2_TRY(ws.alloc((void**)&ci.dev, sizeof(WorkItem) * (size_t)ci.count, s));
+            KM2_CUDA(cudaMemcpyAsync(ci.dev, ci.host.data(), sizeof(WorkItem) * (size_t)ci.count,
+                                     cudaMemcpyHostToDevice, s));
+            classes.push_back(std::move(ci));
+        }
+
+        // ---- the iteration loop as one graph with a device-side while condition
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        KM2_CUDA(cudaGraphCreate(&graph, 0));
+        do {
+            cudaGraphConditionalHandle handle;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+            if (e != cudaSuccess) { set_last_error("cudaGraphConditionalHandleCreate", e); rc = KMEANS2_ERR_CUDA; break; }
+            alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+            std::memset(raw, 0, sizeof(raw));
+            cudaGraphNodeParams* gp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+            gp->type = cudaGraphNodeTypeConditional;
+            gp->conditional.handle = handle;
+            gp->conditional.type = cudaGraphCondTypeWhile;
+            gp->conditional.size = 1;
+            cudaGraphNode_t node;
+            e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, gp);
+            if (e != cudaSuccess) { set_last_error("cudaGraphAddNode", e); rc = KMEANS2_ERR_CUDA; break; }
+            cudaGraph_t body = gp->conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) { set_last_error("cudaStreamBeginCaptureToGraph", e); rc = KMEANS2_ERR_CUDA; break; }
+            for (auto& ci : classes) {
+                rc = launch_class(ci.dc, dinst, ci.dev, ci.count, s, ws.sm_count);
+                if (rc != KMEANS2_OK) break;
+            }
+            if (rc == KMEANS2_OK) {
+                batch_recheck_kernel<<<count, kThreads, 0, s>>>(dinst);
+                batch_finalize_kernel<<<count, kThreads, 0, s>>>(dinst, counters);
+                batch_control_kernel<<<1, 1, 0, s>>>(counters, counters + 1, 2 * max_iter_all + 2,
+                                                     (unsigned long long)handle);
+            }
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(s, &captured);
+            if (rc != KMEANS2_OK) break;
+            if (e != cudaSuccess) { set_last_error("cudaStreamEndCapture", e); rc = KMEANS2_ERR_CUDA; break; }
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess) { set_last_error("cudaGraphInstantiate", e); rc = KMEANS2_ERR_CUDA; break; }
+            e = cudaGraphLaunch(exec, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { set_last_error("batched graph", e); rc = KMEANS2_ERR_CUDA; break; }
+        } while (0);
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (rc == KMEANS2_OK) {
+            int iters = 0;
+            KM2_CUDA(cudaMemcpy(&iters, counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
+            g_launches += (long long)iters * ((long long)classes.size() + 3);
+            // ---- results
+            KM2_CUDA(cudaMemcpyAsync(hi.data(), dinst, sizeof(BatchInst) * (size_t)count,
+                                     cudaMemcpyDeviceToHost, s));
+            KM2_CUDA(cudaStreamSynchronize(s));
+            for (int j = 0; j < count && rc == KMEANS2_OK; ++j) {
+                const kmeans2_job& J = jobs[j];
+                const BatchInst& I = hi[j];
+                KM2_CUDA(cudaMemcpyAsync(J.centers_out, I.c.c64, sizeof(double) * (size_t)J.k * J.d,
+                                         cudaMemcpyDefault, s));
+                KM2_CUDA(cudaMemcpyAsync(J.labels_out, I.lab_slow, sizeof(int) * (size_t)J.n,
+                                         cudaMemcpyDefault, s));
+            }
+            KM2_CUDA(cudaStreamSynchronize(s));
+            const double secs =
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            bool nonfinite = false;
+            for (int j = 0; j < count; ++j) {
+                const BatchInst& I = hi[j];
+                if (I.error) nonfinite = true;
+                if (!results) continue;
+                kmeans2_result& r = results[j];
+                std::memset(&r, 0, sizeof(r));
+                r.J = I.st.J;
+                r.iters_fast = I.iters_fast;
+                r.iters_slow = I.error ? 0 : I.st.iter;
+                r.converged_fast = I.conv_fast;
+                r.converged_slow = I.error ? 0 : I.st.converged;
+                r.empty_clusters = I.st.empty;
+                r.precision_used = KMEANS2_PRECISION_FP32;
+                r.subset_size = I.m;
+                r.rechecked_points = I.rechecked;
+                r.distance_evals = (int64_t)r.iters_fast * I.m * I.k + (int64_t)r.iters_slow * I.n * I.k;
+                r.shift_fast = I.shift_fast;
+                r.shift_slow = I.st.shift;
+                r.seconds = secs;
+            }
+            if (nonfinite) {
+                set_last_error_text("kmeans2_fit_batched: some job holds NaN or infinity");
+                rc = KMEANS2_ERR_NONFINITE;
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    if (o.profile) o.profile->kernel_launches += g_launches - launches0;
+    return rc;
+}

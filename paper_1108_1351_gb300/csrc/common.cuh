@@ -68,6 +68,17 @@ struct Centers {
     int k, d, kpad, dpad;
 };
 
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) as a counter-based generator:
+// output number pos of the stream seeded with `seed`.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                             unsigned long long pos)
+{
+    unsigned long long z = seed + (pos + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ long long to_fixed(float x, float scale)
 {
     return __float2ll_rn(x * scale);

@@ -20,22 +20,14 @@ namespace km2 {
 
 namespace {
 
-constexpr unsigned long long kGamma = 0x9E3779B97F4A7C15ull;
 constexpr int kBins = 2048;           // 11-bit digits
 constexpr int kThreads = 256;
 constexpr int kChunkItems = 4096;     // indices per compaction chunk (16 per thread)
 
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 __device__ __forceinline__ unsigned long long key_at(unsigned long long seed,
                                                      unsigned long long pos)
 {
-    return mix64(seed + (pos + 1ull) * kGamma);
+    return splitmix64_at(seed, pos);
 }
 
 struct SelectState {

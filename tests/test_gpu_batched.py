@@ -1,0 +1,71 @@
+"""Batched form (kmeans2_fit_batched) vs the oracle and vs single fits (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1108_1351_gb300 as km
+from paper_1108_1351_gb300 import synth
+from tests.gpu_helpers import assert_centers_close, assert_J_close, to_np
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1351_gb300 import build
+    build.build()
+    oracle.build()
+    km.load()
+
+
+def _specs(count, seed, n_hi=20000, k_hi=40):
+    specs = synth.instance_specs(count, seed=seed, n_lo=300, n_hi=n_hi, k_lo=1, k_hi=k_hi)
+    return specs
+
+
+def test_batched_matches_oracle_per_job():
+    specs = _specs(48, 1)
+    Xs = [synth.instance_data(s, device=DEV) for s in specs]
+    res, rc = km.fit_batched(Xs, [s.k for s in specs], 0.1, [s.seed for s in specs], 1e-6, 40)
+    assert rc == 0
+    nt = max(1, oracle.max_threads())
+    for s, X, r in zip(specs, Xs, res):
+        Xh = to_np(X)
+        o = oracle.fit(Xh, s.k, 0.1, s.seed, 1e-6, 40, nthreads=nt)
+        assert (r.iters_fast, r.iters_slow) == (o["iters_fast"], o["iters_slow"]), s
+        assert np.array_equal(to_np(r.labels), o["labels"]), s
+        assert_centers_close(to_np(r.centers), o["centers"], Xh)
+        assert_J_close(r.J, o["J"], Xh)
+        assert r.distance_evals == o["distance_evals"]
+
+
+def test_batched_equals_single_fits():
+    specs = _specs(40, 2, n_hi=200_000, k_hi=256)
+    Xs = [synth.instance_data(s, device=DEV) for s in specs]
+    res, rc = km.fit_batched(Xs, [s.k for s in specs], 0.1, [s.seed for s in specs], 1e-5, 30,
+                             tol_fast=1e-3)
+    assert rc == 0
+    for s, X, r in zip(specs, Xs, res):
+        a = km.fit(X, s.k, 0.1, s.seed, 1e-5, 30, tol_fast=1e-3, precision="fp32")
+        assert (r.iters_fast, r.iters_slow) == (a.iters_fast, a.iters_slow), s
+        assert torch.equal(r.labels, a.labels), s
+        assert torch.equal(r.centers, a.centers), s
+        assert r.J == a.J
+
+
+def test_batched_nonfinite_job_does_not_disturb_others():
+    specs = _specs(6, 3)
+    Xs = [synth.instance_data(s, device=DEV) for s in specs]
+    Xs[2][min(5, Xs[2].shape[0] - 1), 0] = float("nan")
+    res, rc = km.fit_batched(Xs, [s.k for s in specs], 0.2, [s.seed for s in specs], 1e-6, 30,
+                             raise_on_error=False)
+    assert rc == -4
+    for j, (s, X, r) in enumerate(zip(specs, Xs, res)):
+        if j == 2:
+            continue
+        a = km.fit(X, s.k, 0.2, s.seed, 1e-6, 30, precision="fp32")
+        assert torch.equal(r.labels, a.labels) and r.J == a.J
