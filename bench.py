@@ -44,6 +44,8 @@ CONFIGS = {
     "aniso8_small": dict(gen="aniso", n=20_000_000, d=8, k=32, f=0.01, tol=1e-5, max_iter=50,
                          seed=0),
     "vmf128": dict(gen="vmf", n=50_000_000, d=128, k=1024, f=0.02, tol=1e-6, max_iter=50, seed=0),
+    "vmf128_small": dict(gen="vmf", n=2_000_000, d=128, k=1024, f=0.02, tol=1e-6, max_iter=50,
+                         seed=0),
 }
 METRIC = "two-stage k-means distance evals/s (time-to-converge per fit beside it)"
 UNIT = "distance evals/s"
@@ -140,6 +142,87 @@ def _dist():
     return ws, rank, local
 
 
+TF32_PER_BF16 = 1.1 / 2.25      # nominal dense TF32 : BF16 tensor rate on GB300
+
+
+def roofline_of(form: str, d: int, k: int, prof, clk):
+    """Roofline entry of the distance kernel the fit ran (the dominant kernel):
+    algorithmic FLOP = 2 N k d per launch (the cross term only), achieved =
+    their sum over the timed launches / their summed CUDA-event time."""
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    achieved = prof.assign_flops / (prof.assign_ms * 1e-3) / 1e12 if prof.assign_ms > 0 else None
+    if form == "bf16":
+        kernel, bound = "assign_bf16", "tensor"
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        peak_source = f"{src} bf16_tflops_sustained (kernel timed inside a long fit)"
+    elif form == "tf32x3":
+        kernel, bound = "assign_tc32", "tensor"
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * TF32_PER_BF16
+        peak_source = f"{src} bf16_tflops_sustained x nominal TF32/BF16 ratio 1.1/2.25"
+    else:
+        kernel = f"assign_small<{d}>" if d <= 16 else "assign_large"
+        bound = "alu"
+        peak = 2.0 * FP32_LANES_PER_SM * SM_COUNT_GB300 * sm_max * 1e6 / 1e12
+        peak_source = (f"derived: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                       f"{sm_max:.0f} MHz ({src} max clock)")
+    roof = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic_of(kernel, prof, d), "peak_source": peak_source,
+            "kernel_ms_avg": prof.assign_ms / max(1, prof.assign_launches),
+            "kernel_launches": prof.assign_launches,
+            "achieved_hbm_gbs": prof.assign_bytes / (prof.assign_ms * 1e-3) / 1e9
+            if prof.assign_ms > 0 else None,
+            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    if achieved and bound == "alu" and clk and clk.get("sm_mhz"):
+        roof["frac_at_observed_clock"] = achieved / (peak * clk["sm_mhz"] / sm_max)
+    return roof
+
+
+def traffic_of(kernel: str, prof, d: int):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary
+    (profiles/<kernel>*.md lines 'traffic-per-point: <kernel> <bytes> <sha256 of
+    the kernel source>'), scaled by the points of an average timed launch; None
+    when there is no summary or the kernel source changed since the capture."""
+    import glob
+    import hashlib
+    base = kernel.split("<")[0]
+    src = {"assign_small": "assign_fp32.cu", "assign_large": "assign_fp32.cu",
+           "assign_bf16": "assign_bf16.cu", "assign_tc32": "assign_tc32.cu"}.get(base)
+    if not src or prof.assign_launches == 0:
+        return None
+    path = os.path.join(ROOT, "paper_1108_1351_gb300", "csrc", src)
+    try:
+        with open(path, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(f) as fh:
+            for ln in fh:
+                parts = ln.strip().strip("`").split()
+                if len(parts) == 4 and parts[0] == "traffic-per-point:" and parts[1] == kernel:
+                    if parts[3] != sha:
+                        return None
+                    # assign_bytes counts 4 d bytes per point of every timed launch
+                    points = prof.assign_bytes / (4.0 * d) / max(1, prof.assign_launches)
+                    return float(parts[2]) * points
+    return None
+
+
+def reduce_over_ranks(ms: float, work: float, ws: int, device):
+    """(max over ranks of the elapsed ms, sum over ranks of the work); the
+    identity at one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def cpu_baseline(X_host, cfg, budget_s: float = 12.0):
     """The oracle as it stands, timed on the host cores: Lloyd steps on the
     first rows of the same data until ~budget_s of CPU work."""
@@ -153,7 +236,7 @@ def cpu_baseline(X_host, cfg, budget_s: float = 12.0):
     C = Xs[:k].astype(np.float64)
     evals, t = 0, 0.0
     steps = 0
-    while t < budget_s and steps < 50:
+    while t < budget_s:
         t0 = time.perf_counter()
         C, lab, J, sh, em = oracle.lloyd_step(Xs, C, nthreads=nt)
         t += time.perf_counter() - t0
@@ -239,23 +322,19 @@ def run_ours(args, cfg):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    rng = torch.cuda.nvtx.range_start("timed")     # lets ncu select the timed launches
     e0.record(stream)
     for _ in range(args.steps):
         results.append(one(prof))
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_end(rng)
     if ws > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     evals = sum(r.distance_evals for r in results)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    ev = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    total_evals = float(ev.item())
+    ms_max, total_evals = reduce_over_ranks(ms, evals, ws, dev)
 
     # end to end through the same C-ABI call with HOST buffers
     e2e = None
@@ -278,14 +357,10 @@ def run_ours(args, cfg):
                        centers_out=ch, labels_out=lh, stream=stream, precision=args.precision)
             e_evals += r.distance_evals
         torch.cuda.synchronize()
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-        ee = torch.tensor([float(e_evals)], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            dist.all_reduce(ee, op=dist.ReduceOp.SUM)
-        e2e = {"value": float(ee.item()) / float(te.item()), "unit": UNIT,
+        te_ms, ee = reduce_over_ranks(1e3 * (time.perf_counter() - t0), e_evals, ws, dev)
+        e2e = {"value": ee / (te_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * 4 + k * d * 8,
-               "steps": args.e2e_steps, "ms_per_step": 1e3 * float(te.item()) / args.e2e_steps}
+               "steps": args.e2e_steps, "ms_per_step": te_ms / args.e2e_steps}
         Xh_host = Xh.numpy()
     else:
         Xh_host = X[: min(n, 2_000_000)].cpu().numpy()
@@ -294,23 +369,8 @@ def run_ours(args, cfg):
         if ws > 1:
             dist.destroy_process_group()
         return 0
-    peaks, peak_src = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    p32 = 2.0 * FP32_LANES_PER_SM * SM_COUNT_GB300 * sm_max * 1e6 / 1e12     # TFLOP/s
-    achieved = prof.assign_flops / (prof.assign_ms * 1e-3) / 1e12 if prof.assign_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": f"assign_small<{d}>" if d <= 16 else "assign_large",
-                "achieved": achieved, "peak": p32, "unit": "TFLOP/s",
-                "frac": (achieved / p32) if achieved else None, "traffic": None,
-                "peak_source": f"derived: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                               f"x {sm_max:.0f} MHz ({peak_src} max clock)",
-                "kernel_ms_avg": prof.assign_ms / max(1, prof.assign_launches),
-                "kernel_launches": prof.assign_launches,
-                "achieved_hbm_gbs": prof.assign_bytes / (prof.assign_ms * 1e-3) / 1e9
-                if prof.assign_ms > 0 else None,
-                "hbm_peak_gbs": peaks.get("hbm_gbs")}
-    if clk and clk.get("sm_mhz"):
-        roofline["frac_at_observed_clock"] = achieved / (p32 * clk["sm_mhz"] / sm_max) if achieved else None
     r0 = results[-1]
+    roofline = roofline_of(r0.precision_used, d, k, prof, clk)
     line = {
         "metric": METRIC, "value": total_evals / (ms_max * 1e-3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -339,12 +399,167 @@ def run_ours(args, cfg):
     return 0
 
 
+SERVE = dict(rate=200.0, duration=60.0, seed=0, f=0.1, tol=1e-6, max_iter=100)
+
+
+def _serve_trace(trace, srv, dev, stream, *, drain_cap: float, data_cap_bytes: int):
+    """Replay the arrival trace against one server: a client thread generates
+    each job's data on the device at its arrival time and submits it; the main
+    thread collects finished jobs.  Latency = completion - scheduled arrival,
+    both on the server's clock.  Jobs still unfinished drain_cap seconds after
+    the last arrival are reported as censored (latency >= their age)."""
+    import torch
+    from paper_1108_1351_gb300 import synth
+
+    outstanding = {}            # ticket -> (job spec, scheduled arrival, bytes)
+    lock = threading.Lock()
+    state = {"bytes": 0, "submitted": 0, "late": 0.0, "error": None}
+    start = srv.now() + 0.5
+
+    def client():
+        try:
+            with torch.cuda.device(dev), torch.cuda.stream(stream):
+                for js in trace:
+                    t_sched = start + js.t_arrival
+                    while True:
+                        with lock:
+                            room = state["bytes"] + js.n * js.d * 4 <= data_cap_bytes or not outstanding
+                        now = srv.now()
+                        if room and now >= t_sched:
+                            break
+                        time.sleep(min(0.002, max(0.0, t_sched - now)) if room else 0.002)
+                    state["late"] = max(state["late"], srv.now() - t_sched)
+                    X = synth.iso_gaussian_mixture(js.n, js.d, js.k, js.seed, lo=-20.0, hi=20.0,
+                                                   device=dev)
+                    stream.synchronize()
+                    t = srv.submit(X, js.k, SERVE["f"], js.seed, SERVE["tol"], SERVE["max_iter"])
+                    with lock:
+                        outstanding[t] = (js, t_sched, js.n * js.d * 4)
+                        state["bytes"] += js.n * js.d * 4
+                        state["submitted"] += 1
+                    del X
+        except Exception as e:      # reported by the collector
+            state["error"] = repr(e)
+
+    th = threading.Thread(target=client, daemon=True)
+    th.start()
+    done = []
+    last_arrival = start + (trace[-1].t_arrival if trace else 0.0)
+    while True:
+        with lock:
+            tickets = list(outstanding)
+        for t in tickets:
+            sv = srv.poll(t)
+            if sv is None:
+                continue
+            with lock:
+                js, t_sched, b = outstanding.pop(t)
+                state["bytes"] -= b
+            done.append((js, t_sched, sv))
+        if state["error"]:
+            raise RuntimeError(state["error"])
+        if not th.is_alive() and not outstanding and state["submitted"] == len(trace):
+            break
+        if srv.now() > last_arrival + drain_cap:
+            break
+        time.sleep(0.001)
+    t_end = srv.now()
+    th.join(timeout=drain_cap + 60)
+    censored = []
+    with lock:
+        for t, (js, t_sched, b) in outstanding.items():
+            censored.append(t_end - t_sched)
+    never = len(trace) - state["submitted"]
+    return done, censored, never, start, t_end, state["late"]
+
+
+def _latency_summary(done, censored, never, start, t_end):
+    import numpy as np
+    lat = [sv.t_done - t_sched for (js, t_sched, sv) in done if sv.status == 0]
+    fails = sum(1 for (_, _, sv) in done if sv.status != 0)
+    cens = list(censored) + [t_end - start] * never
+    allv = np.asarray(lat + cens, dtype=np.float64)
+    evals = sum(sv.result.distance_evals for (_, _, sv) in done if sv.status == 0)
+    span = max((sv.t_done for (_, _, sv) in done), default=t_end) - start
+    return {"completed": len(lat), "failed": fails, "censored": len(cens),
+            "jobs_per_s": len(lat) / span if span > 0 else None,
+            "p50_s": float(np.percentile(allv, 50)) if allv.size else None,
+            "p99_s": float(np.percentile(allv, 99)) if allv.size else None,
+            "mean_s": float(allv.mean()) if allv.size else None,
+            "max_s": float(allv.max()) if allv.size else None,
+            "distance_evals_per_s": evals / span if span > 0 else None,
+            "span_s": span}
+
+
+def run_serve(args):
+    """Serving workload: Poisson arrivals, jobs of mixed n, d, k, served by the
+    continuous-batching server and, on the same trace, one job at a time in the
+    plain FP32 form."""
+    import torch
+    import paper_1108_1351_gb300 as km
+    from paper_1108_1351_gb300 import synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.load()
+    trace = synth.arrival_trace(rate=SERVE["rate"], duration=args.duration, seed=SERVE["seed"] + rank)
+    free, total = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.45)
+    data_cap = int(free * 0.3)
+    stream = torch.cuda.Stream(dev)
+    # warm-up: one small job of each dimension through a throwaway server
+    with km.Server(hbm_budget=budget, max_slots=2) as srv:
+        for d in (4, 16, 64, 128):
+            X = synth.iso_gaussian_mixture(50_000, d, 32, 99, device=dev)
+            srv.wait(srv.submit(X, 32, 0.1, 99, 1e-6, 20))
+    clocks = ClockSampler(None)
+    clocks.start()
+    out = {}
+    for name, slots, prec in (("served", args.serve_slots, "auto"),
+                              ("one_at_a_time_fp32", 1, "fp32")):
+        with km.Server(hbm_budget=budget, max_slots=slots, precision=prec) as srv:
+            done, censored, never, start, t_end, late = _serve_trace(
+                trace, srv, dev, stream, drain_cap=args.drain_cap, data_cap_bytes=data_cap)
+            summ = _latency_summary(done, censored, never, start, t_end)
+            st = srv.stats()
+        summ.update({"slots": slots, "precision": prec, "kernel_launches": st["kernel_launches"],
+                     "hbm_peak_gb": st["hbm_peak"] / 1e9, "client_max_lag_s": late})
+        out[name] = summ
+    clk = clocks.stop()
+    if rank != 0:
+        return 0
+    srv_s = out["served"]
+    line = {
+        "metric": "serving: jobs/s completed under Poisson arrivals (p50/p99 latency beside)",
+        "value": srv_s["jobs_per_s"], "unit": "jobs/s", "n_gpus": ws, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * srv_s["span_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": "serve", "rate_per_s": SERVE["rate"], "duration_s": args.duration,
+                   "jobs": len(trace), "n": "log-U[1e4, 2e7]", "d": [4, 16, 64, 128],
+                   "k": "log-U[4, 1024]", "subset_fraction": SERVE["f"], "tol": SERVE["tol"],
+                   "max_iter": SERVE["max_iter"], "hbm_budget_gb": budget / 1e9,
+                   "drain_cap_s": args.drain_cap},
+        "latency_s": {"p50": srv_s["p50_s"], "p99": srv_s["p99_s"], "mean": srv_s["mean_s"],
+                      "max": srv_s["max_s"]},
+        "served": srv_s, "one_at_a_time_fp32": out["one_at_a_time_fp32"],
+        "gpu_launches": int(srv_s["kernel_launches"]), "roofline": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="aniso8", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="aniso8", choices=sorted(CONFIGS) + ["serve"])
+    ap.add_argument("--duration", type=float, default=SERVE["duration"],
+                    help="serve: seconds of Poisson arrivals")
+    ap.add_argument("--serve-slots", type=int, default=8, help="serve: jobs running at once")
+    ap.add_argument("--drain-cap", type=float, default=120.0,
+                    help="serve: seconds after the last arrival before unfinished jobs are censored")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,6 +567,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
+    if args.config == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no "
+                              "oracle arm; its baseline is the one-job-at-a-time FP32 form"}))
+            return 0
+        return run_serve(args)
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         return run_reference(args, cfg)

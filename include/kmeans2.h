@@ -166,18 +166,21 @@ KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, dou
                 uint64_t seed, double tol, int32_t max_iter, double* centers_out,
                 int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt);
 
-/* One independent clustering problem of a batch (kmeans2_fit_batched). */
+/* One independent clustering problem: an entry of a batch (kmeans2_fit_batched)
+   or a request to a server (kmeans2_server_submit).  The limits in brackets
+   are the batched form's; a server job takes any shape kmeans2_fit takes. */
 typedef struct kmeans2_job {
-    const float* X;             /* n*d FP32 points, DEVICE memory, 16-byte aligned */
+    const float* X;             /* n*d FP32 points [DEVICE memory, 16-byte aligned];
+                                   server: host or device */
     int64_t n;
-    int32_t d;                  /* 1 <= d <= 64 */
-    int32_t k;                  /* 1 <= k <= min(n, 256) */
+    int32_t d;                  /* [1 <= d <= 64] */
+    int32_t k;                  /* [1 <= k <= min(n, 256)] */
     double subset_fraction;     /* per, in (0, 1] */
     uint64_t seed;
     double tol;                 /* slow-stage tolerance; options->tol_fast, when > 0,
                                    is every job's fast-stage tolerance */
     int32_t max_iter;           /* per stage, >= 1 */
-    int32_t reserved;
+    int32_t reserved;           /* must be 0 */
     double* centers_out;        /* k*d FP64 (host or device) */
     int32_t* labels_out;        /* n int32 (host or device) */
 } kmeans2_job;
@@ -203,6 +206,98 @@ typedef struct kmeans2_job {
  */
 KMEANS2_API int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs,
                                     kmeans2_result* results, const kmeans2_options* opt);
+
+/*
+ * Serving: continuous batching of independent two-stage fits.  (The paper has
+ * no counterpart; this is the library's request loop around kmeans2_fit.)
+ *
+ * A server owns `max_slots` worker threads, each with its own non-blocking
+ * CUDA stream on the device that was current at creation.  Submitted jobs wait
+ * in arrival order; a free worker admits the first waiting job whose device
+ * footprint (kmeans2_fit_footprint) fits into the HBM budget beside the jobs
+ * already running, and runs kmeans2_fit on it (graph-captured stage loops), so
+ * the work of different jobs overlaps on the GPU.  A job may be passed over
+ * by later, smaller jobs at most 8 times; after that nothing behind it is
+ * admitted before it.  A job's data, centers and labels stay on the device
+ * from admission until its result is written.  Each result equals kmeans2_fit
+ * on that job alone (same kernels, exact cluster sums).
+ */
+typedef struct kmeans2_server kmeans2_server;
+
+#define KMEANS2_PENDING 1             /* kmeans2_server_poll: not finished yet */
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed, rejected;
+    int64_t kernel_launches;          /* kernels launched by the workers */
+    int32_t queued, running, slots, pad_;
+    uint64_t hbm_budget, hbm_in_use, hbm_peak;   /* bytes, by footprint */
+} kmeans2_server_stats;
+
+typedef struct {
+    double t_submit, t_admit, t_done; /* seconds on the server's clock */
+} kmeans2_ticket_times;
+
+/*
+ * kmeans2_fit_footprint -- upper estimate of the device bytes kmeans2_fit
+ * allocates for one problem: the workspace, S_s and its labels, the sampling
+ * scratch, the BF16 copies when that form is chosen, the labels when the
+ * caller's are not on the device, and a staged copy of X when x_on_host.
+ * precision: as kmeans2_options.precision (AUTO resolves as kmeans2_fit does
+ * for 16-byte aligned device X).  Returns 0 for invalid arguments.
+ */
+KMEANS2_API uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k,
+                                           double subset_fraction, int32_t max_iter,
+                                           int32_t precision, int32_t x_on_host,
+                                           int32_t labels_on_host);
+
+/*
+ * kmeans2_server_create -- start a server on the current device.
+ *  hbm_budget  bytes of device memory the running jobs may hold together
+ *              (their footprints, with device-resident X counted too);
+ *              0 = 90% of the device memory free at creation.
+ *  max_slots   jobs running at once, 1..64.
+ *  opt         may be NULL; precision, tol_fast and deterministic apply to
+ *              every job (stream, init_centers, start_stage, trajectories and
+ *              profile must be unset).
+ * Returns NULL on invalid arguments or if the device cannot be used.
+ */
+KMEANS2_API kmeans2_server* kmeans2_server_create(uint64_t hbm_budget, int32_t max_slots,
+                                                  const kmeans2_options* opt);
+
+/*
+ * kmeans2_server_submit -- queue one job; returns at once with its ticket.
+ * The caller keeps job->X, centers_out and labels_out valid and untouched
+ * until the job is reported finished.  Errors: KMEANS2_ERR_INVALID (argument
+ * out of range), KMEANS2_ERR_ADMISSION (footprint above the whole budget; the
+ * job is not queued).
+ */
+KMEANS2_API int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job,
+                                      uint64_t* ticket);
+
+/*
+ * kmeans2_server_poll -- KMEANS2_PENDING while the job waits or runs; once it
+ * has finished, its kmeans2_fit status (0 or a negative code), with *res and
+ * *times (each may be NULL) filled in, and the ticket is released.
+ * KMEANS2_ERR_INVALID for an unknown or released ticket.
+ */
+KMEANS2_API int kmeans2_server_poll(kmeans2_server* srv, uint64_t ticket, kmeans2_result* res,
+                                    kmeans2_ticket_times* times);
+
+/* kmeans2_server_poll after waiting up to timeout_s seconds (< 0: no limit)
+   for the job to finish; KMEANS2_PENDING if it has not. */
+KMEANS2_API int kmeans2_server_wait(kmeans2_server* srv, uint64_t ticket, double timeout_s,
+                                    kmeans2_result* res, kmeans2_ticket_times* times);
+
+/* Counters of the server; returns KMEANS2_ERR_INVALID for NULL arguments. */
+KMEANS2_API int kmeans2_server_stats_get(kmeans2_server* srv, kmeans2_server_stats* out);
+
+/* Seconds since the server was created (its clock for kmeans2_ticket_times). */
+KMEANS2_API double kmeans2_server_now(kmeans2_server* srv);
+
+/* Stop a server: jobs still waiting finish with KMEANS2_ERR_ADMISSION without
+   running, running jobs complete, the workers exit.  Tickets not yet polled
+   are released. */
+KMEANS2_API void kmeans2_server_destroy(kmeans2_server* srv);
 
 /*
  * kmeans_step -- one Lloyd iteration (Section 4.1; the loop body of the

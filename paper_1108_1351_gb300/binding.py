@@ -95,6 +95,32 @@ class Result(ctypes.Structure):
     ]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("admitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("rejected", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("queued", ctypes.c_int32),
+        ("running", ctypes.c_int32),
+        ("slots", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
+        ("hbm_budget", ctypes.c_uint64),
+        ("hbm_in_use", ctypes.c_uint64),
+        ("hbm_peak", ctypes.c_uint64),
+    ]
+
+
+class TicketTimes(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+PENDING = 1
+
+
 def load():
     """Load libkmeans2.so (raises if it has not been built)."""
     global _lib
@@ -119,6 +145,24 @@ def load():
                                             ctypes.POINTER(Options)]
         lib.kmeans_step_noalloc.restype = ctypes.c_int
         lib.kmeans_step_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P]
+        lib.kmeans2_fit_footprint.restype = u64
+        lib.kmeans2_fit_footprint.argtypes = [i64, i32, i32, f64, i32, i32, i32, i32]
+        lib.kmeans2_server_create.restype = P
+        lib.kmeans2_server_create.argtypes = [u64, i32, ctypes.POINTER(Options)]
+        lib.kmeans2_server_submit.restype = ctypes.c_int
+        lib.kmeans2_server_submit.argtypes = [P, ctypes.POINTER(Job), ctypes.POINTER(u64)]
+        lib.kmeans2_server_poll.restype = ctypes.c_int
+        lib.kmeans2_server_poll.argtypes = [P, u64, ctypes.POINTER(Result),
+                                            ctypes.POINTER(TicketTimes)]
+        lib.kmeans2_server_wait.restype = ctypes.c_int
+        lib.kmeans2_server_wait.argtypes = [P, u64, f64, ctypes.POINTER(Result),
+                                            ctypes.POINTER(TicketTimes)]
+        lib.kmeans2_server_stats_get.restype = ctypes.c_int
+        lib.kmeans2_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
+        lib.kmeans2_server_now.restype = f64
+        lib.kmeans2_server_now.argtypes = [P]
+        lib.kmeans2_server_destroy.restype = None
+        lib.kmeans2_server_destroy.argtypes = [P]
         lib.kmeans2_subset_size.restype = i64
         lib.kmeans2_subset_size.argtypes = [i64, i32, f64]
         lib.kmeans2_sample.restype = ctypes.c_int
@@ -271,6 +315,131 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                      shift_slow=res.shift_slow, seconds=res.seconds,
                      precision_used={0: "fp32", 1: "bf16", 3: "tf32x3"}.get(res.precision_used, "?"),
                      traj=traj)
+
+
+def _fit_result(r, cen, lab, traj=None) -> FitResult:
+    return FitResult(centers=cen, labels=lab, J=r.J, iters_fast=r.iters_fast,
+                     iters_slow=r.iters_slow, converged_fast=bool(r.converged_fast),
+                     converged_slow=bool(r.converged_slow), empty_clusters=r.empty_clusters,
+                     subset_size=r.subset_size, rechecked_points=r.rechecked_points,
+                     distance_evals=r.distance_evals, shift_fast=r.shift_fast,
+                     shift_slow=r.shift_slow, seconds=r.seconds,
+                     precision_used={0: "fp32", 1: "bf16", 3: "tf32x3"}.get(r.precision_used, "?"),
+                     traj=traj or {})
+
+
+def footprint(n: int, d: int, k: int, subset_fraction: float, max_iter: int, *,
+              precision: str = "auto", x_on_host: bool = False,
+              labels_on_host: bool = False) -> int:
+    """Device bytes kmeans2_fit allocates for one problem (kmeans2_fit_footprint)."""
+    return int(load().kmeans2_fit_footprint(n, d, k, subset_fraction, max_iter,
+                                            PRECISION[precision], int(x_on_host),
+                                            int(labels_on_host)))
+
+
+@dataclass
+class Served:
+    """A finished server job: its status, result (None on failure) and the
+    server-clock times of submission, admission and completion."""
+    ticket: int
+    status: int
+    result: "FitResult | None"
+    t_submit: float
+    t_admit: float
+    t_done: float
+
+
+class Server:
+    """Continuous-batching request loop (kmeans2_server_*).
+
+    ``submit`` queues a job and returns its ticket at once; ``poll`` / ``wait``
+    return a ``Served`` once the job has finished.  The server holds references
+    to each job's tensors until the job has been collected."""
+
+    def __init__(self, hbm_budget: int = 0, max_slots: int = 4, *, precision: str = "auto",
+                 tol_fast: float = 0.0, device=None):
+        lib = load()
+        opt = Options()
+        lib.kmeans2_default_options(ctypes.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.tol_fast = tol_fast
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.device = dev
+        with torch.cuda.device(dev):
+            self._h = lib.kmeans2_server_create(int(hbm_budget), int(max_slots), ctypes.byref(opt))
+        if not self._h:
+            raise KMeans2Error(-1, "kmeans2_server_create")
+        self._refs: dict[int, tuple] = {}
+        self._mu = threading.Lock()
+
+    def submit(self, X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int, *,
+               centers_out=None, labels_out=None) -> int:
+        lib = load()
+        X = _as_points(X)
+        n, d = X.shape
+        cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
+        lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+        job = Job(X=_ptr(X), n=n, d=d, k=int(k), subset_fraction=float(subset_fraction),
+                  seed=int(seed) & (2**64 - 1), tol=float(tol), max_iter=int(max_iter), reserved=0,
+                  centers_out=_ptr(cen), labels_out=_ptr(lab))
+        t = ctypes.c_uint64(0)
+        with self._mu:
+            rc = lib.kmeans2_server_submit(self._h, ctypes.byref(job), ctypes.byref(t))
+            if rc != 0:
+                raise KMeans2Error(rc, "kmeans2_server_submit")
+            self._refs[t.value] = (X, cen, lab)
+        return t.value
+
+    def _collect(self, ticket, rc, r, tt):
+        if rc == PENDING:
+            return None
+        with self._mu:
+            X, cen, lab = self._refs.pop(ticket, (None, None, None))
+        res = _fit_result(r, cen, lab) if rc == 0 else None
+        return Served(ticket=ticket, status=rc, result=res, t_submit=tt.t_submit,
+                      t_admit=tt.t_admit, t_done=tt.t_done)
+
+    def poll(self, ticket: int) -> "Served | None":
+        r, tt = Result(), TicketTimes()
+        rc = load().kmeans2_server_poll(self._h, ticket, ctypes.byref(r), ctypes.byref(tt))
+        if rc == -1 and ticket not in self._refs:
+            raise KMeans2Error(rc, "kmeans2_server_poll")
+        return self._collect(ticket, rc, r, tt)
+
+    def wait(self, ticket: int, timeout: float = -1.0) -> "Served | None":
+        r, tt = Result(), TicketTimes()
+        rc = load().kmeans2_server_wait(self._h, ticket, float(timeout), ctypes.byref(r),
+                                        ctypes.byref(tt))
+        if rc == -1 and ticket not in self._refs:
+            raise KMeans2Error(rc, "kmeans2_server_wait")
+        return self._collect(ticket, rc, r, tt)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        load().kmeans2_server_stats_get(self._h, ctypes.byref(st))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_ if name != "pad_"}
+
+    def now(self) -> float:
+        return float(load().kmeans2_server_now(self._h))
+
+    def close(self):
+        if self._h:
+            load().kmeans2_server_destroy(self._h)
+            self._h = None
+            self._refs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: float = 0.0,

@@ -279,8 +279,10 @@ int run_loop_graph(const float* X, long long n, int d, Workspace& w, int* labels
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { set_last_error("cudaStreamSynchronize", e); rc = KMEANS2_ERR_CUDA; break; }
         int iters = 0;
-        e = cudaMemcpy(&iters, &w.st->iter, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) { set_last_error("cudaMemcpy", e); rc = KMEANS2_ERR_CUDA; break; }
+        // stream-ordered read: a legacy-stream copy would wait for every other stream
+        e = cudaMemcpyAsync(&iters, &w.st->iter, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_last_error("cudaMemcpyAsync", e); rc = KMEANS2_ERR_CUDA; break; }
         g_launches += 3ll * (iters > 1 ? iters - 1 : 0);   // body kernels per executed iteration
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
@@ -479,6 +481,7 @@ const char* kmeans2_strerror(int status)
 {
     switch (status) {
         case KMEANS2_OK: return "ok";
+        case KMEANS2_PENDING: return "pending";
         case KMEANS2_ERR_INVALID: return "invalid argument";
         case KMEANS2_ERR_NOMEM: return "out of memory";
         case KMEANS2_ERR_CUDA: return "CUDA error";
@@ -491,6 +494,61 @@ const char* kmeans2_strerror(int status)
 }
 
 const char* kmeans2_last_error(void) { return km2::last_error(); }
+
+uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fraction,
+                               int32_t max_iter, int32_t precision, int32_t x_on_host,
+                               int32_t labels_on_host)
+{
+    if (!valid_shape(n, d, k) || !(subset_fraction > 0.0 && subset_fraction <= 1.0) ||
+        max_iter < 1)
+        return 0;
+    int form = KMEANS2_PRECISION_FP32;
+    const float* aligned = reinterpret_cast<const float*>(static_cast<uintptr_t>(256));
+    if (choose_form(precision, d, k, aligned, &form) != KMEANS2_OK) return 0;
+    const unsigned long long m = (unsigned long long)kmeans2_subset_size(n, k, subset_fraction);
+    const unsigned long long N = (unsigned long long)n, K = (unsigned long long)k,
+                             D = (unsigned long long)d;
+    const unsigned long long kpad = (K + 127) / 128 * 128, dpad = (D + 7) / 8 * 8;
+    const unsigned long long kd = K * D;
+    unsigned long long b = 0;
+    int allocs = 0;
+    auto add = [&](unsigned long long bytes) { b += bytes; ++allocs; };
+    if (x_on_host) add(N * D * 4);
+    // workspace
+    add(kd * 8);
+    add(kd * 4);
+    add(dpad * kpad * 4);
+    add(std::max(kpad, (K + 255) / 256 * 256) * 4);
+    add(kd * 8);
+    add(kd * 8);
+    add(K * 8);
+    add(sizeof(StageState));
+    add(N * 4);
+    add(4 * K * 8);
+    add(2 * (unsigned long long)max_iter * 8);
+    if (form == KMEANS2_PRECISION_BF16) add(bf16_cb_bytes(d, k));
+    if (labels_on_host) add(N * 4);
+    // fast stage: S_s indices, init positions, X_s, its labels
+    add(m * 8);
+    add(K * 8);
+    add(m * D * 4);
+    add(m * 4);
+    // sampling scratch: two radix selects (candidate buffer ~ count / 2048 keys,
+    // per-chunk counts and offsets) and the k selected positions
+    for (unsigned long long cnt : {N, m}) {
+        add(4096 + 2048 * 4);
+        add((2 * cnt / 2048 + 4096) * 8);
+        add((cnt + 4095) / 4096 * 12);
+    }
+    add(K * 8);
+    if (form == KMEANS2_PRECISION_BF16) {
+        add(bf16_xt_bytes((long long)m, d));
+        add(m * 4);
+        add(bf16_xt_bytes(n, d));
+        add(N * 4);
+    }
+    return b + (unsigned long long)allocs * 1024ull + (4ull << 20);
+}
 
 int32_t kmeans2_version(void) { return (1 << 16) | 0; }
 

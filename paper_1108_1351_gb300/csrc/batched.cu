@@ -748,7 +748,8 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         cudaGraphDestroy(graph);
         if (rc == KMEANS2_OK) {
             int iters = 0;
-            KM2_CUDA(cudaMemcpy(&iters, counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
+            KM2_CUDA(cudaMemcpyAsync(&iters, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+            KM2_CUDA(cudaStreamSynchronize(s));
             g_launches += (long long)iters * ((long long)classes.size() + 3);
             // ---- results
             KM2_CUDA(cudaMemcpyAsync(hi.data(), dinst, sizeof(BatchInst) * (size_t)count,

@@ -1,0 +1,322 @@
+// server.cu -- the serving form: a request loop of independent two-stage fits
+// with continuous batching.
+//
+// The server owns W worker threads, each bound to the server's device and to
+// one non-blocking stream of its own.  Jobs wait in arrival order.  A free
+// worker admits the first waiting job whose device footprint fits into the
+// HBM budget next to the jobs already running (a job passed over kMaxBypass
+// times blocks everything behind it, so large jobs are not starved) and runs
+// kmeans2_fit on it: stage loops as graphs with device-side while conditions,
+// the job's data, labels and centers resident from admission to result.
+// Different jobs' kernels therefore overlap on the GPU, and a job that arrives
+// while others run starts as soon as a worker and memory are free -- no batch
+// boundary to wait for.  Every job runs exactly the kernels of a lone
+// kmeans2_fit call (exact fixed-point cluster sums, so sharing the GPU changes
+// no bit of the result).
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace km2 {
+namespace {
+
+constexpr int kMaxSlots = 64;
+constexpr int kMaxBypass = 8;
+
+enum class JobState { Queued, Running, Done };
+
+struct Ticket {
+    kmeans2_job job{};
+    uint64_t footprint = 0;
+    JobState state = JobState::Queued;
+    int status = KMEANS2_PENDING;
+    int bypassed = 0;
+    kmeans2_result res{};
+    kmeans2_ticket_times times{};
+};
+
+bool on_device(const void* p, uintptr_t align)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) &&
+           (reinterpret_cast<uintptr_t>(p) & (align - 1)) == 0;
+}
+
+}  // namespace
+}  // namespace km2
+
+struct kmeans2_server {
+    int device = 0;
+    uint64_t budget = 0;
+    int slots = 0;
+    kmeans2_options opt{};
+    std::chrono::steady_clock::time_point t0;
+
+    std::mutex mu;
+    std::condition_variable cv_work;   // workers: a job arrived, memory was freed, or stop
+    std::condition_variable cv_done;   // waiters: a job finished
+    std::deque<uint64_t> queue;        // waiting tickets, arrival order
+    std::unordered_map<uint64_t, km2::Ticket> tickets;
+    uint64_t next_ticket = 1;
+    uint64_t in_use = 0, peak = 0;
+    int running = 0;
+    int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rejected = 0, launches = 0;
+    bool stop = false;
+
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+
+    // Under mu: the ticket a free worker should start, or 0.
+    uint64_t pick()
+    {
+        for (size_t i = 0; i < queue.size(); ++i) {
+            km2::Ticket& t = tickets[queue[i]];
+            if (in_use + t.footprint <= budget) {
+                const uint64_t id = queue[i];
+                for (size_t j = 0; j < i; ++j) tickets[queue[j]].bypassed += 1;
+                queue.erase(queue.begin() + (long)i);
+                return id;
+            }
+            if (t.bypassed >= km2::kMaxBypass) break;   // nothing may pass it any more
+        }
+        return 0;
+    }
+
+    void work(int slot)
+    {
+        cudaSetDevice(device);
+        for (;;) {
+            uint64_t id = 0;
+            kmeans2_job job{};
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait(lk, [&] {
+                    if (stop) return true;
+                    id = pick();
+                    return id != 0;
+                });
+                if (stop) {
+                    if (id) {   // picked in the same wake-up as the stop: give it back as cancelled
+                        km2::Ticket& t = tickets[id];
+                        t.state = km2::JobState::Done;
+                        t.status = KMEANS2_ERR_ADMISSION;
+                        t.times.t_done = now();
+                        ++failed;
+                        cv_done.notify_all();
+                    }
+                    return;
+                }
+                km2::Ticket& t = tickets[id];
+                t.state = km2::JobState::Running;
+                t.times.t_admit = now();
+                in_use += t.footprint;
+                if (in_use > peak) peak = in_use;
+                ++running;
+                ++admitted;
+                job = t.job;
+            }
+            kmeans2_options o = opt;
+            o.stream = streams[slot];
+            kmeans2_result r;
+            std::memset(&r, 0, sizeof(r));
+            const long long l0 = km2::g_launches;
+            const int rc = kmeans2_fit(job.X, job.n, job.d, job.k, job.subset_fraction, job.seed,
+                                       job.tol, job.max_iter, job.centers_out, job.labels_out,
+                                       &r, &o);
+            const long long dl = km2::g_launches - l0;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                km2::Ticket& t = tickets[id];
+                t.state = km2::JobState::Done;
+                t.status = rc;
+                t.res = r;
+                t.times.t_done = now();
+                in_use -= t.footprint;
+                --running;
+                if (rc == KMEANS2_OK) ++completed; else ++failed;
+                launches += dl;
+            }
+            cv_work.notify_all();
+            cv_done.notify_all();
+        }
+    }
+
+    // Under mu: the status of a finished ticket (and release it), or PENDING.
+    int take(uint64_t id, kmeans2_result* res, kmeans2_ticket_times* times)
+    {
+        auto it = tickets.find(id);
+        if (it == tickets.end()) return KMEANS2_ERR_INVALID;
+        if (it->second.state != km2::JobState::Done) return KMEANS2_PENDING;
+        const int st = it->second.status;
+        if (res) *res = it->second.res;
+        if (times) *times = it->second.times;
+        tickets.erase(it);
+        return st;
+    }
+};
+
+extern "C" {
+
+kmeans2_server* kmeans2_server_create(uint64_t hbm_budget, int32_t max_slots,
+                                      const kmeans2_options* opt)
+{
+    if (max_slots < 1 || max_slots > km2::kMaxSlots) return nullptr;
+    kmeans2_options o;
+    kmeans2_default_options(&o);
+    if (opt) o = *opt;
+    if (o.stream || o.init_centers || o.start_stage != 0 || o.profile || o.traj_J_fast ||
+        o.traj_shift_fast || o.traj_J_slow || o.traj_shift_slow)
+        return nullptr;
+    o.use_graph = 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (hbm_budget == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return nullptr;
+        hbm_budget = (uint64_t)((double)free_b * 0.9);
+    }
+    auto* s = new kmeans2_server();
+    s->device = dev;
+    s->budget = hbm_budget;
+    s->slots = max_slots;
+    s->opt = o;
+    s->t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < max_slots; ++i) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            return nullptr;
+        }
+        s->streams.push_back(st);
+    }
+    for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s, i] { s->work(i); });
+    return s;
+}
+
+int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t* ticket)
+{
+    if (!srv || !job || !ticket) return KMEANS2_ERR_INVALID;
+    const kmeans2_job& J = *job;
+    if (!J.X || !J.centers_out || !J.labels_out || J.reserved != 0 || J.n < 1 || J.d < 1 ||
+        J.k < 1 || J.k > J.n || !(J.subset_fraction > 0.0 && J.subset_fraction <= 1.0) ||
+        !(J.tol >= 0.0) || J.max_iter < 1) {
+        km2::set_last_error_text("kmeans2_server_submit: job out of range");
+        return KMEANS2_ERR_INVALID;
+    }
+    const bool x_dev = km2::on_device(J.X, 16);
+    const bool lab_dev = km2::on_device(J.labels_out, 4);
+    uint64_t fp = kmeans2_fit_footprint(J.n, J.d, J.k, J.subset_fraction, J.max_iter,
+                                        srv->opt.precision, x_dev ? 0 : 1, lab_dev ? 0 : 1);
+    if (fp == 0) {
+        km2::set_last_error_text("kmeans2_server_submit: shape or precision not supported");
+        return KMEANS2_ERR_INVALID;
+    }
+    if (x_dev) fp += (uint64_t)J.n * (uint64_t)J.d * 4;   // resident data counts against the budget
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stop) return KMEANS2_ERR_ADMISSION;
+    if (fp > srv->budget) {
+        ++srv->rejected;
+        km2::set_last_error_text("kmeans2_server_submit: job footprint exceeds the HBM budget");
+        return KMEANS2_ERR_ADMISSION;
+    }
+    const uint64_t id = srv->next_ticket++;
+    km2::Ticket& t = srv->tickets[id];
+    t.job = J;
+    t.footprint = fp;
+    t.times.t_submit = srv->now();
+    srv->queue.push_back(id);
+    ++srv->submitted;
+    *ticket = id;
+    srv->cv_work.notify_all();
+    return KMEANS2_OK;
+}
+
+int kmeans2_server_poll(kmeans2_server* srv, uint64_t ticket, kmeans2_result* res,
+                        kmeans2_ticket_times* times)
+{
+    if (!srv) return KMEANS2_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    return srv->take(ticket, res, times);
+}
+
+int kmeans2_server_wait(kmeans2_server* srv, uint64_t ticket, double timeout_s,
+                        kmeans2_result* res, kmeans2_ticket_times* times)
+{
+    if (!srv) return KMEANS2_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto ready = [&] {
+        auto it = srv->tickets.find(ticket);
+        return it == srv->tickets.end() || it->second.state == km2::JobState::Done;
+    };
+    if (timeout_s < 0)
+        srv->cv_done.wait(lk, ready);
+    else
+        srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+    return srv->take(ticket, res, times);
+}
+
+int kmeans2_server_stats_get(kmeans2_server* srv, kmeans2_server_stats* out)
+{
+    if (!srv || !out) return KMEANS2_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = srv->submitted;
+    out->admitted = srv->admitted;
+    out->completed = srv->completed;
+    out->failed = srv->failed;
+    out->rejected = srv->rejected;
+    out->kernel_launches = srv->launches;
+    out->queued = (int32_t)srv->queue.size();
+    out->running = srv->running;
+    out->slots = srv->slots;
+    out->hbm_budget = srv->budget;
+    out->hbm_in_use = srv->in_use;
+    out->hbm_peak = srv->peak;
+    return KMEANS2_OK;
+}
+
+double kmeans2_server_now(kmeans2_server* srv) { return srv ? srv->now() : 0.0; }
+
+void kmeans2_server_destroy(kmeans2_server* srv)
+{
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        for (uint64_t id : srv->queue) {
+            km2::Ticket& t = srv->tickets[id];
+            t.state = km2::JobState::Done;
+            t.status = KMEANS2_ERR_ADMISSION;
+            t.times.t_done = srv->now();
+            ++srv->failed;
+        }
+        srv->queue.clear();
+    }
+    srv->cv_work.notify_all();
+    srv->cv_done.notify_all();
+    for (std::thread& w : srv->workers) w.join();
+    for (cudaStream_t s : srv->streams) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    delete srv;
+}
+
+}  // extern "C"

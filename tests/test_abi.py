@@ -75,3 +75,43 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert lib.kmeans_step(p, 8, 2, 9, C.ctypes.data, C.ctypes.data, lab.ctypes.data,
                            None, None, None, None) == -1
     assert lib.kmeans2_sample(8, 9, 0.5, 0, lab.ctypes.data, lab.ctypes.data, None) == -1
+
+
+def test_fit_footprint_host_arithmetic(lib):
+    # device bytes of the buffers kmeans2_fit allocates: grows with n, d and k;
+    # host-side X / labels add their staged copies; the BF16 form adds its copies
+    base = km.footprint(1_000_000, 16, 64, 0.1, 50, precision="fp32")
+    assert base > 1_000_000 * 4 * 2          # labels of S_n + recheck list at least
+    assert km.footprint(2_000_000, 16, 64, 0.1, 50, precision="fp32") > base
+    assert km.footprint(1_000_000, 32, 64, 0.1, 50, precision="fp32") > base
+    assert km.footprint(1_000_000, 16, 512, 0.1, 50, precision="fp32") > base
+    host_x = km.footprint(1_000_000, 16, 64, 0.1, 50, precision="fp32", x_on_host=True)
+    assert host_x - base == 1_000_000 * 16 * 4 + 1024
+    host_l = km.footprint(1_000_000, 16, 64, 0.1, 50, precision="fp32", labels_on_host=True)
+    assert host_l - base == 1_000_000 * 4 + 1024
+    f32 = km.footprint(1_000_000, 128, 1024, 0.1, 50, precision="fp32")
+    b16 = km.footprint(1_000_000, 128, 1024, 0.1, 50, precision="bf16")
+    assert b16 - f32 >= 2 * 1_100_000 * 128 * 2      # hi + lo BF16 copies of S_n and S_s
+    assert km.footprint(1_000_000, 128, 1024, 0.1, 50, precision="auto") == b16
+    assert km.footprint(1_000_000, 8, 32, 0.1, 50, precision="auto") == \
+        km.footprint(1_000_000, 8, 32, 0.1, 50, precision="fp32")
+    # invalid shapes and unsupported forms give 0
+    assert km.footprint(10, 2, 11, 0.1, 50) == 0
+    assert km.footprint(10, 2, 2, 0.0, 50) == 0
+    assert km.footprint(10, 2, 2, 0.5, 0) == 0
+    assert km.footprint(1000, 24, 8, 0.5, 10, precision="bf16") == 0
+
+
+def test_server_create_without_device_or_bad_args(lib):
+    o = binding.Options()
+    lib.kmeans2_default_options(ctypes.byref(o))
+    assert not lib.kmeans2_server_create(1 << 30, 0, ctypes.byref(o))
+    assert not lib.kmeans2_server_create(1 << 30, 65, ctypes.byref(o))
+    o.start_stage = 1
+    assert not lib.kmeans2_server_create(1 << 30, 2, ctypes.byref(o))
+    st = binding.ServerStats()
+    assert lib.kmeans2_server_stats_get(None, ctypes.byref(st)) == -1
+    assert lib.kmeans2_server_poll(None, 1, None, None) == -1
+    assert lib.kmeans2_server_now(None) == 0.0
+    lib.kmeans2_server_destroy(None)
+    assert km.strerror(1) == "pending"
