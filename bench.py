@@ -414,6 +414,7 @@ def _serve_trace(trace, srv, dev, stream, *, drain_cap: float, data_cap_bytes: i
     outstanding = {}            # ticket -> (job spec, scheduled arrival, bytes)
     lock = threading.Lock()
     state = {"bytes": 0, "submitted": 0, "late": 0.0, "error": None}
+    stop = threading.Event()
     start = srv.now() + 0.5
 
     def client():
@@ -421,13 +422,15 @@ def _serve_trace(trace, srv, dev, stream, *, drain_cap: float, data_cap_bytes: i
             with torch.cuda.device(dev), torch.cuda.stream(stream):
                 for js in trace:
                     t_sched = start + js.t_arrival
-                    while True:
+                    while not stop.is_set():
                         with lock:
                             room = state["bytes"] + js.n * js.d * 4 <= data_cap_bytes or not outstanding
                         now = srv.now()
                         if room and now >= t_sched:
                             break
                         time.sleep(min(0.002, max(0.0, t_sched - now)) if room else 0.002)
+                    if stop.is_set():
+                        return
                     state["late"] = max(state["late"], srv.now() - t_sched)
                     X = synth.iso_gaussian_mixture(js.n, js.d, js.k, js.seed, lo=-20.0, hi=20.0,
                                                    device=dev)
@@ -464,7 +467,8 @@ def _serve_trace(trace, srv, dev, stream, *, drain_cap: float, data_cap_bytes: i
             break
         time.sleep(0.001)
     t_end = srv.now()
-    th.join(timeout=drain_cap + 60)
+    stop.set()
+    th.join(timeout=120)
     censored = []
     with lock:
         for t, (js, t_sched, b) in outstanding.items():
@@ -516,14 +520,16 @@ def run_serve(args):
     clocks = ClockSampler(None)
     clocks.start()
     out = {}
-    for name, slots, prec in (("served", args.serve_slots, "auto"),
-                              ("one_at_a_time_fp32", 1, "fp32")):
-        with km.Server(hbm_budget=budget, max_slots=slots, precision=prec) as srv:
+    for name, slots, prec, policy in (("served", args.serve_slots, "auto", "shortest"),
+                                      ("one_at_a_time_fp32", 1, "fp32", "fifo")):
+        with km.Server(hbm_budget=budget, max_slots=slots, precision=prec, policy=policy,
+                       aging_s=args.aging) as srv:
             done, censored, never, start, t_end, late = _serve_trace(
                 trace, srv, dev, stream, drain_cap=args.drain_cap, data_cap_bytes=data_cap)
             summ = _latency_summary(done, censored, never, start, t_end)
             st = srv.stats()
-        summ.update({"slots": slots, "precision": prec, "kernel_launches": st["kernel_launches"],
+        summ.update({"slots": slots, "precision": prec, "policy": policy,
+                     "kernel_launches": st["kernel_launches"],
                      "hbm_peak_gb": st["hbm_peak"] / 1e9, "client_max_lag_s": late})
         out[name] = summ
     clk = clocks.stop()
@@ -549,15 +555,103 @@ def run_serve(args):
     return 0
 
 
+BATCH = dict(count=4096, seed=0, f=0.1, tol=1e-6, max_iter=100)
+
+
+def run_batched(args):
+    """Batched workload: many independent instances (n log-uniform in [1e3,
+    1e6], d in {2, 8, 32, 64}, k uniform in [2, 256], Gaussian mixtures with
+    means U[-20, 20]^d) fitted by one kmeans2_fit_batched call, and the same
+    instances fitted one kmeans2_fit call at a time (FP32 form) as the
+    baseline; a sample of instances is checked bit for bit between the two."""
+    import numpy as np
+    import torch
+    import paper_1108_1351_gb300 as km
+    from paper_1108_1351_gb300 import synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.load()
+    specs = synth.instance_specs(args.instances, seed=BATCH["seed"] + rank * args.instances)
+    Xs = [synth.instance_data(s, device=dev) for s in specs]
+    torch.cuda.synchronize()
+    ks = [s.k for s in specs]
+    seeds = [s.seed for s in specs]
+    stream = torch.cuda.current_stream(dev)
+
+    prof = km.Profile()
+
+    def batched(profile=None):
+        return km.fit_batched(Xs, ks, BATCH["f"], seeds, BATCH["tol"], BATCH["max_iter"],
+                              stream=stream, profile=profile)[0]
+
+    for _ in range(args.warmup):
+        res = batched()
+    clocks = ClockSampler(None)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = batched(prof)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    evals = sum(r.distance_evals for r in res)
+    launches = int(prof.kernel_launches)
+    # baseline: the same instances, one kmeans2_fit at a time (plain FP32 form)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    singles = [km.fit(X, k, BATCH["f"], sd, BATCH["tol"], BATCH["max_iter"], precision="fp32",
+                      stream=stream) for X, k, sd in zip(Xs, ks, seeds)]
+    torch.cuda.synchronize()
+    ms_single = 1e3 * (time.perf_counter() - t0)
+    rng = np.random.default_rng(1)
+    sample = rng.choice(len(specs), size=min(64, len(specs)), replace=False)
+    same = all(torch.equal(res[i].labels, singles[i].labels) and res[i].J == singles[i].J and
+               (res[i].iters_fast, res[i].iters_slow) == (singles[i].iters_fast, singles[i].iters_slow)
+               for i in sample)
+    ms_max, total_evals = reduce_over_ranks(ms, evals, ws, dev)
+    if rank != 0:
+        return 0
+    npts = sum(s.n for s in specs)
+    line = {
+        "metric": METRIC, "value": total_evals / (ms_max * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched", "instances": len(specs), "points": npts,
+                   "n": "log-U[1e3, 1e6]", "d": [2, 8, 32, 64], "k": "U[2, 256]",
+                   "subset_fraction": BATCH["f"], "tol": BATCH["tol"],
+                   "max_iter": BATCH["max_iter"],
+                   "l2": "inputs larger than L2 (%.1f GB)" % (sum(s.n * s.d for s in specs) * 4e-9)},
+        "time_to_converge_s": ms_max / 1e3,
+        "one_at_a_time_fp32": {"time_to_converge_s": ms_single / 1e3,
+                               "value": sum(r.distance_evals for r in singles) / (ms_single * 1e-3),
+                               "speedup_of_batched": ms_single / ms_max},
+        "sampled_instances_identical": bool(same), "sampled": int(len(sample)),
+        "gpu_launches": launches, "roofline": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="aniso8", choices=sorted(CONFIGS) + ["serve"])
+    ap.add_argument("--config", default="aniso8", choices=sorted(CONFIGS) + ["serve", "batched"])
+    ap.add_argument("--instances", type=int, default=BATCH["count"],
+                    help="batched: number of independent instances")
     ap.add_argument("--duration", type=float, default=SERVE["duration"],
                     help="serve: seconds of Poisson arrivals")
     ap.add_argument("--serve-slots", type=int, default=8, help="serve: jobs running at once")
+    ap.add_argument("--aging", type=float, default=30.0,
+                    help="serve: seconds after which a waiting job is admitted before smaller ones")
     ap.add_argument("--drain-cap", type=float, default=120.0,
                     help="serve: seconds after the last arrival before unfinished jobs are censored")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -567,6 +661,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
+    if args.config == "batched":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload's "
+                              "baseline is the one-at-a-time FP32 form in the same line"}))
+            return 0
+        return run_batched(args)
     if args.config == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no "

@@ -291,6 +291,19 @@ KMEANS2_API int kmeans2_server_wait(kmeans2_server* srv, uint64_t ticket, double
 /* Counters of the server; returns KMEANS2_ERR_INVALID for NULL arguments. */
 KMEANS2_API int kmeans2_server_stats_get(kmeans2_server* srv, kmeans2_server_stats* out);
 
+/*
+ * kmeans2_server_set_policy -- which waiting job a free worker admits.
+ *  KMEANS2_POLICY_FIFO (default): the first job in arrival order that fits the
+ *      budget; a job passed over 8 times blocks everything behind it.
+ *  KMEANS2_POLICY_SHORTEST: the fitting job with the least work per iteration
+ *      (n * k * d), except that the oldest job goes first once it has waited
+ *      aging_s seconds (and nothing else is admitted until it fits).
+ * Errors: KMEANS2_ERR_INVALID (NULL server, unknown policy, aging_s < 0).
+ */
+#define KMEANS2_POLICY_FIFO 0
+#define KMEANS2_POLICY_SHORTEST 1
+KMEANS2_API int kmeans2_server_set_policy(kmeans2_server* srv, int32_t policy, double aging_s);
+
 /* Seconds since the server was created (its clock for kmeans2_ticket_times). */
 KMEANS2_API double kmeans2_server_now(kmeans2_server* srv);
 

@@ -159,6 +159,8 @@ def load():
                                             ctypes.POINTER(TicketTimes)]
         lib.kmeans2_server_stats_get.restype = ctypes.c_int
         lib.kmeans2_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
+        lib.kmeans2_server_set_policy.restype = ctypes.c_int
+        lib.kmeans2_server_set_policy.argtypes = [P, i32, f64]
         lib.kmeans2_server_now.restype = f64
         lib.kmeans2_server_now.argtypes = [P]
         lib.kmeans2_server_destroy.restype = None
@@ -356,8 +358,11 @@ class Server:
     return a ``Served`` once the job has finished.  The server holds references
     to each job's tensors until the job has been collected."""
 
+    POLICY = {"fifo": 0, "shortest": 1}
+
     def __init__(self, hbm_budget: int = 0, max_slots: int = 4, *, precision: str = "auto",
-                 tol_fast: float = 0.0, device=None):
+                 tol_fast: float = 0.0, policy: str = "fifo", aging_s: float = 30.0,
+                 device=None):
         lib = load()
         opt = Options()
         lib.kmeans2_default_options(ctypes.byref(opt))
@@ -370,6 +375,11 @@ class Server:
             self._h = lib.kmeans2_server_create(int(hbm_budget), int(max_slots), ctypes.byref(opt))
         if not self._h:
             raise KMeans2Error(-1, "kmeans2_server_create")
+        rc = lib.kmeans2_server_set_policy(self._h, self.POLICY[policy], float(aging_s))
+        if rc != 0:
+            lib.kmeans2_server_destroy(self._h)
+            self._h = None
+            raise KMeans2Error(rc, "kmeans2_server_set_policy")
         self._refs: dict[int, tuple] = {}
         self._mu = threading.Lock()
 
@@ -443,7 +453,7 @@ class Server:
 
 
 def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: float = 0.0,
-                stream=None, raise_on_error: bool = True):
+                stream=None, raise_on_error: bool = True, profile: "Profile | None" = None):
     """Batched two-stage fits (kmeans2_fit_batched) of independent problems.
 
     Xs: list of 2-D float32 CUDA tensors; ks, seeds: per-job lists; the other
@@ -475,6 +485,7 @@ def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: floa
     opt.precision = PRECISION["fp32"]
     opt.tol_fast = tol_fast
     opt.stream = _stream_of(Xs[0], stream)
+    opt.profile = ctypes.addressof(profile) if profile is not None else None
     with _device_of(Xs[0]):
         rc = lib.kmeans2_fit_batched(cnt, jobs, res, ctypes.byref(opt))
     if rc != 0 and raise_on_error:

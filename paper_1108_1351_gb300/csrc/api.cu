@@ -9,6 +9,7 @@
 // body of a CUDA-graph WHILE node whose condition finalize sets on the device,
 // so a whole stage is one graph launch with no host round trip per iteration.
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -165,7 +166,9 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     KM2_TRY(ws.alloc((void**)&w.traj_J, (size_t)max_iter * sizeof(double), s));
     KM2_TRY(ws.alloc((void**)&w.traj_shift, (size_t)max_iter * sizeof(double), s));
     KM2_CUDA(cudaMemsetAsync(w.c.c32t, 0, (size_t)w.c.dpad * w.c.kpad * sizeof(float), s));
-    KM2_TRY(fill_f32(w.c.cnorm, cn_len, INFINITY, s));
+    // padding centers: the largest finite key, so that packing an index into
+    // its low mantissa bits never makes a NaN and it never wins or ties
+    KM2_TRY(fill_f32(w.c.cnorm, cn_len, FLT_MAX, s));
     if (w.form == KMEANS2_PRECISION_BF16)
         KM2_TRY(ws.alloc((void**)&w.cb, bf16_cb_bytes(d, k), s));
     return KMEANS2_OK;

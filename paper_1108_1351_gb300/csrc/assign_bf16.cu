@@ -4,27 +4,33 @@
 // x = xh + xl (xh = bf16(x), xl = bf16(x - xh)) and m = -2c = mh + ml, and
 // three MMAs per K-step accumulate xh.mh + xh.ml + xl.mh: the error drops from
 // 2^-7 |x||c| for plain BF16 to about 2^-15 |x||c| at the price of two extra
-// MMAs, which the epilogue-bound kernel hides.  A near tie under the bound is
-// re-decided from the FP32 master data in FP64 (recheck_kernel), so the labels
-// are the same as in every other form.
+// MMAs.  A near tie under the bound is re-decided from the FP32 master data in
+// FP64 (recheck_kernel), so the labels are the same as in every other form.
 //
 // Data layout (global, rebuilt per stage / per iteration):
 //   Xt : one contiguous block per 128-point tile: the xh tile then the xl
 //        tile, each d/16 K-steps of 4 KB in the K-major core-matrix layout
 //        (tc_common.cuh);
 //   xn2: FP32 ||x||^2 per point (for the error bound);
-//   Cb : one contiguous block per chunk of NC centers: the mh then the ml
-//        chunk, each d/16 K-steps of NC * 32 bytes.
-// One CTA per SM (256 threads).  Thread 0 streams A tiles and B chunks with
-// 1-D bulk TMA copies into double-buffered shared memory and issues d/16 MMAs
-// (M = 128, N = NC, K = 16) per (tile, chunk) into one of two TMEM
-// accumulators; all 8 warps run the epilogue of the previous unit meanwhile:
-// warp w reads TMEM lanes 32 (w % 4) .. +31, columns of half w / 4 of the
-// chunk, adds ||c||^2 and keeps a packed-key top-2 per row.  At a tile's last
-// chunk the two halves are merged through shared memory and warps 0-3 decide
-// each row: near-tie flag, label, exact fixed-point cluster sums.  Every
-// mbarrier wait is bounded; on timeout the CTA records an error, waits
-// (bounded) for its own copies and MMAs, frees TMEM and exits.
+//   Cb : one contiguous slice per (chunk of NC centers, K-step): the mh then
+//        the ml part, NC * 32 bytes each.
+//
+// Warp-specialised pipeline, one CTA per SM, 11 warps:
+//   warp 0  A producer: one bulk TMA copy per tile into a 2-stage ring;
+//   warp 1  B producer: one bulk TMA copy per (chunk, K-step) slice into an
+//           SB-stage ring (SB <= 8);
+//   warp 2  MMA issuer: per (tile, chunk) unit, 3 MMAs (M 128, N NC, K 16) per
+//           K-step into a TMEM accumulator; tcgen05.commit frees each slice,
+//           each tile and hands the accumulator to the epilogue;
+//   warps 3-6, 7-10  two epilogue groups taking alternate tiles, each with its
+//           own two TMEM accumulators (4 x NC columns in all): a thread owns
+//           one row (TMEM lane) of the tile, adds ||c||^2, keeps a packed-key
+//           top-2 across the chunks and decides the row (near-tie flag, label,
+//           exact fixed-point cluster sums).
+// Roles are coupled only by mbarriers (full / empty per ring slot and per
+// accumulator), so copies, MMAs and epilogues of different units overlap.
+// Every wait is bounded; on timeout the CTA records an error, each role lets
+// its own copies or MMAs finish (bounded), TMEM is freed and the CTA exits.
 #include <cfloat>
 #include <cstdint>
 
@@ -37,8 +43,13 @@ namespace km2 {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kEpiGroups = 2;
+constexpr int kEpiWarps = 4 * kEpiGroups;
+constexpr int kThreads = 32 * (3 + kEpiWarps);
 constexpr int kRows = 128;
+constexpr int kSA = 2;                 // A ring depth (tiles)
+constexpr int kMaxSB = 8;              // B ring depth (slices)
+constexpr int kSmemBudget = 220 * 1024;
 constexpr int kWaitTries = 1 << 22;
 
 __device__ __forceinline__ float pack_key(float v, unsigned j)
@@ -51,6 +62,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(mbar)),
                  "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(mbar))
                  : "memory");
 }
 
@@ -69,46 +87,80 @@ struct Bf16Args {
     const float* X;          // FP32 master rows (sums, ||x||^2 in full mode)
     const unsigned char* Xt; // BF16 tiles
     const float* xn2;        // FP32 ||x||^2 per point
-    const unsigned char* Cb; // BF16 -2c chunks
+    const unsigned char* Cb; // BF16 -2c slices
     long long n;
-    int d, k, nc, nch;       // chunk width NC and chunk count
+    int d, k, nc, nch, sb;   // chunk width NC, chunk count, B ring depth
     uint32_t tmem_cols;
     float kappa, kpack;
 };
+
+struct Bars {
+    uint64_t a_full[kSA], a_empty[kSA];
+    uint64_t b_full[kMaxSB], b_empty[kMaxSB];
+    uint64_t acc_full[2 * kEpiGroups], acc_empty[2 * kEpiGroups];
+    uint64_t drain;
+};
+
+// Bounded wait for the phase of `parity`; gives up early once another role
+// has aborted.  On its own timeout it raises the abort flag and the error.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                         StageState* st)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < kWaitTries; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 63) == 63 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(&st->error, kErrTimeout);
+    return false;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
 assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Accum acc,
             int* __restrict__ list)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t barA[2], barB[2], barM[2];
+    __shared__ Bars bars;
     __shared__ uint32_t tmem_base;
-    __shared__ float xb1[kRows], xb2[kRows];
-    __shared__ int xbi[kRows];
+    __shared__ int abort_flag;
 
     if (st->error) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int d = a.d, NC = a.nc, nch = a.nch;
-    const uint32_t Ahalf = (uint32_t)kRows * (uint32_t)d * 2u;   // one part of a tile
-    const uint32_t Bhalf = (uint32_t)NC * (uint32_t)d * 2u;      // one part of a chunk
-    const uint32_t Abytes = 2u * Ahalf, Bbytes = 2u * Bhalf;
-    unsigned char* sA = smem;                        // 2 stages x (xh, xl)
-    unsigned char* sB = smem + 2 * Abytes;           // 2 stages x (mh, ml)
+    const int d = a.d, NC = a.nc, nch = a.nch, SB = a.sb;
+    const int ksteps = d / 16;
+    const uint32_t Ahalf = (uint32_t)ksteps * 4096u;             // one part of a tile
+    const uint32_t Abytes = 2u * Ahalf;
+    const uint32_t Sbytes = (uint32_t)NC * 64u;                  // one (chunk, K-step) slice
+    unsigned char* sA = smem;                                    // kSA x Abytes
+    unsigned char* sB = smem + kSA * Abytes;                     // SB x Sbytes
     const uint32_t sAaddr = (uint32_t)__cvta_generic_to_shared(sA);
     const uint32_t sBaddr = (uint32_t)__cvta_generic_to_shared(sB);
-    const int mode = st->mode;
-    const float scaleF = st->scaleF, scaleG = st->scaleG;
-    const float thr_base = 2.0f * st->cmax2;
-    const uint32_t idesc = tc::instr_desc(1u, (uint32_t)NC, (uint32_t)kRows);
-    const int ksteps = d / 16;
+    volatile int* abort_v = &abort_flag;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+    if (warp == 2) tc::tmem_alloc(&tmem_base, a.tmem_cols);
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(&barA[s], 1);
-            tc::mbar_init(&barB[s], 1);
-            tc::mbar_init(&barM[s], 1);
+        for (int s = 0; s < kSA; ++s) {
+            tc::mbar_init(&bars.a_full[s], 1);
+            tc::mbar_init(&bars.a_empty[s], 1);
         }
+        for (int s = 0; s < kMaxSB; ++s) {
+            tc::mbar_init(&bars.b_full[s], 1);
+            tc::mbar_init(&bars.b_empty[s], 1);
+        }
+        for (int b = 0; b < 2 * kEpiGroups; ++b) {
+            tc::mbar_init(&bars.acc_full[b], 1);
+            tc::mbar_init(&bars.acc_empty[b], 4);   // the 4 warps of the owning group
+        }
+        tc::mbar_init(&bars.drain, 1);
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
@@ -119,185 +171,191 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     const long long ntiles = (a.n + kRows - 1) / kRows;
     const long long cnt = (long long)blockIdx.x < ntiles
                               ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    const long long U = cnt * nch;
 
-    auto issue_loads = [&](long long u) {
-        const long long i = u / nch;
-        const int ch = (int)(u % nch);
-        const long long tile = blockIdx.x + i * gridDim.x;
-        if (ch == 0) {
-            const int sa = (int)(i & 1);
-            mbar_expect_tx(&barA[sa], Abytes);
-            bulk_load(sA + (size_t)sa * Abytes, a.Xt + (size_t)tile * Abytes, Abytes, &barA[sa]);
-        }
-        const int sb = (int)(u & 1);
-        mbar_expect_tx(&barB[sb], Bbytes);
-        bulk_load(sB + (size_t)sb * Bbytes, a.Cb + (size_t)ch * Bbytes, Bbytes, &barB[sb]);
-    };
-    // returns false on a timed-out wait
-    auto issue_mma = [&](long long u) -> bool {
-        const long long i = u / nch;
-        const int sa = (int)(i & 1), sb = (int)(u & 1);
-        if (!tc::mbar_wait(&barA[sa], (uint32_t)((i >> 1) & 1), kWaitTries)) return false;
-        if (!tc::mbar_wait(&barB[sb], (uint32_t)((u >> 1) & 1), kWaitTries)) return false;
-        tc::fence_after_sync();
-        const uint32_t dt = tmem + (uint32_t)(sb * NC);
-        for (int s = 0; s < ksteps; ++s) {
-            const uint32_t ah = sAaddr + (uint32_t)sa * Abytes + (uint32_t)s * 4096u;
-            const uint32_t bh = sBaddr + (uint32_t)sb * Bbytes + (uint32_t)(s * NC * 32);
-            tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, s > 0 ? 1u : 0u);
-            tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh + Bhalf), idesc, 1u);
-            tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
-        }
-        tc::mma_commit(&barM[sb]);
-        return true;
-    };
-
-    bool ok = true;
-    bool next_issued = false;        // thread 0: MMA of unit u + 1 issued
-    if (tid == 0 && U > 0) {
-        issue_loads(0);
-        if (U > 1) issue_loads(1);
-        ok = issue_mma(0);
-    }
-    // per-row running top-2 across the chunks of the current tile
-    float B1 = INFINITY, B2 = INFINITY;
-    int BI = 0;
-    const int half = warp >> 2;                 // which half of each chunk's columns
-    const int row = 32 * (warp & 3) + lane;     // TMEM lane = tile row
-    long long qloc = 0;
-    long long u = 0;
-    for (; u < U; ++u) {
-        next_issued = false;
-        if (tid == 0 && ok && u + 1 < U) {
-            ok = issue_mma(u + 1);
-            next_issued = ok;
-        }
-        const int sb = (int)(u & 1);
-        bool mine = ok && tc::mbar_wait(&barM[sb], (uint32_t)((u >> 1) & 1), kWaitTries);
-        if (!__syncthreads_and(mine)) break;
-        tc::fence_after_sync();
-        if (tid == 0 && u + 2 < U) issue_loads(u + 2);
-
-        const long long i = u / nch;
-        const int ch = (int)(u % nch);
-        // ---- epilogue of unit u: my half of the chunk's NC columns
-        const int cols = NC / 2;
-        for (int c0 = 0; c0 < cols; c0 += 32) {
-            float v[32];
-            const int col = half * cols + c0;          // column within the chunk
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(sb * NC + col), v);
-            const int j0 = ch * NC + col;              // center index of v[0]
-            const float4* cn4 = reinterpret_cast<const float4*>(c.cnorm + j0);
-            float q1[4], q2[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const float4 cn = __ldg(cn4 + g);
-                const float w0 = v[4 * g] + cn.x, w1 = v[4 * g + 1] + cn.y;
-                const float w2 = v[4 * g + 2] + cn.z, w3 = v[4 * g + 3] + cn.w;
-                const int q = g & 3;
-                {
-                    const float k0 = pack_key(w0, 4u * g), k1 = pack_key(w1, 4u * g + 1u);
-                    const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                    q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
-                    q1[q] = fminf(q1[q], lo);
-                }
-                {
-                    const float k0 = pack_key(w2, 4u * g + 2u), k1 = pack_key(w3, 4u * g + 3u);
-                    const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                    q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
-                    q1[q] = fminf(q1[q], lo);
-                }
+    if (warp == 0) {
+        // ---------------- A producer: tile i -> stage i % 2
+        if (lane == 0) {
+            long long issued = 0;
+            for (long long i = 0; i < cnt; ++i) {
+                const int s = (int)(i & 1);
+                if (!wait_bar(&bars.a_empty[s], (uint32_t)(((i >> 1) & 1) ^ 1), abort_v, st)) break;
+                const long long tile = blockIdx.x + i * gridDim.x;
+                mbar_expect_tx(&bars.a_full[s], Abytes);
+                bulk_load(sA + (size_t)s * Abytes, a.Xt + (size_t)tile * Abytes, Abytes,
+                          &bars.a_full[s]);
+                issued = i + 1;
             }
-            const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
-            const float l01 = fminf(q1[0], q1[1]);
-            const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
-            const float l23 = fminf(q1[2], q1[3]);
-            const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
-            const float b1 = fminf(l01, l23);
-            if (b1 < B1) {
-                B2 = fminf(B1, b2);
-                B1 = b1;
-                BI = j0 + (int)(__float_as_uint(b1) & 31u);
-            } else {
-                B2 = fminf(B2, b1);
-            }
+            // let this CTA's own copies land before it can exit
+            for (long long i = issued > kSA ? issued - kSA : 0; i < issued; ++i)
+                tc::mbar_wait(&bars.a_full[i & 1], (uint32_t)((i >> 1) & 1), kWaitTries);
         }
-        tc::fence_before_sync();
-        if (ch == nch - 1) {
-            // merge the two halves of each row, then warps 0-3 decide the row
-            if (half == 1) { xb1[row] = B1; xb2[row] = B2; xbi[row] = BI; }
-            __syncthreads();
-            if (half == 0) {
-                const float o1 = xb1[row], o2 = xb2[row];
-                const int oi = xbi[row];
-                if (o1 < B1 || (o1 == B1 && oi < BI)) {
-                    B2 = fminf(B1, o2);
-                    B1 = o1;
-                    BI = oi;
-                } else {
-                    B2 = fminf(B2, o1);
+    } else if (warp == 1) {
+        // ---------------- B producer: slice q = (unit, K-step) -> stage q % SB
+        if (lane == 0) {
+            const long long total = cnt * nch * ksteps;
+            long long q = 0;
+            for (; q < total; ++q) {
+                const int slot = (int)(q % SB);
+                if (!wait_bar(&bars.b_empty[slot], (uint32_t)(((q / SB) & 1) ^ 1), abort_v, st))
+                    break;
+                const long long unit = q / ksteps;
+                const int ch = (int)(unit % nch), ks = (int)(q % ksteps);
+                mbar_expect_tx(&bars.b_full[slot], Sbytes);
+                bulk_load(sB + (size_t)slot * Sbytes, a.Cb + ((size_t)ch * ksteps + ks) * Sbytes,
+                          Sbytes, &bars.b_full[slot]);
+            }
+            for (long long r = q > SB ? q - SB : 0; r < q; ++r)
+                tc::mbar_wait(&bars.b_full[r % SB], (uint32_t)((r / SB) & 1), kWaitTries);
+        }
+    } else if (warp == 2) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::instr_desc(1u, (uint32_t)NC, (uint32_t)kRows);
+            uint32_t use[2 * kEpiGroups] = {0u, 0u, 0u, 0u};
+            long long q = 0;
+            bool ok = true;
+            for (long long i = 0; i < cnt && ok; ++i) {
+                const int sa = (int)(i & 1);
+                if (!(ok = wait_bar(&bars.a_full[sa], (uint32_t)((i >> 1) & 1), abort_v, st))) break;
+                tc::fence_after_sync();
+                const uint32_t aBase = sAaddr + (uint32_t)sa * Abytes;
+                for (int ch = 0; ch < nch && ok; ++ch) {
+                    const int b = 2 * (int)(i & 1) + (ch & 1);
+                    if (!(ok = wait_bar(&bars.acc_empty[b], (use[b] & 1u) ^ 1u, abort_v, st))) break;
+                    tc::fence_after_sync();
+                    const uint32_t dt = tmem + (uint32_t)(b * NC);
+                    for (int ks = 0; ks < ksteps; ++ks, ++q) {
+                        const int slot = (int)(q % SB);
+                        if (!(ok = wait_bar(&bars.b_full[slot], (uint32_t)((q / SB) & 1), abort_v, st)))
+                            break;
+                        tc::fence_after_sync();
+                        const uint32_t ah = aBase + (uint32_t)ks * 4096u;
+                        const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes;
+                        tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
+                        tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh + (uint32_t)NC * 32u), idesc, 1u);
+                        tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                        tc::mma_commit(&bars.b_empty[slot]);
+                    }
+                    if (!ok) break;
+                    tc::mma_commit(&bars.acc_full[b]);
+                    ++use[b];
                 }
-                const long long p = (blockIdx.x + i * gridDim.x) * kRows + row;
-                const bool valid = p < a.n;
-                if ((i & 255) == 255) {
-                    // keep each ||x||^2 partial below 2^62: fold it every 256 tiles
-                    long long qs = qloc;
-                    for (int o = 16; o; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
-                    if (lane == 0 && qs) split_add(&st->q_lo, &st->q_hi, qs);
-                    qloc = 0;
-                }
-                const float xx = valid ? __ldg(a.xn2 + p) : 0.0f;
-                const float thr = a.kappa * (thr_base + xx) + a.kpack * (fabsf(B1) + fabsf(B2));
-                const bool flag = valid && (B2 - B1 <= thr);
-                recheck_append(flag, (int)p, list, &st->recheck_count);
-                const float* xr = a.X + p * d;
-                if (mode == kModeFull && valid)
-                    for (int t = 0; t < d; ++t) qloc += sq_fixed(__ldg(xr + t), scaleG);
-                if (valid && !flag) {
-                    const int old = (mode == kModeDelta) ? labels[p] : -1;
-                    if (BI != old) {
-                        for (int t = 0; t < d; ++t) {
-                            const long long val = to_fixed(__ldg(xr + t), scaleF);
-                            split_add(acc.s_lo + (long long)BI * d + t, acc.s_hi + (long long)BI * d + t, val);
-                            if (old >= 0)
-                                split_add(acc.s_lo + (long long)old * d + t,
-                                          acc.s_hi + (long long)old * d + t, -val);
+                if (ok) tc::mma_commit(&bars.a_empty[sa]);
+            }
+            // every MMA issued by this thread has completed once `drain` flips
+            tc::mma_commit(&bars.drain);
+            tc::mbar_wait(&bars.drain, 0u, kWaitTries);
+        }
+    } else {
+        // ---------------- epilogue group g: tiles i = g, g + 2, ...
+        const int ew = warp - 3;
+        const int g = ew >> 2;
+        const int quarter = warp & 3;                     // TMEM lanes 32 * (warp % 4) ...
+        const int row = 32 * quarter + lane;
+        const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
+        const int mode = st->mode;
+        const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float thr_base = 2.0f * st->cmax2;
+        uint32_t use[2] = {0u, 0u};
+        long long qloc = 0;
+        long long done = 0;
+        bool ok = true;
+        for (long long i = g; i < cnt && ok; i += kEpiGroups) {
+            float B1 = INFINITY, B2 = INFINITY;
+            int BI = 0;
+            for (int ch = 0; ch < nch; ++ch) {
+                const int b = 2 * g + (ch & 1);
+                bool w = wait_bar(&bars.acc_full[b], use[ch & 1] & 1u, abort_v, st);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                tc::fence_after_sync();
+                for (int c0 = 0; c0 < NC; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * NC + c0), v);
+                    const int j0 = ch * NC + c0;           // center index of v[0]
+                    const float4* cn4 = reinterpret_cast<const float4*>(c.cnorm + j0);
+                    float q1[4], q2[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
+#pragma unroll
+                    for (int gq = 0; gq < 8; ++gq) {
+                        const float4 cn = __ldg(cn4 + gq);
+                        const float w0 = v[4 * gq] + cn.x, w1 = v[4 * gq + 1] + cn.y;
+                        const float w2 = v[4 * gq + 2] + cn.z, w3 = v[4 * gq + 3] + cn.w;
+                        const int q = gq & 3;
+                        {
+                            const float k0 = pack_key(w0, 4u * gq), k1 = pack_key(w1, 4u * gq + 1u);
+                            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+                            q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
+                            q1[q] = fminf(q1[q], lo);
                         }
-                        atomicAdd(acc.cnt + BI, 1ull);
-                        if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
-                        labels[p] = BI;
+                        {
+                            const float k0 = pack_key(w2, 4u * gq + 2u), k1 = pack_key(w3, 4u * gq + 3u);
+                            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+                            q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
+                            q1[q] = fminf(q1[q], lo);
+                        }
+                    }
+                    const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
+                    const float l01 = fminf(q1[0], q1[1]);
+                    const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
+                    const float l23 = fminf(q1[2], q1[3]);
+                    const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
+                    const float b1 = fminf(l01, l23);
+                    if (b1 < B1) {
+                        B2 = fminf(B1, b2);
+                        B1 = b1;
+                        BI = j0 + (int)(__float_as_uint(b1) & 31u);
+                    } else {
+                        B2 = fminf(B2, b1);
                     }
                 }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
+                ++use[ch & 1];
             }
-            B1 = INFINITY;
-            B2 = INFINITY;
-            BI = 0;
-        }
-        __syncthreads();
-    }
-    if (u < U) {
-        // a wait gave up: record it, let this CTA's own copies and MMAs finish, then leave
-        if (tid == 0) {
-            atomicExch(&st->error, kErrTimeout);
-            tc::mbar_wait(&barM[u & 1], (uint32_t)((u >> 1) & 1), kWaitTries);
-            if (u + 1 < U) {
-                const long long v = u + 1, vi = v / nch;
-                tc::mbar_wait(&barB[v & 1], (uint32_t)((v >> 1) & 1), kWaitTries);
-                if (v % nch == 0) tc::mbar_wait(&barA[vi & 1], (uint32_t)((vi >> 1) & 1), kWaitTries);
-                if (next_issued) tc::mbar_wait(&barM[v & 1], (uint32_t)((v >> 1) & 1), kWaitTries);
+            if (!ok) break;
+            // ---- decide row `row` of tile i
+            const long long p = (blockIdx.x + i * gridDim.x) * kRows + row;
+            const bool valid = p < a.n;
+            if ((done & 255) == 255) {
+                // keep each ||x||^2 partial below 2^62: fold it every 256 tiles
+                long long qs = qloc;
+                for (int o = 16; o; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
+                if (lane == 0 && qs) split_add(&st->q_lo, &st->q_hi, qs);
+                qloc = 0;
+            }
+            ++done;
+            const float xx = valid ? __ldg(a.xn2 + p) : 0.0f;
+            const float thr = a.kappa * (thr_base + xx) + a.kpack * (fabsf(B1) + fabsf(B2));
+            const bool flag = valid && (B2 - B1 <= thr);
+            recheck_append(flag, (int)p, list, &st->recheck_count);
+            const float* xr = a.X + p * d;
+            if (mode == kModeFull && valid)
+                for (int t = 0; t < d; ++t) qloc += sq_fixed(__ldg(xr + t), scaleG);
+            if (valid && !flag) {
+                const int old = (mode == kModeDelta) ? labels[p] : -1;
+                if (BI != old) {
+                    for (int t = 0; t < d; ++t) {
+                        const long long val = to_fixed(__ldg(xr + t), scaleF);
+                        split_add(acc.s_lo + (long long)BI * d + t, acc.s_hi + (long long)BI * d + t, val);
+                        if (old >= 0)
+                            split_add(acc.s_lo + (long long)old * d + t,
+                                      acc.s_hi + (long long)old * d + t, -val);
+                    }
+                    atomicAdd(acc.cnt + BI, 1ull);
+                    if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                    labels[p] = BI;
+                }
             }
         }
-        __syncthreads();
+        // one partial of ||x||^2 per warp (each below 2^62)
+        for (int o = 16; o; o >>= 1) qloc += __shfl_xor_sync(0xffffffffu, qloc, o);
+        if (lane == 0 && qloc) split_add(&st->q_lo, &st->q_hi, qloc);
     }
-    // one partial of ||x||^2 per warp (warps 0-3 hold them; each is below 2^62)
-    for (int o = 16; o; o >>= 1) qloc += __shfl_xor_sync(0xffffffffu, qloc, o);
-    if (lane == 0 && qloc) split_add(&st->q_lo, &st->q_hi, qloc);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, a.tmem_cols);
+    if (warp == 2) tc::tmem_dealloc(tmem, a.tmem_cols);
 }
 
 // X -> BF16 tiles (K-major core-matrix layout) and FP32 ||x||^2; one warp per row.
@@ -340,12 +398,13 @@ __global__ void convert_x_kernel(const float* __restrict__ X, long long n, int d
     }
 }
 
-// -2c -> BF16 chunks of NC centers (padding centers are zero).
+// -2c -> BF16 slices: for each chunk of NC centers and K-step, the mh part then
+// the ml part (NC * 32 bytes each); padding centers are zero.
 __global__ void convert_c_kernel(const float* __restrict__ c32, int k, int d, int NC, int nch,
                                  unsigned char* __restrict__ Cb)
 {
     const long long total = (long long)nch * NC * d;
-    const size_t Bhalf = (size_t)NC * d * 2;
+    const int ksteps = d / 16;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(e / d), t = (int)(e - (long long)j * d);
@@ -354,9 +413,9 @@ __global__ void convert_c_kernel(const float* __restrict__ c32, int k, int d, in
         const int s = t >> 4, kc = (t >> 3) & 1, el = t & 7;
         const __nv_bfloat16 h = __float2bfloat16_rn(m);
         const __nv_bfloat16 l = __float2bfloat16_rn(m - __bfloat162float(h));
-        const size_t off = (size_t)ch * 2 * Bhalf + (size_t)s * NC * 32 + tc::tile_offset(jj, kc) + el * 2;
+        const size_t off = ((size_t)ch * ksteps + s) * NC * 64 + tc::tile_offset(jj, kc) + el * 2;
         *reinterpret_cast<__nv_bfloat16*>(Cb + off) = h;
-        *reinterpret_cast<__nv_bfloat16*>(Cb + off + Bhalf) = l;
+        *reinterpret_cast<__nv_bfloat16*>(Cb + off + (size_t)NC * 32) = l;
     }
 }
 
@@ -379,9 +438,11 @@ float bf16_kappa(int d)
     return (float)(2.0 * kb * 1.0625);
 }
 
+// Two A stages of a 128-row tile (hi + lo parts) and at least two B slices of
+// the widest chunk must fit into the shared-memory budget.
 int bf16_fits(int d)
 {
-    return 2 * 2 * 128 * d * 2 + 2 * 2 * 64 * d * 2 <= 200 * 1024;
+    return d <= 128 && kSA * 4 * kRows * d + 2 * 128 * 64 <= kSmemBudget;
 }
 
 int assign_bf16_supported(int d, int k, const float* X)
@@ -391,16 +452,14 @@ int assign_bf16_supported(int d, int k, const float* X)
     return d >= 16 && d % 16 == 0 && bf16_fits(d);
 }
 
-// Chunk width NC in {64, 128, 256} (a divisor of 256, so NC * chunks never
-// exceeds k rounded up to 256, the length of the padded ||c||^2 array):
-// halved while k fits in half a chunk or the two A and two B stages would
-// exceed 200 KB of shared memory.
+// Chunk width NC: 128, or 64 when k fits in 64 (NC * chunks then never exceeds
+// k rounded up to 128, the least length of the padded ||c||^2 array).  Two
+// epilogue groups x two accumulators x NC columns fill at most the 512 TMEM
+// columns of the SM.
 int bf16_chunk(int d, int k)
 {
-    int nc = 256;
-    while (nc > 64 && nc / 2 >= k) nc /= 2;
-    while (nc > 64 && 2 * 2 * 128 * d * 2 + 2 * 2 * nc * d * 2 > 200 * 1024) nc /= 2;
-    return nc;
+    (void)d;
+    return k <= 64 ? 64 : 128;
 }
 
 size_t bf16_xt_bytes(long long n, int d)
@@ -443,14 +502,21 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
         KM2_CUDA(cudaGetLastError());
     }
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * NC)) cols <<= 1;
-    const size_t smem = (size_t)2 * 2 * kRows * d * 2 + (size_t)2 * 2 * NC * d * 2;
+    while (cols < (uint32_t)(2 * kEpiGroups * NC)) cols <<= 1;
+    const size_t abytes = (size_t)4 * kRows * d, sbytes = (size_t)NC * 64;
+    int sb = (int)((kSmemBudget - kSA * abytes) / sbytes);
+    if (sb > kMaxSB) sb = kMaxSB;
+    if (sb < 2) {
+        set_last_error_text("assign_bf16: shared-memory budget too small for this d");
+        return KMEANS2_ERR_UNSUPPORTED;
+    }
+    const size_t smem = kSA * abytes + (size_t)sb * sbytes;
     static thread_local int configured_for = -1;
     int dev = 0;
     KM2_CUDA(cudaGetDevice(&dev));
     if (configured_for != dev) {
         KM2_CUDA(cudaFuncSetAttribute(assign_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      210 * 1024));
+                                      kSmemBudget));
         configured_for = dev;
     }
     const long long tiles = (n + kRows - 1) / kRows;
@@ -467,6 +533,7 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     a.k = c.k;
     a.nc = NC;
     a.nch = nch;
+    a.sb = sb;
     a.tmem_cols = cols;
     a.kappa = bf16_kappa(d);
     a.kpack = kPackSlack;

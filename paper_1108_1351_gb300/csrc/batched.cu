@@ -18,7 +18,9 @@
 // Work items hold a number of tiles chosen per dimension class by an
 // autotuner: on the first call for a class it times the real first pass of
 // the batch for a few item sizes (resetting the sums between trials) and keeps
-// the fastest for the rest of the process.
+// the fastest for the rest of the process.  CTAs claim items from an atomic
+// counter, largest jobs first, so the iterations in which only a few large
+// jobs still run keep every SM busy.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -238,7 +240,7 @@ __device__ __forceinline__ float pack_key(float v, unsigned j)
 
 template <int DC>
 __global__ void __launch_bounds__(kThreads, 2)
-batch_assign(BatchInst* insts, const WorkItem* items, int nitems)
+batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item)
 {
     using C = BCfg<DC>;
     constexpr int P = C::P;
@@ -248,9 +250,17 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems)
     long long* sacc = reinterpret_cast<long long*>(ss + kMaxK);
     int* scnt = reinterpret_cast<int*>(sacc + kMaxK * DC);
     __shared__ unsigned long long sq;
+    __shared__ int s_item;
     const int tid = threadIdx.x;
 
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // items are claimed dynamically (largest jobs first), so the CTAs stay busy
+    // when only a few jobs are still running
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();   // every thread has read it before thread 0 claims the next
+        if (it >= nitems) break;
         const WorkItem w = items[it];
         BatchInst* I = insts + w.inst;
         const int stage = I->stage;
@@ -453,10 +463,12 @@ __global__ void __launch_bounds__(kThreads) batch_finalize_kernel(BatchInst* ins
     }
 }
 
-__global__ void batch_control_kernel(int* active, int* iter, int cap, unsigned long long handle)
+__global__ void batch_control_kernel(int* active, int* iter, int* next_item, int nclass, int cap,
+                                     unsigned long long handle)
 {
     const int a = *active;
     *active = 0;
+    for (int c = 0; c < nclass; ++c) next_item[c] = 0;   // work lists of the next iteration
     const int it = ++*iter;
     cudaGraphSetConditional(handle, (a > 0 && it < cap) ? 1u : 0u);
 }
@@ -474,8 +486,8 @@ int dclass(int d)
 }
 
 template <int DC>
-int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, cudaStream_t s,
-                        int sm_count)
+int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item,
+                        cudaStream_t s, int sm_count)
 {
     static thread_local int configured_for = -1;
     int dev = 0;
@@ -493,21 +505,21 @@ int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, cud
     if (grid > nitems) grid = nitems;
     if (grid < 1) grid = 1;
     ++g_launches;
-    batch_assign<DC><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems);
+    batch_assign<DC><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems, next_item);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
 
-int launch_class(int dc, BatchInst* insts, const WorkItem* items, int nitems, cudaStream_t s,
-                 int sm_count)
+int launch_class(int dc, BatchInst* insts, const WorkItem* items, int nitems, int* next_item,
+                 cudaStream_t s, int sm_count)
 {
     switch (dc) {
-        case 2: return launch_batch_assign<2>(insts, items, nitems, s, sm_count);
-        case 4: return launch_batch_assign<4>(insts, items, nitems, s, sm_count);
-        case 8: return launch_batch_assign<8>(insts, items, nitems, s, sm_count);
-        case 16: return launch_batch_assign<16>(insts, items, nitems, s, sm_count);
-        case 32: return launch_batch_assign<32>(insts, items, nitems, s, sm_count);
-        default: return launch_batch_assign<64>(insts, items, nitems, s, sm_count);
+        case 2: return launch_batch_assign<2>(insts, items, nitems, next_item, s, sm_count);
+        case 4: return launch_batch_assign<4>(insts, items, nitems, next_item, s, sm_count);
+        case 8: return launch_batch_assign<8>(insts, items, nitems, next_item, s, sm_count);
+        case 16: return launch_batch_assign<16>(insts, items, nitems, next_item, s, sm_count);
+        case 32: return launch_batch_assign<32>(insts, items, nitems, next_item, s, sm_count);
+        default: return launch_batch_assign<64>(insts, items, nitems, next_item, s, sm_count);
     }
 }
 
@@ -522,11 +534,15 @@ struct ClassItems {
     int count = 0;
 };
 
+// Work items of a dimension class, largest jobs first (longest-processing-
+// time order: the big jobs' items start early and the small ones fill in).
 void build_items(ClassItems& ci, const std::vector<int>& members, const std::vector<long long>& n,
                  int tpi)
 {
     ci.host.clear();
-    for (int j : members) {
+    std::vector<int> order(members);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    for (int j : order) {
         const long long tiles = (n[j] + kTile - 1) / kTile;
         for (long long t = 0; t < tiles; t += tpi)
             ci.host.push_back(WorkItem{j, (int)t, tpi});
@@ -605,7 +621,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         int* counters = nullptr;
         KM2_TRY(ws.alloc((void**)&arena, total, s));
         KM2_TRY(ws.alloc((void**)&dinst, sizeof(BatchInst) * (size_t)count, s));
-        KM2_TRY(ws.alloc((void**)&counters, 2 * sizeof(int), s));
+        KM2_TRY(ws.alloc((void**)&counters, 8 * sizeof(int), s));   // active, iteration, 6 item counters
         for (int j = 0; j < count; ++j) {
             const kmeans2_job& J = jobs[j];
             BatchInst& I = hi[j];
@@ -647,7 +663,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         }
         KM2_CUDA(cudaMemcpyAsync(dinst, hi.data(), sizeof(BatchInst) * (size_t)count,
                                  cudaMemcpyHostToDevice, s));
-        KM2_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
+        KM2_CUDA(cudaMemsetAsync(counters, 0, 8 * sizeof(int), s));
         g_launches += 3;
         batch_sample_kernel<<<count, kThreads, 0, s>>>(dinst);
         batch_gather_kernel<<<count, kThreads, 0, s>>>(dinst);
@@ -669,7 +685,9 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             }
             if (tpi == 0) {
                 // time the real first pass for a few item sizes, resetting the sums between
-                const int cand[4] = {1, 4, 16, kMaxTilesPerItem};
+                // small items keep every SM busy once only a few jobs still run
+                const int cand[4] = {1, 2, 4, 8};
+                static_assert(8 <= kMaxTilesPerItem, "item partial sums must stay below 2^62");
                 float best_ms = 0.f;
                 cudaEvent_t e0, e1;
                 KM2_CUDA(cudaEventCreate(&e0));
@@ -681,8 +699,10 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
                     KM2_CUDA(cudaMemcpyAsync(trial.dev, trial.host.data(),
                                              sizeof(WorkItem) * (size_t)trial.count,
                                              cudaMemcpyHostToDevice, s));
+                    KM2_CUDA(cudaMemsetAsync(counters + 2, 0, sizeof(int), s));
                     KM2_CUDA(cudaEventRecord(e0, s));
-                    KM2_TRY(launch_class(ci.dc, dinst, trial.dev, trial.count, s, ws.sm_count));
+                    KM2_TRY(launch_class(ci.dc, dinst, trial.dev, trial.count, counters + 2, s,
+                                         ws.sm_count));
                     KM2_CUDA(cudaEventRecord(e1, s));
                     ++g_launches;
                     batch_reset_kernel<<<count, kThreads, 0, s>>>(dinst);
@@ -703,6 +723,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             classes.push_back(std::move(ci));
         }
 
+        KM2_CUDA(cudaMemsetAsync(counters + 2, 0, 6 * sizeof(int), s));
         // ---- the iteration loop as one graph with a device-side while condition
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -724,14 +745,16 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             cudaGraph_t body = gp->conditional.phGraph_out[0];
             e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) { set_last_error("cudaStreamBeginCaptureToGraph", e); rc = KMEANS2_ERR_CUDA; break; }
-            for (auto& ci : classes) {
-                rc = launch_class(ci.dc, dinst, ci.dev, ci.count, s, ws.sm_count);
+            for (size_t c = 0; c < classes.size(); ++c) {
+                rc = launch_class(classes[c].dc, dinst, classes[c].dev, classes[c].count,
+                                  counters + 2 + c, s, ws.sm_count);
                 if (rc != KMEANS2_OK) break;
             }
             if (rc == KMEANS2_OK) {
                 batch_recheck_kernel<<<count, kThreads, 0, s>>>(dinst);
                 batch_finalize_kernel<<<count, kThreads, 0, s>>>(dinst, counters);
-                batch_control_kernel<<<1, 1, 0, s>>>(counters, counters + 1, 2 * max_iter_all + 2,
+                batch_control_kernel<<<1, 1, 0, s>>>(counters, counters + 1, counters + 2,
+                                                     (int)classes.size(), 2 * max_iter_all + 2,
                                                      (unsigned long long)handle);
             }
             cudaGraph_t captured = nullptr;

@@ -3,11 +3,14 @@
 //
 // The server owns W worker threads, each bound to the server's device and to
 // one non-blocking stream of its own.  Jobs wait in arrival order.  A free
-// worker admits the first waiting job whose device footprint fits into the
-// HBM budget next to the jobs already running (a job passed over kMaxBypass
-// times blocks everything behind it, so large jobs are not starved) and runs
-// kmeans2_fit on it: stage loops as graphs with device-side while conditions,
-// the job's data, labels and centers resident from admission to result.
+// worker admits, under the FIFO policy, the first waiting job whose device
+// footprint fits into the HBM budget next to the jobs already running (a job
+// passed over kMaxBypass times blocks everything behind it, so large jobs are
+// not starved), or under the SHORTEST policy the fitting job with the least
+// work per iteration (n k d) unless some job has waited longer than the aging
+// limit; it runs kmeans2_fit on it: stage loops as graphs with device-side
+// while conditions, the job's data, labels and centers resident from
+// admission to result.
 // Different jobs' kernels therefore overlap on the GPU, and a job that arrives
 // while others run starts as soon as a worker and memory are free -- no batch
 // boundary to wait for.  Every job runs exactly the kernels of a lone
@@ -35,6 +38,7 @@ enum class JobState { Queued, Running, Done };
 struct Ticket {
     kmeans2_job job{};
     uint64_t footprint = 0;
+    double work = 0.0;          // n k d: the cost of one iteration
     JobState state = JobState::Queued;
     int status = KMEANS2_PENDING;
     int bypassed = 0;
@@ -73,6 +77,8 @@ struct kmeans2_server {
     int running = 0;
     int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rejected = 0, launches = 0;
     bool stop = false;
+    int policy = KMEANS2_POLICY_FIFO;
+    double aging_s = 0.0;
 
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
@@ -85,6 +91,7 @@ struct kmeans2_server {
     // Under mu: the ticket a free worker should start, or 0.
     uint64_t pick()
     {
+        if (policy == KMEANS2_POLICY_SHORTEST) return pick_shortest();
         for (size_t i = 0; i < queue.size(); ++i) {
             km2::Ticket& t = tickets[queue[i]];
             if (in_use + t.footprint <= budget) {
@@ -96,6 +103,32 @@ struct kmeans2_server {
             if (t.bypassed >= km2::kMaxBypass) break;   // nothing may pass it any more
         }
         return 0;
+    }
+
+    // Under mu: a job that has waited aging_s or longer goes first (oldest
+    // first; while it does not fit nothing else is admitted); otherwise the
+    // waiting job with the least work per iteration that fits.
+    uint64_t pick_shortest()
+    {
+        if (queue.empty()) return 0;
+        const double t = now();
+        const uint64_t head = queue.front();
+        km2::Ticket& h = tickets[head];
+        if (t - h.times.t_submit >= aging_s) {
+            if (in_use + h.footprint > budget) return 0;
+            queue.pop_front();
+            return head;
+        }
+        size_t best = queue.size();
+        for (size_t i = 0; i < queue.size(); ++i) {
+            const km2::Ticket& c = tickets[queue[i]];
+            if (in_use + c.footprint > budget) continue;
+            if (best == queue.size() || c.work < tickets[queue[best]].work) best = i;
+        }
+        if (best == queue.size()) return 0;
+        const uint64_t id = queue[best];
+        queue.erase(queue.begin() + (long)best);
+        return id;
     }
 
     void work(int slot)
@@ -240,6 +273,7 @@ int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t*
     km2::Ticket& t = srv->tickets[id];
     t.job = J;
     t.footprint = fp;
+    t.work = (double)J.n * (double)J.k * (double)J.d;
     t.times.t_submit = srv->now();
     srv->queue.push_back(id);
     ++srv->submitted;
@@ -293,6 +327,18 @@ int kmeans2_server_stats_get(kmeans2_server* srv, kmeans2_server_stats* out)
 }
 
 double kmeans2_server_now(kmeans2_server* srv) { return srv ? srv->now() : 0.0; }
+
+int kmeans2_server_set_policy(kmeans2_server* srv, int32_t policy, double aging_s)
+{
+    if (!srv || (policy != KMEANS2_POLICY_FIFO && policy != KMEANS2_POLICY_SHORTEST) ||
+        !(aging_s >= 0.0))
+        return KMEANS2_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->policy = policy;
+    srv->aging_s = aging_s;
+    srv->cv_work.notify_all();
+    return KMEANS2_OK;
+}
 
 void kmeans2_server_destroy(kmeans2_server* srv)
 {

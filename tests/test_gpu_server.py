@@ -149,3 +149,54 @@ def test_server_destroy_with_queued_jobs():
         srv.submit(X, 256, 0.1, 50 + j, 1e-6, 30)
     srv.close()          # the running job completes, the waiting ones are cancelled
     torch.cuda.synchronize()
+
+
+def test_server_faulty_job_leaves_the_others_unchanged():
+    # a job holding a NaN fails with KMEANS2_ERR_NONFINITE; the jobs beside it
+    # still equal their lone runs, and malformed requests are refused at submit
+    specs = [(40_000, 16, 30, 0.1, 1e-6, 50, 61), (60_000, 64, 100, 0.1, 1e-6, 40, 62),
+             (30_000, 4, 12, 0.1, 1e-6, 60, 63)]
+    Xs = [_data(n, d, k, s) for (n, d, k, f, tol, it, s) in specs]
+    bad = _data(50_000, 16, 20, 64)
+    bad[123, 5] = float("nan")
+    alone = [km.fit(X, k, f, s, tol, it) for X, (n, d, k, f, tol, it, s) in zip(Xs, specs)]
+    with km.Server(max_slots=4) as srv:
+        tb = srv.submit(bad, 20, 0.1, 64, 1e-6, 50)
+        tickets = [srv.submit(X, k, f, s, tol, it) for X, (n, d, k, f, tol, it, s) in zip(Xs, specs)]
+        for args in [(Xs[0], 0, 0.1, 1, 1e-6, 10), (Xs[0], 10, 0.0, 1, 1e-6, 10),
+                     (Xs[0], 10, 0.1, 1, -1.0, 10), (Xs[0], 10, 0.1, 1, 1e-6, 0)]:
+            with pytest.raises(km.KMeans2Error) as ei:
+                srv.submit(*args)
+            assert ei.value.status == -1
+        fb = srv.wait(tb)
+        served = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert fb.status == -4 and fb.result is None
+    assert st["failed"] == 1 and st["completed"] == len(specs)
+    for a, sv in zip(alone, served):
+        assert sv.status == 0
+        _same(sv.result, a)
+
+
+@pytest.mark.parametrize("aging,order", [(1000.0, "CDB"), (0.0, "BCD")])
+def test_server_shortest_policy_admission_order(aging, order):
+    # one slot held by a long job; three jobs queue behind it.  SHORTEST admits
+    # the least work per iteration first; with aging 0 every job is "old" and
+    # the oldest goes first (arrival order)
+    XA = _data(2_000_000, 128, 1024, 71)
+    jobs = {"B": (100_000, 16, 64, 72), "C": (20_000, 4, 8, 73), "D": (50_000, 16, 16, 74)}
+    Xs = {name: _data(n, d, k, s) for name, (n, d, k, s) in jobs.items()}
+    with km.Server(max_slots=1, policy="shortest", aging_s=aging) as srv:
+        ta = srv.submit(XA, 1024, 0.1, 71, 1e-7, 40)
+        t0 = time.time()
+        while srv.stats()["running"] < 1 and time.time() - t0 < 30:
+            time.sleep(0.001)
+        tickets = {name: srv.submit(Xs[name], k, 0.1, s, 1e-6, 50)
+                   for name, (n, d, k, s) in jobs.items()}
+        res = {name: srv.wait(t) for name, t in tickets.items()}
+        a = srv.wait(ta)
+    assert a.status == 0 and all(r.status == 0 for r in res.values())
+    got = "".join(sorted(res, key=lambda nm: res[nm].t_admit))
+    assert got == order
+    for name, (n, d, k, s) in jobs.items():
+        _same(res[name].result, km.fit(Xs[name], k, 0.1, s, 1e-6, 50))
