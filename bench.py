@@ -555,6 +555,70 @@ def run_serve(args):
     return 0
 
 
+SWEEP = dict(fractions=(0.01, 0.10, 0.15, 0.20, 0.30, 0.40),
+             tols=(1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10), max_iter=500,
+             seed=0)
+
+
+def run_sweep(args):
+    """Normal (single-stage) k-means vs the two-stage method (Section 6, Tables
+    2-3, Fig. 13) on a synthetic stand-in: for each stopping tolerance, normal
+    k-means is Lloyd on S_n from the same k initial data points the two-stage
+    fit draws (kmeans2_fit with start_stage = 1), and the two-stage fit runs for
+    each subset fraction; time-to-converge and final J side by side."""
+    import torch
+    import paper_1108_1351_gb300 as km
+    from paper_1108_1351_gb300 import synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.load()
+    n, d, k = args.sweep_n, args.sweep_d, args.sweep_k
+    X = synth.aniso_gaussian_noise(n, d, k, SWEEP["seed"] + rank, device=dev, chunk=1 << 24)
+    stream = torch.cuda.current_stream(dev)
+    seed = SWEEP["seed"] + rank
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    rows = []
+    for f in SWEEP["fractions"]:
+        sub, pos = km.sample(n, k, f, seed)
+        C0 = X[sub[pos]].double()          # the two-stage fit's own initial centers
+        for tol in SWEEP["tols"]:
+            normal, t_n = timed(lambda: km.fit(X, k, f, seed, tol, SWEEP["max_iter"],
+                                               init_centers=C0, start_stage=1, stream=stream))
+            two, t_2 = timed(lambda: km.fit(X, k, f, seed, tol, SWEEP["max_iter"], stream=stream))
+            rows.append({"subset_fraction": f, "tol": tol,
+                         "normal": {"s": t_n, "J": normal.J, "iters": normal.iters_slow},
+                         "two_stage": {"s": t_2, "J": two.J, "iters_fast": two.iters_fast,
+                                       "iters_slow": two.iters_slow},
+                         "speedup": t_n / t_2 if t_2 > 0 else None,
+                         "J_rel_diff": (two.J - normal.J) / normal.J if normal.J else None})
+    if rank != 0:
+        return 0
+    best = max(r["speedup"] for r in rows)
+    line = {"metric": "two-stage vs normal k-means: time-to-converge speedup (J beside)",
+            "value": best, "unit": "x (best over the sweep)", "n_gpus": ws, "steps": 1,
+            "warmup": 2, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep", "n": n, "d": d, "k": k,
+                       "generator": "anisotropic Gaussian mixture + 2% noise",
+                       "max_iter": SWEEP["max_iter"]},
+            "sweep": rows, "roofline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 BATCH = dict(count=4096, seed=0, f=0.1, tol=1e-6, max_iter=100)
 
 
@@ -595,13 +659,25 @@ def run_batched(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        res = batched(prof)
+        res = batched()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
     evals = sum(r.distance_evals for r in res)
+    # one more call in the profiled (host-driven) mode: the distance kernels'
+    # own time for the roofline entry, and the number of kernels a call launches
+    batched(prof)
     launches = int(prof.kernel_launches)
+    peaks, src = _peaks()
+    p32 = 2.0 * FP32_LANES_PER_SM * SM_COUNT_GB300 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e-6
+    ach = prof.assign_flops / (prof.assign_ms * 1e-3) / 1e12 if prof.assign_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "batch_assign<DC> (all dimension classes)",
+                "achieved": ach, "peak": p32, "unit": "TFLOP/s",
+                "frac": ach / p32 if ach else None, "traffic": None,
+                "peak_source": f"derived: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                               f"x max clock ({src})",
+                "kernel_ms_per_call": prof.assign_ms}
     # baseline: the same instances, one kmeans2_fit at a time (plain FP32 form)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -633,7 +709,7 @@ def run_batched(args):
                                "value": sum(r.distance_evals for r in singles) / (ms_single * 1e-3),
                                "speedup_of_batched": ms_single / ms_max},
         "sampled_instances_identical": bool(same), "sampled": int(len(sample)),
-        "gpu_launches": launches, "roofline": None, "clocks": clk,
+        "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -644,7 +720,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="aniso8", choices=sorted(CONFIGS) + ["serve", "batched"])
+    ap.add_argument("--config", default="aniso8",
+                    choices=sorted(CONFIGS) + ["serve", "batched", "sweep"])
+    ap.add_argument("--sweep-n", type=int, default=10_000_000, help="sweep: points")
+    ap.add_argument("--sweep-d", type=int, default=12, help="sweep: dimensions")
+    ap.add_argument("--sweep-k", type=int, default=16, help="sweep: clusters")
     ap.add_argument("--instances", type=int, default=BATCH["count"],
                     help="batched: number of independent instances")
     ap.add_argument("--duration", type=float, default=SERVE["duration"],
@@ -661,6 +741,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
+    if args.config == "sweep":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the sweep compares two GPU "
+                              "forms of the method with each other"}))
+            return 0
+        return run_sweep(args)
     if args.config == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload's "

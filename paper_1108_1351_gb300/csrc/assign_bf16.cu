@@ -13,7 +13,10 @@
 //        (tc_common.cuh);
 //   xn2: FP32 ||x||^2 per point (for the error bound);
 //   Cb : one contiguous slice per (chunk of NC centers, K-step): the mh then
-//        the ml part, NC * 32 bytes each.
+//        the ml part, NC * 32 bytes each; after a chunk's d/16 data slices a
+//        norm slice holds ||c_j||^2 = nh + nm + nl (three exact BF16 parts) in
+//        the first three columns of row j, multiplied by a constant A tile of
+//        ones, so the accumulator holds ||c||^2 - 2 x.c with no epilogue add.
 //
 // Warp-specialised pipeline, one CTA per SM, 11 warps:
 //   warp 0  A producer: one bulk TMA copy per tile into a 2-stage ring;
@@ -24,9 +27,10 @@
 //           each tile and hands the accumulator to the epilogue;
 //   warps 3-6, 7-10  two epilogue groups taking alternate tiles, each with its
 //           own two TMEM accumulators (4 x NC columns in all): a thread owns
-//           one row (TMEM lane) of the tile, adds ||c||^2, keeps a packed-key
-//           top-2 across the chunks and decides the row (near-tie flag, label,
-//           exact fixed-point cluster sums).
+//           one row (TMEM lane) of the tile, keeps a packed-key top-2 across
+//           the chunks (the next 32 columns load while the current ones are
+//           compared) and decides the row (near-tie flag, label, exact
+//           fixed-point cluster sums).
 // Roles are coupled only by mbarriers (full / empty per ring slot and per
 // accumulator), so copies, MMAs and epilogues of different units overlap.
 // Every wait is bounded; on timeout the CTA records an error, each role lets
@@ -123,6 +127,41 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     return false;
 }
 
+// Packed-key top-2 of 32 accumulator columns (center indices j0 .. j0 + 31)
+// folded into the running (B1, B2, BI) of a row.
+__device__ __forceinline__ void top2_cols(const uint32_t* r, int j0, float& B1, float& B2, int& BI)
+{
+    float q1[4], q2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = j + 2 * q;
+            const float k0 = pack_key(__uint_as_float(r[jj]), (unsigned)jj);
+            const float k1 = pack_key(__uint_as_float(r[jj + 1]), (unsigned)jj + 1u);
+            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+            q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
+            q1[q] = fminf(q1[q], lo);
+        }
+    }
+    const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
+    const float l01 = fminf(q1[0], q1[1]);
+    const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
+    const float l23 = fminf(q1[2], q1[3]);
+    const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
+    const float b1 = fminf(l01, l23);
+    if (b1 < B1) {
+        B2 = fminf(B1, b2);
+        B1 = b1;
+        BI = j0 + (int)(__float_as_uint(b1) & 31u);
+    } else {
+        B2 = fminf(B2, b1);
+    }
+}
+
+template <int NC>
 __global__ void __launch_bounds__(kThreads, 1)
 assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Accum acc,
             int* __restrict__ list)
@@ -134,17 +173,27 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
 
     if (st->error) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int d = a.d, NC = a.nc, nch = a.nch, SB = a.sb;
+    const int d = a.d, nch = a.nch, SB = a.sb;
     const int ksteps = d / 16;
+    const int kslices = ksteps + 1;                              // data K-steps + the norm slice
     const uint32_t Ahalf = (uint32_t)ksteps * 4096u;             // one part of a tile
     const uint32_t Abytes = 2u * Ahalf;
     const uint32_t Sbytes = (uint32_t)NC * 64u;                  // one (chunk, K-step) slice
     unsigned char* sA = smem;                                    // kSA x Abytes
     unsigned char* sB = smem + kSA * Abytes;                     // SB x Sbytes
+    unsigned char* sOnes = sB + (size_t)SB * Sbytes;             // 128 x 16 BF16: [1, 1, 1, 0, ...]
     const uint32_t sAaddr = (uint32_t)__cvta_generic_to_shared(sA);
     const uint32_t sBaddr = (uint32_t)__cvta_generic_to_shared(sB);
+    const uint32_t sOnesAddr = (uint32_t)__cvta_generic_to_shared(sOnes);
     volatile int* abort_v = &abort_flag;
 
+    // constant A tile of the norm K-step: row r = [1, 1, 1, 0, ..., 0] (BF16)
+    if (tid < kRows) {
+        *reinterpret_cast<uint4*>(sOnes + tc::tile_offset(tid, 0)) =
+            make_uint4(0x3f803f80u, 0x00003f80u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sOnes + tc::tile_offset(tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc::fence_proxy_async();
     if (warp == 2) tc::tmem_alloc(&tmem_base, a.tmem_cols);
     if (tid == 0) {
         for (int s = 0; s < kSA; ++s) {
@@ -192,16 +241,16 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     } else if (warp == 1) {
         // ---------------- B producer: slice q = (unit, K-step) -> stage q % SB
         if (lane == 0) {
-            const long long total = cnt * nch * ksteps;
+            const long long total = cnt * nch * kslices;
             long long q = 0;
             for (; q < total; ++q) {
                 const int slot = (int)(q % SB);
                 if (!wait_bar(&bars.b_empty[slot], (uint32_t)(((q / SB) & 1) ^ 1), abort_v, st))
                     break;
-                const long long unit = q / ksteps;
-                const int ch = (int)(unit % nch), ks = (int)(q % ksteps);
+                const long long unit = q / kslices;
+                const int ch = (int)(unit % nch), ks = (int)(q % kslices);
                 mbar_expect_tx(&bars.b_full[slot], Sbytes);
-                bulk_load(sB + (size_t)slot * Sbytes, a.Cb + ((size_t)ch * ksteps + ks) * Sbytes,
+                bulk_load(sB + (size_t)slot * Sbytes, a.Cb + ((size_t)ch * kslices + ks) * Sbytes,
                           Sbytes, &bars.b_full[slot]);
             }
             for (long long r = q > SB ? q - SB : 0; r < q; ++r)
@@ -211,7 +260,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc(1u, (uint32_t)NC, (uint32_t)kRows);
-            uint32_t use[2 * kEpiGroups] = {0u, 0u, 0u, 0u};
+            uint32_t phase = 0u;             // bit b: parity of accumulator b's next use
             long long q = 0;
             bool ok = true;
             for (long long i = 0; i < cnt && ok; ++i) {
@@ -221,24 +270,29 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 const uint32_t aBase = sAaddr + (uint32_t)sa * Abytes;
                 for (int ch = 0; ch < nch && ok; ++ch) {
                     const int b = 2 * (int)(i & 1) + (ch & 1);
-                    if (!(ok = wait_bar(&bars.acc_empty[b], (use[b] & 1u) ^ 1u, abort_v, st))) break;
+                    if (!(ok = wait_bar(&bars.acc_empty[b], ((phase >> b) & 1u) ^ 1u, abort_v, st))) break;
                     tc::fence_after_sync();
                     const uint32_t dt = tmem + (uint32_t)(b * NC);
-                    for (int ks = 0; ks < ksteps; ++ks, ++q) {
+                    for (int ks = 0; ks < kslices; ++ks, ++q) {
                         const int slot = (int)(q % SB);
                         if (!(ok = wait_bar(&bars.b_full[slot], (uint32_t)((q / SB) & 1), abort_v, st)))
                             break;
                         tc::fence_after_sync();
-                        const uint32_t ah = aBase + (uint32_t)ks * 4096u;
                         const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes;
-                        tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
-                        tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh + (uint32_t)NC * 32u), idesc, 1u);
-                        tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                        if (ks < ksteps) {
+                            const uint32_t ah = aBase + (uint32_t)ks * 4096u;
+                            tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
+                            tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh + (uint32_t)NC * 32u), idesc, 1u);
+                            tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                        } else {
+                            // + ||c||^2: ones x (nh, nm, nl)
+                            tc::mma_bf16(dt, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
+                        }
                         tc::mma_commit(&bars.b_empty[slot]);
                     }
                     if (!ok) break;
                     tc::mma_commit(&bars.acc_full[b]);
-                    ++use[b];
+                    phase ^= 1u << b;
                 }
                 if (ok) tc::mma_commit(&bars.a_empty[sa]);
             }
@@ -256,7 +310,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
         const int mode = st->mode;
         const float scaleF = st->scaleF, scaleG = st->scaleG;
         const float thr_base = 2.0f * st->cmax2;
-        uint32_t use[2] = {0u, 0u};
+        uint32_t phase = 0u;                 // bit s: parity of accumulator 2 g + s's next use
         long long qloc = 0;
         long long done = 0;
         bool ok = true;
@@ -265,54 +319,29 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             int BI = 0;
             for (int ch = 0; ch < nch; ++ch) {
                 const int b = 2 * g + (ch & 1);
-                bool w = wait_bar(&bars.acc_full[b], use[ch & 1] & 1u, abort_v, st);
+                bool w = wait_bar(&bars.acc_full[b], (phase >> (ch & 1)) & 1u, abort_v, st);
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 tc::fence_after_sync();
-                for (int c0 = 0; c0 < NC; c0 += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * NC + c0), v);
-                    const int j0 = ch * NC + c0;           // center index of v[0]
-                    const float4* cn4 = reinterpret_cast<const float4*>(c.cnorm + j0);
-                    float q1[4], q2[4];
+                // 32 columns at a time; the next load overlaps the current compare
+                uint32_t ra[32], rb[32];
+                const uint32_t cb = tmem + lane_addr + (uint32_t)(b * NC);
+                tc::tmem_ld32_async(cb, ra);
+                tc::tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
-#pragma unroll
-                    for (int gq = 0; gq < 8; ++gq) {
-                        const float4 cn = __ldg(cn4 + gq);
-                        const float w0 = v[4 * gq] + cn.x, w1 = v[4 * gq + 1] + cn.y;
-                        const float w2 = v[4 * gq + 2] + cn.z, w3 = v[4 * gq + 3] + cn.w;
-                        const int q = gq & 3;
-                        {
-                            const float k0 = pack_key(w0, 4u * gq), k1 = pack_key(w1, 4u * gq + 1u);
-                            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                            q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
-                            q1[q] = fminf(q1[q], lo);
-                        }
-                        {
-                            const float k0 = pack_key(w2, 4u * gq + 2u), k1 = pack_key(w3, 4u * gq + 3u);
-                            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                            q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
-                            q1[q] = fminf(q1[q], lo);
-                        }
-                    }
-                    const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
-                    const float l01 = fminf(q1[0], q1[1]);
-                    const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
-                    const float l23 = fminf(q1[2], q1[3]);
-                    const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
-                    const float b1 = fminf(l01, l23);
-                    if (b1 < B1) {
-                        B2 = fminf(B1, b2);
-                        B1 = b1;
-                        BI = j0 + (int)(__float_as_uint(b1) & 31u);
-                    } else {
-                        B2 = fminf(B2, b1);
+                for (int c0 = 0; c0 < NC; c0 += 64) {
+                    if (c0 + 32 < NC) tc::tmem_ld32_async(cb + (uint32_t)(c0 + 32), rb);
+                    top2_cols(ra, ch * NC + c0, B1, B2, BI);
+                    tc::tmem_wait_ld();
+                    if (c0 + 32 < NC) {
+                        if (c0 + 64 < NC) tc::tmem_ld32_async(cb + (uint32_t)(c0 + 64), ra);
+                        top2_cols(rb, ch * NC + c0 + 32, B1, B2, BI);
+                        tc::tmem_wait_ld();
                     }
                 }
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
-                ++use[ch & 1];
+                phase ^= 1u << (ch & 1);
             }
             if (!ok) break;
             // ---- decide row `row` of tile i
@@ -404,7 +433,7 @@ __global__ void convert_c_kernel(const float* __restrict__ c32, int k, int d, in
                                  unsigned char* __restrict__ Cb)
 {
     const long long total = (long long)nch * NC * d;
-    const int ksteps = d / 16;
+    const int kslices = d / 16 + 1;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(e / d), t = (int)(e - (long long)j * d);
@@ -413,9 +442,40 @@ __global__ void convert_c_kernel(const float* __restrict__ c32, int k, int d, in
         const int s = t >> 4, kc = (t >> 3) & 1, el = t & 7;
         const __nv_bfloat16 h = __float2bfloat16_rn(m);
         const __nv_bfloat16 l = __float2bfloat16_rn(m - __bfloat162float(h));
-        const size_t off = ((size_t)ch * ksteps + s) * NC * 64 + tc::tile_offset(jj, kc) + el * 2;
+        const size_t off = ((size_t)ch * kslices + s) * NC * 64 + tc::tile_offset(jj, kc) + el * 2;
         *reinterpret_cast<__nv_bfloat16*>(Cb + off) = h;
         *reinterpret_cast<__nv_bfloat16*>(Cb + off + (size_t)NC * 32) = l;
+    }
+}
+
+// Norm slice of every chunk: row j = [nh, nm, nl, 0, ...] with nh + nm + nl =
+// ||c_j||^2 up to 2^-27 relative (three round-to-nearest BF16 parts of the FP32
+// value, each residual exact in FP32); its ml half and the other columns are
+// zero.  A padding center gets the largest finite BF16, so it never wins.
+__global__ void convert_norm_kernel(const float* __restrict__ cnorm, int k, int d, int NC, int nch,
+                                    unsigned char* __restrict__ Cb)
+{
+    const int kslices = d / 16 + 1;
+    const int total = nch * NC;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        const int ch = j / NC, jj = j - ch * NC;
+        const float nrm = j < k ? cnorm[j] : 3.3895313892515355e38f;
+        const __nv_bfloat16 nh = __float2bfloat16_rn(nrm);
+        const float r1 = nrm - __bfloat162float(nh);
+        const __nv_bfloat16 nm = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(nm);
+        const __nv_bfloat16 nl = __float2bfloat16_rn(r2);
+        unsigned char* base = Cb + ((size_t)ch * kslices + (kslices - 1)) * NC * 64;
+        uint4 v0;
+        v0.x = (uint32_t)__bfloat16_as_ushort(nh) | ((uint32_t)__bfloat16_as_ushort(nm) << 16);
+        v0.y = (uint32_t)__bfloat16_as_ushort(nl);
+        v0.z = 0u;
+        v0.w = 0u;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(base + tc::tile_offset(jj, 0)) = v0;
+        *reinterpret_cast<uint4*>(base + tc::tile_offset(jj, 1)) = z;
+        *reinterpret_cast<uint4*>(base + (size_t)NC * 32 + tc::tile_offset(jj, 0)) = z;
+        *reinterpret_cast<uint4*>(base + (size_t)NC * 32 + tc::tile_offset(jj, 1)) = z;
     }
 }
 
@@ -425,15 +485,16 @@ __global__ void convert_c_kernel(const float* __restrict__ c32, int k, int d, in
 // |m - mh - ml| <= 2^-18 |m| (two round-to-nearest BF16 steps), the three
 // products miss xl.ml, (x - xh - xl) m and (xh + xl)(m - mh - ml): at most
 // 3.02 * 2^-18 |x_t||m_t| per dimension, i.e. 6.04 * 2^-18 sum_t |x_t||c_t|.
-// The FP32 accumulation of nt = 3d + 1 exact products (truncation assumed):
-// nt * 2^-23 (2 |x||c| + ||c||^2); FP32 centers and ||c||^2: 2^-23 |x||c| and
-// 2^-23 ||c||^2.  With 2 |x||c| <= X2 + C2 the sum is below k_b (2 C2 + X2).
-// Two keys of a gap, 1.0625 slack.
+// The FP32 accumulation of nt = 3d + 3 exact products (the data K-steps and
+// the three norm parts; truncation assumed): nt * 2^-23 (2 |x||c| + ||c||^2);
+// FP32 centers and ||c||^2: 2^-23 |x||c| and 2^-23 ||c||^2; the BF16 parts of
+// ||c||^2: 2^-27 ||c||^2.  With 2 |x||c| <= X2 + C2 the sum is below
+// k_b (2 C2 + X2).  Two keys of a gap, 1.0625 slack.
 float bf16_kappa(int d)
 {
-    const double nt = 3.0 * d + 1.0;
-    const double a1 = 6.04 * 0x1p-18 + 2.0 * nt * 0x1p-23 + 0x1p-23;   // |x||c|
-    const double a2 = nt * 0x1p-23 + 0x1p-23;                            // ||c||^2
+    const double nt = 3.0 * d + 3.0;
+    const double a1 = 6.04 * 0x1p-18 + 2.0 * nt * 0x1p-23 + 0x1p-23;           // |x||c|
+    const double a2 = nt * 0x1p-23 + 0x1p-23 + 0x1p-27;                         // ||c||^2
     const double kb = fmax(a1 / 2.0, (a1 / 2.0 + a2) / 2.0);
     return (float)(2.0 * kb * 1.0625);
 }
@@ -442,7 +503,7 @@ float bf16_kappa(int d)
 // the widest chunk must fit into the shared-memory budget.
 int bf16_fits(int d)
 {
-    return d <= 128 && kSA * 4 * kRows * d + 2 * 128 * 64 <= kSmemBudget;
+    return d <= 128 && kSA * 4 * kRows * d + 2 * 128 * 64 + 4096 <= kSmemBudget;
 }
 
 int assign_bf16_supported(int d, int k, const float* X)
@@ -471,7 +532,7 @@ size_t bf16_cb_bytes(int d, int k)
 {
     const int nc = bf16_chunk(d, k);
     const int nch = (k + nc - 1) / nc;
-    return (size_t)nch * nc * (size_t)d * 2 * 2;
+    return (size_t)nch * nc * 64 * (size_t)(d / 16 + 1);
 }
 
 int launch_convert_x_bf16(const float* X, long long n, int d, unsigned char* Xt, float* xn2,
@@ -500,22 +561,27 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
         ++g_launches;
         convert_c_kernel<<<(int)blocks, 256, 0, s>>>(c.c32, c.k, d, NC, nch, Cb);
         KM2_CUDA(cudaGetLastError());
+        ++g_launches;
+        convert_norm_kernel<<<(nch * NC + 255) / 256, 256, 0, s>>>(c.cnorm, c.k, d, NC, nch, Cb);
+        KM2_CUDA(cudaGetLastError());
     }
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * kEpiGroups * NC)) cols <<= 1;
     const size_t abytes = (size_t)4 * kRows * d, sbytes = (size_t)NC * 64;
-    int sb = (int)((kSmemBudget - kSA * abytes) / sbytes);
+    int sb = (int)((kSmemBudget - kSA * abytes - 4096) / sbytes);
     if (sb > kMaxSB) sb = kMaxSB;
     if (sb < 2) {
         set_last_error_text("assign_bf16: shared-memory budget too small for this d");
         return KMEANS2_ERR_UNSUPPORTED;
     }
-    const size_t smem = kSA * abytes + (size_t)sb * sbytes;
+    const size_t smem = kSA * abytes + (size_t)sb * sbytes + 4096;
     static thread_local int configured_for = -1;
     int dev = 0;
     KM2_CUDA(cudaGetDevice(&dev));
     if (configured_for != dev) {
-        KM2_CUDA(cudaFuncSetAttribute(assign_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        KM2_CUDA(cudaFuncSetAttribute(assign_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSmemBudget));
+        KM2_CUDA(cudaFuncSetAttribute(assign_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kSmemBudget));
         configured_for = dev;
     }
@@ -538,7 +604,10 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     a.kappa = bf16_kappa(d);
     a.kpack = kPackSlack;
     ++g_launches;
-    assign_bf16<<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+    if (NC == 64)
+        assign_bf16<64><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+    else
+        assign_bf16<128><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }

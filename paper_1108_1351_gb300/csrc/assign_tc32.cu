@@ -6,18 +6,29 @@
 // high part (its TF32 truncation) and the FP32 remainder: x = xh + xl,
 // m = -2c = mh + ml.  Three MMAs per K-step accumulate xh.mh + xh.ml + xl.mh
 // (the dropped xl.ml is below 2^-20 |x||m|), and one more K-step adds
-// ||c||^2 = nh + nl against a constant [1, 1, 0, ...] A column, so the
+// ||c||^2 = nh + nl against a constant [1, 1, 0, ...] A tile, so the
 // accumulator holds D_j = ||c_j||^2 - 2 x.c_j for all centers of a 128-point
-// tile.  The CUDA cores only run the epilogue: packed-key top-2, the near-tie
-// flag (a bound that covers the split, the tensor core's FP32 accumulation and
-// the key packing), labels and the exact fixed-point cluster sums.
+// tile.  The CUDA cores only split the points and run the epilogue: packed-key
+// top-2, the near-tie flag (a bound that covers the split, the tensor core's
+// FP32 accumulation and the key packing), labels and the exact fixed-point
+// cluster sums.
 //
-// Pipeline of one CTA (one warpgroup; thread t owns row t of every tile and
-// TMEM lane t): cp.async fetches each thread's own point two tiles ahead;
-// produce(i) splits tile i into the K-major shared A tiles and thread 0 issues
-// its MMAs into TMEM buffer i % 2; the epilogue of tile i runs while the MMAs
-// of tile i + 1 execute.  Every mbarrier wait is bounded: on timeout the CTA
-// records an error, waits (bounded) for its own MMAs, frees TMEM and exits.
+// Warp-specialised pipeline, one CTA per SM, 14 warps:
+//   warp 0      loader: one bulk TMA copy per 128-point tile of raw X rows into
+//               an RS-stage ring (the rows stay there until the tile's
+//               epilogue is done: the sums read them back);
+//   warps 1-4   producers: thread r splits row r into the hi / lo A tiles of an
+//               SA-stage ring (K-major core-matrix layout, tc_common.cuh);
+//   warp 5      MMA issuer: 3 KD + 1 MMAs (M 128, N npad, K 8) per tile into a
+//               TMEM accumulator, then tcgen05.commit hands it on;
+//   warps 6-13  two epilogue groups taking alternate tiles, each with NB (1 or
+//               2) accumulators of npad columns: thread r owns row r (TMEM lane)
+//               and decides it; each warp keeps its own shared-memory partial
+//               sums (when they fit), flushed by the warp alone.
+// The B operand (every center's -2c hi / lo per K-step and ||c||^2 hi / lo) is
+// built once per launch and stays in shared memory.  Roles are coupled only by
+// mbarriers; every wait is bounded, and on a timeout the CTA records an error,
+// lets its own copies and MMAs finish (bounded), frees TMEM and exits.
 #include <cfloat>
 #include <cstdint>
 
@@ -28,18 +39,15 @@ namespace km2 {
 
 namespace {
 
-constexpr int kThreads = 128;       // one warpgroup
-constexpr int kRows = 128;          // points per tile (UMMA M)
-constexpr int kStepBytes = kRows * 32;   // one K-step (8 TF32) of a 128-row A tile
+constexpr int kWarps = 14;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kEpiWarps = 8;
+constexpr int kRows = 128;                 // points per tile (UMMA M)
+constexpr int kStepBytes = kRows * 32;     // one K-step (8 TF32) of a 128-row A tile
+constexpr int kMaxRS = 8, kMaxSA = 4;
+constexpr int kSmemBudget = 210 * 1024;
 constexpr int kWaitTries = 1 << 22;
-
-template <int D>
-struct TcCfg {
-    static constexpr int KD = (D + 7) / 8;            // data K-steps
-    static constexpr int XV = D >= 4 ? 4 : D;         // floats per cp.async copy
-    static constexpr int NX = D / XV;                 // copies per point
-    static constexpr int FLUSH_TILES = kFlushPoints / kRows;
-};
+constexpr int kWarpFlushTiles = kFlushPoints / 32;   // 32 points per tile and warp
 
 __device__ __forceinline__ float tf32_hi(float v)
 {
@@ -51,72 +59,125 @@ __device__ __forceinline__ float pack_key(float v, unsigned j)
     return __uint_as_float((__float_as_uint(v) & ~31u) | j);
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(mbar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes,
+                                          uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(sdst)),
+        "l"(gsrc), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(mbar))
+        : "memory");
+}
+
+// Bounded wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                         StageState* st)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < kWaitTries; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 63) == 63 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(&st->error, kErrTimeout);
+    return false;
+}
+
+template <int D>
+struct TcCfg {
+    static constexpr int KD = (D + 7) / 8;                     // data K-steps
+    static constexpr uint32_t ABYTES = 2u * KD * kStepBytes;   // hi + lo A tiles
+};
+
 struct TcLayout {
-    uint32_t a_off;      // 2 stages x 2 parts (hi, lo) x KD steps x kStepBytes
-    uint32_t an_off;     // constant norm A tile (kStepBytes)
-    uint32_t b_off;      // (2 KD + 1) x npad x 32 bytes: mh_s, ml_s ..., norm
-    uint32_t xs_off;     // 2 stages x kRows x D floats (thread-major)
-    uint32_t ls_off;     // 2 stages x kRows ints
-    uint32_t acc_off;    // k x D int64 + k int32 (optional)
-    uint32_t total;
+    int rs, sa, nb;          // raw ring, A ring, accumulators per epilogue group
+    int sacc;                // per-warp shared-memory partial sums
+    uint32_t a_off, ones_off, b_off, raw_off, acc_off, acc_bytes, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int D, int KD, int npad, int k, bool with_acc)
+__host__ __device__ inline TcLayout tc_layout(int D, int npad, int k, int rs, int sa, int sacc)
 {
+    const int KD = (D + 7) / 8;
     TcLayout L;
+    L.rs = rs;
+    L.sa = sa;
+    L.nb = 4 * npad <= 512 ? 2 : 1;
+    L.sacc = sacc;
     uint32_t o = 0;
     L.a_off = o;
-    o += 2u * 2u * (uint32_t)KD * kStepBytes;
-    L.an_off = o;
+    o += (uint32_t)sa * 2u * KD * kStepBytes;
+    L.ones_off = o;
     o += kStepBytes;
     L.b_off = o;
     o += (uint32_t)(2 * KD + 1) * (uint32_t)npad * 32u;
     o = align_up(o, 128);
-    L.xs_off = o;
-    o += 2u * kRows * (uint32_t)D * 4u;
-    L.ls_off = o;
-    o += 2u * kRows * 4u;
+    L.raw_off = o;
+    o += (uint32_t)rs * kRows * (uint32_t)D * 4u;
     o = align_up(o, 16);
     L.acc_off = o;
-    if (with_acc) o += (uint32_t)k * (uint32_t)D * 8u + (uint32_t)k * 4u;
+    L.acc_bytes = align_up((uint32_t)k * (uint32_t)D * 8u + (uint32_t)k * 4u, 16);
+    if (sacc) o += (uint32_t)kEpiWarps * L.acc_bytes;
     L.total = align_up(o, 16);
     return L;
 }
 
+struct TcBars {
+    uint64_t raw_full[kMaxRS], raw_empty[kMaxRS];
+    uint64_t a_full[kMaxSA], a_empty[kMaxSA];
+    uint64_t acc_full[4], acc_empty[4];
+    uint64_t drain;
+};
+
 template <int D>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
             StageState* st, Accum acc, int* __restrict__ list, float kappa, float kpack,
-            int npad, uint32_t tmem_cols, int use_sacc)
+            int npad, uint32_t tmem_cols, TcLayout L)
 {
     using C = TcCfg<D>;
     constexpr int KD = C::KD;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ TcBars bars;
     __shared__ uint32_t tmem_base;
-    __shared__ unsigned long long sq;
+    __shared__ int abort_flag;
 
     if (st->error) return;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = c.k;
-    const TcLayout L = tc_layout(D, KD, npad, k, use_sacc != 0);
+    const int RS = L.rs, SA = L.sa, NB = L.nb;
     unsigned char* sA = smem + L.a_off;
-    unsigned char* sAn = smem + L.an_off;
+    unsigned char* sOnes = smem + L.ones_off;
     unsigned char* sB = smem + L.b_off;
-    float* xs = reinterpret_cast<float*>(smem + L.xs_off);
-    int* ls = reinterpret_cast<int*>(smem + L.ls_off);
-    long long* sacc = reinterpret_cast<long long*>(smem + L.acc_off);
-    int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);
+    float* raw = reinterpret_cast<float*>(smem + L.raw_off);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    const int mode = st->mode;
-    const float scaleF = st->scaleF, scaleG = st->scaleG;
-    const float thr_base = 2.0f * st->cmax2;
-    const uint32_t idesc = tc::instr_desc(2u, (uint32_t)npad, (uint32_t)kRows);
+    volatile int* abort_v = &abort_flag;
 
     // ---- B operand: -2c split in TF32 hi / lo per K-step, then ||c||^2 hi / lo
-    const int bitems = npad * (2 * KD + 1) * 2;        // (row, tile, chunk)
+    const int bitems = npad * (2 * KD + 1) * 2;        // (row, tile, 16-byte chunk)
     for (int e = tid; e < bitems; e += kThreads) {
         const int j = e % npad;
         const int rest = e / npad;
@@ -135,7 +196,8 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                 }
             }
         } else if (kc == 0) {
-            const float nrm = j < k ? c.cnorm[j] : 1e30f;   // padding center: never the best
+            // a padding center gets the largest finite TF32 norm: never the best
+            const float nrm = j < k ? c.cnorm[j] : 3.3895313892515355e38f;
             const float h = tf32_hi(nrm);
             v[0] = h;
             v[1] = nrm - h;
@@ -143,18 +205,33 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
         *reinterpret_cast<float4*>(sB + (size_t)tile * npad * 32 + tc::tile_offset(j, kc)) =
             make_float4(v[0], v[1], v[2], v[3]);
     }
-    // constant A column pair [1, 1] for the norm K-step
-    *reinterpret_cast<float4*>(sAn + tc::tile_offset(tid, 0)) = make_float4(1.f, 1.f, 0.f, 0.f);
-    *reinterpret_cast<float4*>(sAn + tc::tile_offset(tid, 1)) = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (use_sacc) {
-        for (int e = tid; e < k * D; e += kThreads) sacc[e] = 0;
-        for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
+    // constant A tile [1, 1, 0, ...] for the norm K-step
+    if (tid < kRows) {
+        *reinterpret_cast<float4*>(sOnes + tc::tile_offset(tid, 0)) = make_float4(1.f, 1.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(sOnes + tc::tile_offset(tid, 1)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_base, tmem_cols);
+    if (L.sacc) {
+        long long* s0 = reinterpret_cast<long long*>(smem + L.acc_off);
+        const int words = (int)((uint32_t)kEpiWarps * L.acc_bytes / 8u);
+        for (int e = tid; e < words; e += kThreads) s0[e] = 0;
+    }
+    if (warp == 5) tc::tmem_alloc(&tmem_base, tmem_cols);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
-        sq = 0;
+        for (int s = 0; s < kMaxRS; ++s) {
+            tc::mbar_init(&bars.raw_full[s], 1);
+            tc::mbar_init(&bars.raw_empty[s], 4);      // the 4 warps of the consuming group
+        }
+        for (int s = 0; s < kMaxSA; ++s) {
+            tc::mbar_init(&bars.a_full[s], 4);         // the 4 producer warps
+            tc::mbar_init(&bars.a_empty[s], 1);
+        }
+        for (int b = 0; b < 4; ++b) {
+            tc::mbar_init(&bars.acc_full[b], 1);
+            tc::mbar_init(&bars.acc_empty[b], 4);
+        }
+        tc::mbar_init(&bars.drain, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -166,223 +243,252 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
     const long long cnt = (long long)blockIdx.x < ntiles
                               ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
-    // cp.async of this thread's own point of local tile i into stage i % 2
-    auto prefetch = [&](long long i, unsigned dep) {
-        asm volatile("" ::"r"(dep) : "memory");
-        if (i < cnt) {
-            const long long p = (blockIdx.x + i * gridDim.x) * kRows + tid;
-            if (p < n) {
-                const int sg = (int)(i & 1);
-                const float* src = X + p * D;
-#pragma unroll
-                for (int q = 0; q < C::NX; ++q) {
-                    float* dst = xs + ((size_t)(sg * C::NX + q) * kThreads + tid) * C::XV;
-                    if constexpr (C::XV == 4) cp_async16(dst, src + 4 * q);
-                    else if constexpr (C::XV == 2) cp_async8(dst, src + 2 * q);
-                    else cp_async4(dst, src + q);
-                }
-                if (mode == kModeDelta) cp_async4(ls + sg * kThreads + tid, labels + p);
+    if (warp == 0) {
+        // ---------------- loader: raw rows of tile i -> raw stage i % RS
+        if (lane == 0) {
+            long long issued = 0;
+            for (long long i = 0; i < cnt; ++i) {
+                const int rs = (int)(i % RS);
+                if (!wait_bar(&bars.raw_empty[rs], (uint32_t)(((i / RS) & 1) ^ 1), abort_v, st))
+                    break;
+                const long long tile = blockIdx.x + i * gridDim.x;
+                const long long rows = n - tile * kRows < kRows ? n - tile * kRows : kRows;
+                const uint32_t bytes = (uint32_t)rows * (uint32_t)D * 4u;   // D * 4 is a multiple of 16
+                mbar_expect_tx(&bars.raw_full[rs], bytes);
+                bulk_load(raw + (size_t)rs * kRows * D, X + tile * kRows * D, bytes,
+                          &bars.raw_full[rs]);
+                issued = i + 1;
             }
+            // let this CTA's own copies land before it can exit
+            for (long long i = issued > RS ? issued - RS : 0; i < issued; ++i)
+                tc::mbar_wait(&bars.raw_full[i % RS], (uint32_t)((i / RS) & 1), kWaitTries);
         }
-        cp_async_commit();
-    };
-
-    // split tile i into the A tiles of stage i % 2 and issue its MMAs
-    auto produce = [&](long long i, float* xr, int& old) {
-        const int sg = (int)(i & 1);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        const long long p = (blockIdx.x + i * gridDim.x) * kRows + tid;
-        if (p < n) {
+    } else if (warp <= 4) {
+        // ---------------- producers: thread r splits row r of tile i into A stage i % SA
+        const int r = tid - 32;
+        for (long long i = 0; i < cnt; ++i) {
+            const int rs = (int)(i % RS), sa = (int)(i % SA);
+            bool ok = wait_bar(&bars.raw_full[rs], (uint32_t)((i / RS) & 1), abort_v, st);
+            ok = ok && wait_bar(&bars.a_empty[sa], (uint32_t)(((i / SA) & 1) ^ 1), abort_v, st);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const long long tile = blockIdx.x + i * gridDim.x;
+            const bool valid = tile * kRows + r < n;
+            float x[8 * KD];
+            const float* src = raw + (size_t)rs * kRows * D + (size_t)r * D;
 #pragma unroll
-            for (int q = 0; q < C::NX; ++q) {
-                const float* src = xs + ((size_t)(sg * C::NX + q) * kThreads + tid) * C::XV;
-#pragma unroll
-                for (int e = 0; e < C::XV; ++e) xr[q * C::XV + e] = src[e];
+            for (int q = 0; q < D / 4; ++q) {
+                const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * q)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
             }
-            old = (mode == kModeDelta) ? ls[sg * kThreads + tid] : -1;
-        } else {
 #pragma unroll
-            for (int t = 0; t < D; ++t) xr[t] = 0.f;
-            old = -1;
-        }
-        unsigned dep = 0;
-#pragma unroll
-        for (int t = 0; t < D; ++t) dep ^= __float_as_uint(xr[t]);
-        prefetch(i + 2, dep ^ (unsigned)old);
-#pragma unroll
-        for (int s = 0; s < KD; ++s) {
-#pragma unroll
-            for (int kc = 0; kc < 2; ++kc) {
-                float v[4], h[4], l[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = 8 * s + 4 * kc + q;
-                    v[q] = t < D ? xr[t] : 0.f;
-                    h[q] = tf32_hi(v[q]);
-                    l[q] = v[q] - h[q];
-                }
-                const uint32_t off = tc::tile_offset(tid, kc);
-                *reinterpret_cast<float4*>(sA + ((size_t)(sg * 2 + 0) * KD + s) * kStepBytes + off) =
-                    make_float4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<float4*>(sA + ((size_t)(sg * 2 + 1) * KD + s) * kStepBytes + off) =
-                    make_float4(l[0], l[1], l[2], l[3]);
-            }
-        }
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
-            const uint32_t d_tmem = tmem + (uint32_t)(sg * npad);
+            for (int t = D; t < 8 * KD; ++t) x[t] = 0.f;
+            unsigned char* a = sA + (size_t)sa * C::ABYTES;
 #pragma unroll
             for (int s = 0; s < KD; ++s) {
-                const uint32_t ah = sbase + L.a_off + (uint32_t)(((sg * 2 + 0) * KD + s) * kStepBytes);
-                const uint32_t al = sbase + L.a_off + (uint32_t)(((sg * 2 + 1) * KD + s) * kStepBytes);
-                const uint32_t bh = sbase + L.b_off + (uint32_t)((2 * s + 0) * npad * 32);
-                const uint32_t bl = sbase + L.b_off + (uint32_t)((2 * s + 1) * npad * 32);
-                tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bh), idesc, s > 0 ? 1u : 0u);
-                tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
-                tc::mma_tf32(d_tmem, tc::smem_desc(al), tc::smem_desc(bh), idesc, 1u);
-            }
-            const uint32_t bn = sbase + L.b_off + (uint32_t)(2 * KD * npad * 32);
-            tc::mma_tf32(d_tmem, tc::smem_desc(sbase + L.an_off), tc::smem_desc(bn), idesc, 1u);
-            tc::mma_commit(&mbar[sg]);
-        }
-    };
-
-    prefetch(0, 0u);
-    prefetch(1, 0u);
-    float xc[D], xn[D];
-    int oldc = -1, oldn = -1;
-    long long qloc = 0;
-    bool failed = false;
-    if (cnt > 0) produce(0, xc, oldc);
-    for (long long i = 0; i < cnt; ++i) {
-        if (i + 1 < cnt) produce(i + 1, xn, oldn);
-        const int sg = (int)(i & 1);
-        bool ok = tc::mbar_wait(&mbar[sg], (uint32_t)((i >> 1) & 1), kWaitTries);
-        if (!__syncthreads_and(ok)) {
-            // give up: record the error, let this CTA's own MMAs finish, then leave
-            if (tid == 0) atomicExch(&st->error, kErrTimeout);
-            tc::mbar_wait(&mbar[sg], (uint32_t)((i >> 1) & 1), kWaitTries);
-            if (i + 1 < cnt) tc::mbar_wait(&mbar[sg ^ 1], (uint32_t)(((i + 1) >> 1) & 1), kWaitTries);
-            failed = true;
-            break;
-        }
-        tc::fence_after_sync();
-        // ---- epilogue of tile i
-        const long long p = (blockIdx.x + i * gridDim.x) * kRows + tid;
-        const bool valid = p < n;
-        float B1 = INFINITY, B2 = INFINITY;
-        int BI = 0;
-        for (int c0 = 0; c0 < npad; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(sg * npad + c0), v);
-            // four independent top-2 chains over interleaved column pairs, then merged
-            float q1[4], q2[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
+                for (int kc = 0; kc < 2; ++kc) {
+                    float h[4], l[4];
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int jj = j + 2 * q;
-                    const float k0 = pack_key(v[jj], (unsigned)jj);
-                    const float k1 = pack_key(v[jj + 1], (unsigned)jj + 1u);
-                    const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                    q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
-                    q1[q] = fminf(q1[q], lo);
+                    for (int q = 0; q < 4; ++q) {
+                        const float v = x[8 * s + 4 * kc + q];
+                        h[q] = tf32_hi(v);
+                        l[q] = v - h[q];
+                    }
+                    const uint32_t off = tc::tile_offset(r, kc);
+                    *reinterpret_cast<float4*>(a + (size_t)s * kStepBytes + off) =
+                        make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(a + (size_t)(KD + s) * kStepBytes + off) =
+                        make_float4(l[0], l[1], l[2], l[3]);
                 }
             }
-            const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
-            const float l01 = fminf(q1[0], q1[1]);
-            const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
-            const float l23 = fminf(q1[2], q1[3]);
-            const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
-            const float b1 = fminf(l01, l23);
-            if (b1 < B1) {
-                B2 = fminf(B1, b2);
-                B1 = b1;
-                BI = c0 | (int)(__float_as_uint(b1) & 31u);
-            } else {
-                B2 = fminf(B2, b1);
+            tc::fence_proxy_async();        // generic writes -> visible to the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.a_full[sa]);
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::instr_desc(2u, (uint32_t)npad, (uint32_t)kRows);
+            uint32_t phase = 0u;             // bit b: parity of accumulator b's next use
+            for (long long i = 0; i < cnt; ++i) {
+                const int sa = (int)(i % SA);
+                const int b = (int)(i & 1) * NB + (int)((i >> 1) % NB);
+                if (!wait_bar(&bars.a_full[sa], (uint32_t)((i / SA) & 1), abort_v, st)) break;
+                if (!wait_bar(&bars.acc_empty[b], ((phase >> b) & 1u) ^ 1u, abort_v, st)) break;
+                tc::fence_after_sync();
+                const uint32_t d_tmem = tmem + (uint32_t)(b * npad);
+                const uint32_t ab = sbase + L.a_off + (uint32_t)sa * C::ABYTES;
+#pragma unroll
+                for (int s = 0; s < KD; ++s) {
+                    const uint32_t ah = ab + (uint32_t)s * kStepBytes;
+                    const uint32_t al = ab + (uint32_t)(KD + s) * kStepBytes;
+                    const uint32_t bh = sbase + L.b_off + (uint32_t)((2 * s + 0) * npad * 32);
+                    const uint32_t bl = sbase + L.b_off + (uint32_t)((2 * s + 1) * npad * 32);
+                    tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bh), idesc, s > 0 ? 1u : 0u);
+                    tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
+                    tc::mma_tf32(d_tmem, tc::smem_desc(al), tc::smem_desc(bh), idesc, 1u);
+                }
+                const uint32_t bn = sbase + L.b_off + (uint32_t)(2 * KD * npad * 32);
+                tc::mma_tf32(d_tmem, tc::smem_desc(sbase + L.ones_off), tc::smem_desc(bn), idesc, 1u);
+                tc::mma_commit(&bars.acc_full[b]);
+                phase ^= 1u << b;
+                tc::mma_commit(&bars.a_empty[sa]);
             }
+            // every MMA issued by this thread has completed once `drain` flips
+            tc::mma_commit(&bars.drain);
+            tc::mbar_wait(&bars.drain, 0u, kWaitTries);
         }
-        tc::fence_before_sync();
-        float xn2 = 0.f;
+    } else {
+        // ---------------- epilogue group g: tiles i = g, g + 2, ...
+        const int ew = warp - 6;
+        const int g = ew >> 2;
+        const int quarter = warp & 3;                      // TMEM lanes 32 * (warp % 4) ...
+        const int row = 32 * quarter + lane;
+        const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
+        const int mode = st->mode;
+        const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float thr_base = 2.0f * st->cmax2;
+        long long* sacc = reinterpret_cast<long long*>(smem + L.acc_off + (size_t)ew * L.acc_bytes);
+        int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);
+        uint32_t phase = 0u;                 // bit s: parity of accumulator g NB + s's next use
+        long long qloc = 0;
+        long long done = 0;
+        for (long long i = g; i < cnt; i += 2) {
+            const int slot = (int)((i >> 1) % NB);
+            const int b = g * NB + slot;
+            const int rs = (int)(i % RS);
+            bool w = wait_bar(&bars.acc_full[b], (phase >> slot) & 1u, abort_v, st);
+            w = w && wait_bar(&bars.raw_full[rs], (uint32_t)((i / RS) & 1), abort_v, st);
+            if (!__all_sync(0xffffffffu, w)) break;
+            tc::fence_after_sync();
+            float B1 = INFINITY, B2 = INFINITY;
+            int BI = 0;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * npad + c0), v);
+                float q1[4], q2[4];
 #pragma unroll
-        for (int t = 0; t < D; ++t) xn2 = fmaf(xc[t], xc[t], xn2);
-        const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1) + fabsf(B2));
-        const bool flag = valid && (B2 - B1 <= thr);
-        if (mode == kModeFull && valid) {
+                for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
 #pragma unroll
-            for (int t = 0; t < D; ++t) qloc += sq_fixed(xc[t], scaleG);
-        }
-        recheck_append(flag, (int)p, list, &st->recheck_count);
-        if (valid && !flag && BI != oldc) {
-            const int lab = BI, old = oldc;
+                for (int j = 0; j < 32; j += 8) {
 #pragma unroll
-            for (int t = 0; t < D; ++t) {
-                const long long v = to_fixed(xc[t], scaleF);
-                if (use_sacc) {
-                    atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * D + t),
-                              (unsigned long long)v);
-                    if (old >= 0)
-                        atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + t),
-                                  (unsigned long long)(-v));
+                    for (int q = 0; q < 4; ++q) {
+                        const int jj = j + 2 * q;
+                        const float k0 = pack_key(v[jj], (unsigned)jj);
+                        const float k1 = pack_key(v[jj + 1], (unsigned)jj + 1u);
+                        const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+                        q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
+                        q1[q] = fminf(q1[q], lo);
+                    }
+                }
+                const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
+                const float l01 = fminf(q1[0], q1[1]);
+                const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
+                const float l23 = fminf(q1[2], q1[3]);
+                const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
+                const float b1 = fminf(l01, l23);
+                if (b1 < B1) {
+                    B2 = fminf(B1, b2);
+                    B1 = b1;
+                    BI = c0 | (int)(__float_as_uint(b1) & 31u);
                 } else {
-                    split_add(acc.s_lo + (long long)lab * D + t, acc.s_hi + (long long)lab * D + t, v);
-                    if (old >= 0)
-                        split_add(acc.s_lo + (long long)old * D + t,
-                                  acc.s_hi + (long long)old * D + t, -v);
+                    B2 = fminf(B2, b1);
                 }
             }
-            if (use_sacc) {
-                atomicAdd(scnt + lab, 1);
-                if (old >= 0) atomicAdd(scnt + old, -1);
-            } else {
-                atomicAdd(acc.cnt + lab, 1ull);
-                if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
-            }
-            labels[p] = lab;
-        }
-        // static flush schedule: at most FLUSH_TILES tiles (2^16 points) per partial
-        if (((i + 1) % C::FLUSH_TILES) == 0 || i + 1 == cnt) {
-            if (qloc) atomicAdd(&sq, (unsigned long long)qloc);
-            qloc = 0;
-            __syncthreads();
-            if (use_sacc) {
-                for (int e = tid; e < k * D; e += kThreads) {
-                    const long long v = sacc[e];
-                    if (v) {
-                        split_add(acc.s_lo + e, acc.s_hi + e, v);
-                        sacc[e] = 0;
-                    }
-                }
-                for (int e = tid; e < k; e += kThreads) {
-                    const int v = scnt[e];
-                    if (v) {
-                        atomicAdd(acc.cnt + e, (unsigned long long)(long long)v);
-                        scnt[e] = 0;
-                    }
-                }
-            }
-            if (tid == 0) {
-                if (sq) split_add(&st->q_lo, &st->q_hi, (long long)sq);
-                sq = 0;
-            }
-            __syncthreads();
-        }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
+            phase ^= 1u << slot;
+
+            // ---- decide row `row` of tile i from its raw FP32 values
+            const long long tile = blockIdx.x + i * gridDim.x;
+            const long long p = tile * kRows + row;
+            const bool valid = p < n;
+            float x[D];
+            const float* src = raw + (size_t)rs * kRows * D + (size_t)row * D;
 #pragma unroll
-        for (int t = 0; t < D; ++t) xc[t] = xn[t];
-        oldc = oldn;
+            for (int q = 0; q < D / 4; ++q) {
+                const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * q)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+            }
+            float xn2 = 0.f;
+#pragma unroll
+            for (int t = 0; t < D; ++t) xn2 = fmaf(x[t], x[t], xn2);
+            const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1) + fabsf(B2));
+            const bool flag = valid && (B2 - B1 <= thr);
+            if (mode == kModeFull && valid) {
+#pragma unroll
+                for (int t = 0; t < D; ++t) qloc += sq_fixed(x[t], scaleG);
+            }
+            recheck_append(flag, (int)p, list, &st->recheck_count);
+            if (valid && !flag) {
+                const int old = (mode == kModeDelta) ? labels[p] : -1;
+                if (BI != old) {
+#pragma unroll
+                    for (int t = 0; t < D; ++t) {
+                        const long long val = to_fixed(x[t], scaleF);
+                        if (L.sacc) {
+                            atomicAdd(reinterpret_cast<unsigned long long*>(sacc + BI * D + t),
+                                      (unsigned long long)val);
+                            if (old >= 0)
+                                atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + t),
+                                          (unsigned long long)(-val));
+                        } else {
+                            split_add(acc.s_lo + (long long)BI * D + t,
+                                      acc.s_hi + (long long)BI * D + t, val);
+                            if (old >= 0)
+                                split_add(acc.s_lo + (long long)old * D + t,
+                                          acc.s_hi + (long long)old * D + t, -val);
+                        }
+                    }
+                    if (L.sacc) {
+                        atomicAdd(scnt + BI, 1);
+                        if (old >= 0) atomicAdd(scnt + old, -1);
+                    } else {
+                        atomicAdd(acc.cnt + BI, 1ull);
+                        if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                    }
+                    labels[p] = BI;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.raw_empty[rs]);
+            // static flush schedule: at most kWarpFlushTiles tiles (2^16 points) per partial
+            ++done;
+            if (done % kWarpFlushTiles == 0 || i + 2 >= cnt) {
+                long long qs = qloc;
+                for (int o = 16; o; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
+                if (lane == 0 && qs) split_add(&st->q_lo, &st->q_hi, qs);
+                qloc = 0;
+                if (L.sacc) {
+                    __syncwarp();
+                    for (int e = lane; e < k * D; e += 32) {
+                        const long long vv = sacc[e];
+                        if (vv) {
+                            split_add(acc.s_lo + e, acc.s_hi + e, vv);
+                            sacc[e] = 0;
+                        }
+                    }
+                    for (int e = lane; e < k; e += 32) {
+                        const int vv = scnt[e];
+                        if (vv) {
+                            atomicAdd(acc.cnt + e, (unsigned long long)(long long)vv);
+                            scnt[e] = 0;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
     }
-    (void)failed;
-    cp_async_wait_all();
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+    if (warp == 5) tc::tmem_dealloc(tmem, tmem_cols);
 }
+
+}  // namespace
 
 // Per-key error bound of the 3xTF32 form, as a multiple of (2 C2 + X2),
 // doubled for the two keys of the gap (derivation in the design notes):
@@ -398,51 +504,46 @@ inline float tc32_kappa(int KD)
     return (float)(2.0 * per_key * 1.0625);
 }
 
+namespace {
+
 template <int D>
 int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageState* st,
               const Accum& acc, int* list, cudaStream_t s, int sm_count)
 {
     using C = TcCfg<D>;
     const int npad = (c.k + 31) / 32 * 32;
+    // ring depths and per-warp partial sums, deepest first, within the budget
+    TcLayout L{};
+    bool found = false;
+    for (int sacc = 1; sacc >= 0 && !found; --sacc)
+        for (int rs = kMaxRS; rs >= 3 && !found; --rs)
+            for (int sa = kMaxSA; sa >= 2 && !found; --sa) {
+                if (sa > rs - 1) continue;
+                L = tc_layout(D, npad, c.k, rs, sa, sacc);
+                found = L.total <= (uint32_t)kSmemBudget;
+            }
+    if (!found) {
+        set_last_error_text("assign_tc32: shared-memory budget too small for this shape");
+        return KMEANS2_ERR_UNSUPPORTED;
+    }
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * npad)) cols <<= 1;
-    const bool with_acc = tc_layout(D, C::KD, npad, c.k, true).total <= 160u * 1024u;
-    const TcLayout L = tc_layout(D, C::KD, npad, c.k, with_acc);
+    while (cols < (uint32_t)(2 * L.nb * npad)) cols <<= 1;
     static thread_local int configured_for = -1;
     int dev = 0;
     KM2_CUDA(cudaGetDevice(&dev));
     if (configured_for != dev) {
         KM2_CUDA(cudaFuncSetAttribute(assign_tc32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      200 * 1024));
+                                      kSmemBudget));
         configured_for = dev;
     }
-    // CTAs per SM from the kernel's own resources (the occupancy API does not
-    // account for tensor-memory kernels the way the hardware schedules them):
-    // registers, shared memory (228 KB per SM, 1 KB reserved per CTA), warps,
-    // and the 512 TMEM columns each CTA takes `cols` of.
-    static thread_local int regs_per_thread = 0;
-    if (regs_per_thread == 0) {
-        cudaFuncAttributes fa;
-        KM2_CUDA(cudaFuncGetAttributes(&fa, assign_tc32<D>));
-        regs_per_thread = fa.numRegs > 0 ? fa.numRegs : 255;
-    }
-    const int by_regs = 65536 / (((regs_per_thread * kThreads) + 255) / 256 * 256);
-    const int by_smem = (int)((228u * 1024u) / (L.total + 1024u + 1024u));
-    const int by_warps = 64 / (kThreads / 32);
-    const int by_tmem = (int)(512u / cols);
-    int per_sm = by_regs;
-    if (per_sm > by_smem) per_sm = by_smem;
-    if (per_sm > by_warps) per_sm = by_warps;
-    if (per_sm > by_tmem) per_sm = by_tmem;
-    if (per_sm < 1) return KMEANS2_ERR_UNSUPPORTED;
     const long long tiles = (n + kRows - 1) / kRows;
-    long long grid = (long long)sm_count * per_sm;
+    long long grid = sm_count;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
     ++g_launches;
     assign_tc32<D><<<(int)grid, kThreads, L.total, s>>>(X, n, c, labels, st, acc, list,
                                                         tc32_kappa(C::KD), kPackSlack, npad, cols,
-                                                        with_acc ? 1 : 0);
+                                                        L);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }

@@ -473,6 +473,17 @@ __global__ void batch_control_kernel(int* active, int* iter, int* next_item, int
     cudaGraphSetConditional(handle, (a > 0 && it < cap) ? 1u : 0u);
 }
 
+// Host-driven form of batch_control_kernel (profiled runs): hands the number of
+// jobs still running to the host instead of a graph condition.
+__global__ void batch_step_kernel(int* active, int* iter, int* next_item, int nclass, int* out)
+{
+    const int a = *active;
+    *active = 0;
+    for (int c = 0; c < nclass; ++c) next_item[c] = 0;
+    ++*iter;
+    *out = a;
+}
+
 // ---------------------------------------------------------------- host
 
 int dclass(int d)
@@ -621,7 +632,8 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         int* counters = nullptr;
         KM2_TRY(ws.alloc((void**)&arena, total, s));
         KM2_TRY(ws.alloc((void**)&dinst, sizeof(BatchInst) * (size_t)count, s));
-        KM2_TRY(ws.alloc((void**)&counters, 8 * sizeof(int), s));   // active, iteration, 6 item counters
+        // active, iteration, 6 item counters, active count handed to the host
+        KM2_TRY(ws.alloc((void**)&counters, 9 * sizeof(int), s));
         for (int j = 0; j < count; ++j) {
             const kmeans2_job& J = jobs[j];
             BatchInst& I = hi[j];
@@ -663,7 +675,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         }
         KM2_CUDA(cudaMemcpyAsync(dinst, hi.data(), sizeof(BatchInst) * (size_t)count,
                                  cudaMemcpyHostToDevice, s));
-        KM2_CUDA(cudaMemsetAsync(counters, 0, 8 * sizeof(int), s));
+        KM2_CUDA(cudaMemsetAsync(counters, 0, 9 * sizeof(int), s));
         g_launches += 3;
         batch_sample_kernel<<<count, kThreads, 0, s>>>(dinst);
         batch_gather_kernel<<<count, kThreads, 0, s>>>(dinst);
@@ -724,11 +736,74 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         }
 
         KM2_CUDA(cudaMemsetAsync(counters + 2, 0, 6 * sizeof(int), s));
+        // one side stream per dimension class: the classes' distance kernels run
+        // side by side (parallel branches of the graph body)
+        std::vector<cudaStream_t> side(classes.size(), nullptr);
+        std::vector<cudaEvent_t> joins(classes.size(), nullptr);
+        cudaEvent_t fork = nullptr;
+        KM2_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (size_t c = 0; c < classes.size(); ++c) {
+            KM2_CUDA(cudaStreamCreateWithFlags(&side[c], cudaStreamNonBlocking));
+            KM2_CUDA(cudaEventCreateWithFlags(&joins[c], cudaEventDisableTiming));
+        }
+        auto destroy_side = [&]() {
+            for (size_t c = 0; c < classes.size(); ++c) {
+                if (side[c]) cudaStreamDestroy(side[c]);
+                if (joins[c]) cudaEventDestroy(joins[c]);
+            }
+            cudaEventDestroy(fork);
+        };
+        auto launch_classes = [&]() -> int {
+            if (cudaEventRecord(fork, s) != cudaSuccess) return KMEANS2_ERR_CUDA;
+            for (size_t c = 0; c < classes.size(); ++c) {
+                if (cudaStreamWaitEvent(side[c], fork, 0) != cudaSuccess) return KMEANS2_ERR_CUDA;
+                const int r = launch_class(classes[c].dc, dinst, classes[c].dev, classes[c].count,
+                                           counters + 2 + c, side[c], ws.sm_count);
+                if (r != KMEANS2_OK) return r;
+                if (cudaEventRecord(joins[c], side[c]) != cudaSuccess) return KMEANS2_ERR_CUDA;
+                if (cudaStreamWaitEvent(s, joins[c], 0) != cudaSuccess) return KMEANS2_ERR_CUDA;
+            }
+            return KMEANS2_OK;
+        };
+        const int cap = 2 * max_iter_all + 2;
+        if (o.profile) {
+            // ---- profiled: host-driven loop, CUDA events around each iteration's
+            // distance kernels (every kernel is then visible to profilers)
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int it = 0; it < cap && rc == KMEANS2_OK; ++it) {
+                cudaEventRecord(e0, s);
+                rc = launch_classes();
+                if (rc != KMEANS2_OK) break;
+                cudaEventRecord(e1, s);
+                ++g_launches;
+                batch_recheck_kernel<<<count, kThreads, 0, s>>>(dinst);
+                ++g_launches;
+                batch_finalize_kernel<<<count, kThreads, 0, s>>>(dinst, counters);
+                ++g_launches;
+                batch_step_kernel<<<1, 1, 0, s>>>(counters, counters + 1, counters + 2,
+                                                  (int)classes.size(), counters + 8);
+                int active = 0;
+                cudaError_t e = cudaMemcpyAsync(&active, counters + 8, sizeof(int),
+                                                cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) { set_last_error("batched loop", e); rc = KMEANS2_ERR_CUDA; break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                o.profile->assign_launches += (long long)classes.size();
+                o.profile->assign_ms += ms;
+                if (active == 0) break;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
         // ---- the iteration loop as one graph with a device-side while condition
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        KM2_CUDA(cudaGraphCreate(&graph, 0));
+        if (!o.profile) KM2_CUDA(cudaGraphCreate(&graph, 0));
         do {
+            if (o.profile) break;
             cudaGraphConditionalHandle handle;
             cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
             if (e != cudaSuccess) { set_last_error("cudaGraphConditionalHandleCreate", e); rc = KMEANS2_ERR_CUDA; break; }
@@ -745,16 +820,12 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             cudaGraph_t body = gp->conditional.phGraph_out[0];
             e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) { set_last_error("cudaStreamBeginCaptureToGraph", e); rc = KMEANS2_ERR_CUDA; break; }
-            for (size_t c = 0; c < classes.size(); ++c) {
-                rc = launch_class(classes[c].dc, dinst, classes[c].dev, classes[c].count,
-                                  counters + 2 + c, s, ws.sm_count);
-                if (rc != KMEANS2_OK) break;
-            }
+            rc = launch_classes();
             if (rc == KMEANS2_OK) {
                 batch_recheck_kernel<<<count, kThreads, 0, s>>>(dinst);
                 batch_finalize_kernel<<<count, kThreads, 0, s>>>(dinst, counters);
                 batch_control_kernel<<<1, 1, 0, s>>>(counters, counters + 1, counters + 2,
-                                                     (int)classes.size(), 2 * max_iter_all + 2,
+                                                     (int)classes.size(), cap,
                                                      (unsigned long long)handle);
             }
             cudaGraph_t captured = nullptr;
@@ -768,12 +839,16 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             if (e != cudaSuccess) { set_last_error("batched graph", e); rc = KMEANS2_ERR_CUDA; break; }
         } while (0);
         if (exec) cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        if (rc == KMEANS2_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamSynchronize(s);
+        destroy_side();
+        if (rc == KMEANS2_OK && !o.profile) {
             int iters = 0;
             KM2_CUDA(cudaMemcpyAsync(&iters, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
             KM2_CUDA(cudaStreamSynchronize(s));
             g_launches += (long long)iters * ((long long)classes.size() + 3);
+        }
+        if (rc == KMEANS2_OK) {
             // ---- results
             KM2_CUDA(cudaMemcpyAsync(hi.data(), dinst, sizeof(BatchInst) * (size_t)count,
                                      cudaMemcpyDeviceToHost, s));
@@ -806,6 +881,11 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
                 r.subset_size = I.m;
                 r.rechecked_points = I.rechecked;
                 r.distance_evals = (int64_t)r.iters_fast * I.m * I.k + (int64_t)r.iters_slow * I.n * I.k;
+                if (o.profile) {
+                    const double pts = (double)r.iters_fast * I.m + (double)r.iters_slow * I.n;
+                    o.profile->assign_flops += 2.0 * pts * I.k * I.d;
+                    o.profile->assign_bytes += 4.0 * pts * I.d;
+                }
                 r.shift_fast = I.shift_fast;
                 r.shift_slow = I.st.shift;
                 r.seconds = secs;

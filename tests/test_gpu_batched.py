@@ -69,3 +69,22 @@ def test_batched_nonfinite_job_does_not_disturb_others():
             continue
         a = km.fit(X, s.k, 0.2, s.seed, 1e-6, 30, precision="fp32")
         assert torch.equal(r.labels, a.labels) and r.J == a.J
+
+
+def test_batched_profiled_host_loop_equals_graph():
+    # the profiled (host-driven) loop runs the same kernels as the graph loop
+    specs = _specs(24, 5, n_hi=100_000, k_hi=200)
+    Xs = [synth.instance_data(s, device=DEV) for s in specs]
+    args = ([s.k for s in specs], 0.1, [s.seed for s in specs], 1e-5, 40)
+    a, rc_a = km.fit_batched(Xs, *args)
+    prof = km.Profile()
+    b, rc_b = km.fit_batched(Xs, *args, profile=prof)
+    assert rc_a == rc_b == 0
+    for ra, rb in zip(a, b):
+        assert (ra.iters_fast, ra.iters_slow) == (rb.iters_fast, rb.iters_slow)
+        assert torch.equal(ra.labels, rb.labels) and torch.equal(ra.centers, rb.centers)
+        assert ra.J == rb.J
+    assert prof.assign_launches > 0 and prof.assign_ms > 0 and prof.kernel_launches > 0
+    want = sum(2.0 * (r.iters_fast * r.subset_size + r.iters_slow * s.n) * s.k * s.d
+               for r, s in zip(b, specs))
+    assert abs(prof.assign_flops - want) <= 1e-9 * want
