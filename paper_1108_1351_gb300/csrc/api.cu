@@ -40,6 +40,23 @@ void set_last_error_text(const char* text)
 
 const char* last_error() { return g_last_error; }
 
+namespace {
+std::mutex g_attr_mu;
+std::vector<std::pair<const void*, int>> g_attr_done;   // (kernel, device) already raised
+}
+
+int set_max_dynamic_smem(const void* kernel, int bytes)
+{
+    int dev = 0;
+    KM2_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    for (const auto& e : g_attr_done)
+        if (e.first == kernel && e.second == dev) return KMEANS2_OK;
+    KM2_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    g_attr_done.emplace_back(kernel, dev);
+    return KMEANS2_OK;
+}
+
 // A private blocking stream per thread and device, used when the caller passes
 // the legacy default stream (which cannot be captured into a graph).
 cudaStream_t private_stream(int device)

@@ -61,6 +61,12 @@ struct DeviceScratch {
     DeviceScratch& operator=(const DeviceScratch&) = delete;
 };
 
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per (kernel,
+// device) for the whole process, under a lock.  The value must be fixed per
+// kernel: worker threads that launch the same kernel concurrently then never
+// see the limit change under them.
+int set_max_dynamic_smem(const void* kernel, int bytes);
+
 // sample.cu
 int sample_device(long long n, int k, long long m, unsigned long long seed, long long* subset,
                   long long* init_pos, cudaStream_t s, DeviceScratch& ws);

@@ -22,9 +22,12 @@
 //   warp 0  A producer: one bulk TMA copy per tile into a 2-stage ring;
 //   warp 1  B producer: one bulk TMA copy per (chunk, K-step) slice into an
 //           SB-stage ring (SB <= 8);
-//   warp 2  MMA issuer: per (tile, chunk) unit, 3 MMAs (M 128, N NC, K 16) per
-//           K-step into a TMEM accumulator; tcgen05.commit frees each slice,
-//           each tile and hands the accumulator to the epilogue;
+//   warp 2  MMA issuer: tiles go in pairs (one per epilogue group and A
+//           stage); per (pair, chunk) unit and K-step it issues 3 MMAs
+//           (M 128, N NC, K 16) for each tile of the pair into its TMEM
+//           accumulator, so each B slice is read from L2 once for 256 points;
+//           tcgen05.commit frees each slice and both tiles and hands the
+//           accumulators to the epilogues;
 //   warps 3-6, 7-10  two epilogue groups taking alternate tiles, each with its
 //           own two TMEM accumulators (4 x NC columns in all): a thread owns
 //           one row (TMEM lane) of the tile, keeps a packed-key top-2 across
@@ -53,7 +56,7 @@ constexpr int kThreads = 32 * (3 + kEpiWarps);
 constexpr int kRows = 128;
 constexpr int kSA = 2;                 // A ring depth (tiles)
 constexpr int kMaxSB = 8;              // B ring depth (slices)
-constexpr int kSmemBudget = 220 * 1024;
+constexpr int kSmemBudget = 226 * 1024;    // dynamic + static shared memory of the CTA
 constexpr int kWaitTries = 1 << 22;
 
 __device__ __forceinline__ float pack_key(float v, unsigned j)
@@ -94,16 +97,35 @@ struct Bf16Args {
     const unsigned char* Cb; // BF16 -2c slices
     long long n;
     int d, k, nc, nch, sb;   // chunk width NC, chunk count, B ring depth
+    int lab_bulk;            // old labels can be bulk-copied (16-byte aligned)
     uint32_t tmem_cols;
     float kappa, kpack;
 };
+
+constexpr int kSR = 4;                 // side ring depth (tiles): ||x||^2 and old labels
+constexpr int kRecheckQ = 256;         // flagged points staged per epilogue warp
 
 struct Bars {
     uint64_t a_full[kSA], a_empty[kSA];
     uint64_t b_full[kMaxSB], b_empty[kMaxSB];
     uint64_t acc_full[2 * kEpiGroups], acc_empty[2 * kEpiGroups];
+    uint64_t side_full[kSR], side_empty[kSR];
     uint64_t drain;
 };
+
+// Per-tile values the row decisions need, loaded with each tile by bulk
+// copies, whose shared-memory destinations must be 16-byte aligned.
+struct __align__(128) SideRing {
+    float xn2[kSR][kRows];
+    int lab[kSR][kRows];
+};
+static_assert(sizeof(float) * kRows % 16 == 0, "side ring rows must keep 16-byte alignment");
+
+// Static shared memory of the kernel (barriers, side ring, recheck queues),
+// rounded up; the dynamic part must fit beside it.
+constexpr int kStaticSmem = 16 * 1024;
+static_assert(sizeof(Bars) + sizeof(SideRing) + kEpiWarps * kRecheckQ * 4 + 64 <= kStaticSmem,
+              "static shared memory estimate too small");
 
 // Bounded wait for the phase of `parity`; gives up early once another role
 // has aborted.  On its own timeout it raises the abort flag and the error.
@@ -168,12 +190,16 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Bars bars;
+    __shared__ __align__(128) SideRing side;
+    __shared__ int rqs[kEpiWarps][kRecheckQ];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
     if (st->error) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d, nch = a.nch, SB = a.sb;
+    const int mode = st->mode;
+    const bool lab_bulk = a.lab_bulk != 0 && mode == kModeDelta;
     const int ksteps = d / 16;
     const int kslices = ksteps + 1;                              // data K-steps + the norm slice
     const uint32_t Ahalf = (uint32_t)ksteps * 4096u;             // one part of a tile
@@ -208,6 +234,10 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             tc::mbar_init(&bars.acc_full[b], 1);
             tc::mbar_init(&bars.acc_empty[b], 4);   // the 4 warps of the owning group
         }
+        for (int r = 0; r < kSR; ++r) {
+            tc::mbar_init(&bars.side_full[r], 1);
+            tc::mbar_init(&bars.side_empty[r], 4);  // the 4 warps of the consuming group
+        }
         tc::mbar_init(&bars.drain, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -226,22 +256,33 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
         if (lane == 0) {
             long long issued = 0;
             for (long long i = 0; i < cnt; ++i) {
-                const int s = (int)(i & 1);
+                const int s = (int)(i & 1), r = (int)(i % kSR);
                 if (!wait_bar(&bars.a_empty[s], (uint32_t)(((i >> 1) & 1) ^ 1), abort_v, st)) break;
+                if (!wait_bar(&bars.side_empty[r], (uint32_t)(((i / kSR) & 1) ^ 1), abort_v, st)) break;
                 const long long tile = blockIdx.x + i * gridDim.x;
                 mbar_expect_tx(&bars.a_full[s], Abytes);
                 bulk_load(sA + (size_t)s * Abytes, a.Xt + (size_t)tile * Abytes, Abytes,
                           &bars.a_full[s]);
+                // ||x||^2 and old labels of the tile's first rows & ~3 points
+                const long long rows = a.n - tile * kRows < kRows ? a.n - tile * kRows : kRows;
+                const uint32_t vb = (uint32_t)(rows & ~3ll) * 4u;
+                const uint32_t lb = lab_bulk ? vb : 0u;
+                mbar_expect_tx(&bars.side_full[r], vb + lb);
+                if (vb) bulk_load(side.xn2[r], a.xn2 + tile * kRows, vb, &bars.side_full[r]);
+                if (lb) bulk_load(side.lab[r], labels + tile * kRows, lb, &bars.side_full[r]);
                 issued = i + 1;
             }
             // let this CTA's own copies land before it can exit
             for (long long i = issued > kSA ? issued - kSA : 0; i < issued; ++i)
                 tc::mbar_wait(&bars.a_full[i & 1], (uint32_t)((i >> 1) & 1), kWaitTries);
+            for (long long i = issued > kSR ? issued - kSR : 0; i < issued; ++i)
+                tc::mbar_wait(&bars.side_full[i % kSR], (uint32_t)((i / kSR) & 1), kWaitTries);
         }
     } else if (warp == 1) {
         // ---------------- B producer: slice q = (unit, K-step) -> stage q % SB
         if (lane == 0) {
-            const long long total = cnt * nch * kslices;
+            // slices go once per PAIR of tiles (both tiles' MMAs read each slice)
+            const long long total = ((cnt + 1) / 2) * nch * kslices;
             long long q = 0;
             for (; q < total; ++q) {
                 const int slot = (int)(q % SB);
@@ -263,16 +304,22 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             uint32_t phase = 0u;             // bit b: parity of accumulator b's next use
             long long q = 0;
             bool ok = true;
-            for (long long i = 0; i < cnt && ok; ++i) {
-                const int sa = (int)(i & 1);
-                if (!(ok = wait_bar(&bars.a_full[sa], (uint32_t)((i >> 1) & 1), abort_v, st))) break;
+            // tiles go in pairs (2 pr -> A stage 0 and epilogue group 0, 2 pr + 1 ->
+            // stage 1 and group 1): each B slice feeds both tiles' MMAs
+            const long long npairs = (cnt + 1) / 2;
+            for (long long pr = 0; pr < npairs && ok; ++pr) {
+                const bool two = 2 * pr + 1 < cnt;
+                const uint32_t par = (uint32_t)(pr & 1);
+                if (!(ok = wait_bar(&bars.a_full[0], par, abort_v, st))) break;
+                if (two && !(ok = wait_bar(&bars.a_full[1], par, abort_v, st))) break;
                 tc::fence_after_sync();
-                const uint32_t aBase = sAaddr + (uint32_t)sa * Abytes;
                 for (int ch = 0; ch < nch && ok; ++ch) {
-                    const int b = 2 * (int)(i & 1) + (ch & 1);
-                    if (!(ok = wait_bar(&bars.acc_empty[b], ((phase >> b) & 1u) ^ 1u, abort_v, st))) break;
+                    const int b0 = ch & 1, b1 = 2 + (ch & 1);
+                    if (!(ok = wait_bar(&bars.acc_empty[b0], ((phase >> b0) & 1u) ^ 1u, abort_v, st))) break;
+                    if (two && !(ok = wait_bar(&bars.acc_empty[b1], ((phase >> b1) & 1u) ^ 1u, abort_v, st)))
+                        break;
                     tc::fence_after_sync();
-                    const uint32_t dt = tmem + (uint32_t)(b * NC);
+                    const uint32_t d0 = tmem + (uint32_t)(b0 * NC), d1 = tmem + (uint32_t)(b1 * NC);
                     for (int ks = 0; ks < kslices; ++ks, ++q) {
                         const int slot = (int)(q % SB);
                         if (!(ok = wait_bar(&bars.b_full[slot], (uint32_t)((q / SB) & 1), abort_v, st)))
@@ -280,21 +327,35 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                         tc::fence_after_sync();
                         const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes;
                         if (ks < ksteps) {
-                            const uint32_t ah = aBase + (uint32_t)ks * 4096u;
-                            tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
-                            tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh + (uint32_t)NC * 32u), idesc, 1u);
-                            tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                            const uint32_t bl = bh + (uint32_t)NC * 32u;
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                if (t == 1 && !two) break;
+                                const uint32_t dt = t ? d1 : d0;
+                                const uint32_t ah = sAaddr + (uint32_t)t * Abytes + (uint32_t)ks * 4096u;
+                                tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
+                                tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
+                                tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                            }
                         } else {
                             // + ||c||^2: ones x (nh, nm, nl)
-                            tc::mma_bf16(dt, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
+                            tc::mma_bf16(d0, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
+                            if (two) tc::mma_bf16(d1, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
                         }
                         tc::mma_commit(&bars.b_empty[slot]);
                     }
                     if (!ok) break;
-                    tc::mma_commit(&bars.acc_full[b]);
-                    phase ^= 1u << b;
+                    tc::mma_commit(&bars.acc_full[b0]);
+                    phase ^= 1u << b0;
+                    if (two) {
+                        tc::mma_commit(&bars.acc_full[b1]);
+                        phase ^= 1u << b1;
+                    }
                 }
-                if (ok) tc::mma_commit(&bars.a_empty[sa]);
+                if (ok) {
+                    tc::mma_commit(&bars.a_empty[0]);
+                    if (two) tc::mma_commit(&bars.a_empty[1]);
+                }
             }
             // every MMA issued by this thread has completed once `drain` flips
             tc::mma_commit(&bars.drain);
@@ -307,9 +368,21 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
         const int quarter = warp & 3;                     // TMEM lanes 32 * (warp % 4) ...
         const int row = 32 * quarter + lane;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
-        const int mode = st->mode;
         const float scaleF = st->scaleF, scaleG = st->scaleG;
         const float thr_base = 2.0f * st->cmax2;
+        int* rq = rqs[ew];
+        int rq_n = 0;                                      // warp-uniform queue length
+        // hands the queued flagged points to the global recheck list (one atomic)
+        auto rq_flush = [&]() {
+            if (rq_n == 0) return;
+            __syncwarp();
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&st->recheck_count, rq_n);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int e = lane; e < rq_n; e += 32) list[base + e] = rq[e];
+            __syncwarp();
+            rq_n = 0;
+        };
         uint32_t phase = 0u;                 // bit s: parity of accumulator 2 g + s's next use
         long long qloc = 0;
         long long done = 0;
@@ -345,8 +418,15 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             }
             if (!ok) break;
             // ---- decide row `row` of tile i
-            const long long p = (blockIdx.x + i * gridDim.x) * kRows + row;
+            const long long tile = blockIdx.x + i * gridDim.x;
+            const long long p = tile * kRows + row;
             const bool valid = p < a.n;
+            const int r = (int)(i % kSR);
+            {
+                const bool w = wait_bar(&bars.side_full[r], (uint32_t)((i / kSR) & 1), abort_v, st);
+                if (!__all_sync(0xffffffffu, w)) break;
+            }
+            const bool in_ring = (long long)row < ((a.n - tile * kRows) & ~3ll);
             if ((done & 255) == 255) {
                 // keep each ||x||^2 partial below 2^62: fold it every 256 tiles
                 long long qs = qloc;
@@ -355,15 +435,26 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 qloc = 0;
             }
             ++done;
-            const float xx = valid ? __ldg(a.xn2 + p) : 0.0f;
+            const float xx = valid ? (in_ring ? side.xn2[r][row] : __ldg(a.xn2 + p)) : 0.0f;
             const float thr = a.kappa * (thr_base + xx) + a.kpack * (fabsf(B1) + fabsf(B2));
             const bool flag = valid && (B2 - B1 <= thr);
-            recheck_append(flag, (int)p, list, &st->recheck_count);
+            {
+                const unsigned m = __ballot_sync(0xffffffffu, flag);
+                if (m) {
+                    if (rq_n + 32 > kRecheckQ) rq_flush();
+                    if (flag) rq[rq_n + __popc(m & lanemask_lt())] = (int)p;
+                    rq_n += __popc(m);
+                }
+            }
             const float* xr = a.X + p * d;
             if (mode == kModeFull && valid)
                 for (int t = 0; t < d; ++t) qloc += sq_fixed(__ldg(xr + t), scaleG);
+            int old = -1;
+            if (mode == kModeDelta && valid)
+                old = (lab_bulk && in_ring) ? side.lab[r][row] : labels[p];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.side_empty[r]);
             if (valid && !flag) {
-                const int old = (mode == kModeDelta) ? labels[p] : -1;
                 if (BI != old) {
                     for (int t = 0; t < d; ++t) {
                         const long long val = to_fixed(__ldg(xr + t), scaleF);
@@ -378,6 +469,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 }
             }
         }
+        rq_flush();
         // one partial of ||x||^2 per warp (each below 2^62)
         for (int o = 16; o; o >>= 1) qloc += __shfl_xor_sync(0xffffffffu, qloc, o);
         if (lane == 0 && qloc) split_add(&st->q_lo, &st->q_hi, qloc);
@@ -503,7 +595,7 @@ float bf16_kappa(int d)
 // the widest chunk must fit into the shared-memory budget.
 int bf16_fits(int d)
 {
-    return d <= 128 && kSA * 4 * kRows * d + 2 * 128 * 64 + 4096 <= kSmemBudget;
+    return d <= 128 && kSA * 4 * kRows * d + 2 * 128 * 64 + 4096 <= kSmemBudget - kStaticSmem;
 }
 
 int assign_bf16_supported(int d, int k, const float* X)
@@ -568,23 +660,17 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * kEpiGroups * NC)) cols <<= 1;
     const size_t abytes = (size_t)4 * kRows * d, sbytes = (size_t)NC * 64;
-    int sb = (int)((kSmemBudget - kSA * abytes - 4096) / sbytes);
+    int sb = (int)((kSmemBudget - kStaticSmem - kSA * abytes - 4096) / sbytes);
     if (sb > kMaxSB) sb = kMaxSB;
     if (sb < 2) {
         set_last_error_text("assign_bf16: shared-memory budget too small for this d");
         return KMEANS2_ERR_UNSUPPORTED;
     }
     const size_t smem = kSA * abytes + (size_t)sb * sbytes + 4096;
-    static thread_local int configured_for = -1;
-    int dev = 0;
-    KM2_CUDA(cudaGetDevice(&dev));
-    if (configured_for != dev) {
-        KM2_CUDA(cudaFuncSetAttribute(assign_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSmemBudget));
-        KM2_CUDA(cudaFuncSetAttribute(assign_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSmemBudget));
-        configured_for = dev;
-    }
+    // one fixed limit for both instantiations (the static part holds the
+    // barriers, the side ring and the recheck queues)
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<64>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<128>, kSmemBudget - kStaticSmem));
     const long long tiles = (n + kRows - 1) / kRows;
     long long grid = sm_count;
     if (grid > tiles) grid = tiles;
@@ -600,6 +686,7 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     a.nc = NC;
     a.nch = nch;
     a.sb = sb;
+    a.lab_bulk = (reinterpret_cast<uintptr_t>(labels) & 15) == 0 ? 1 : 0;
     a.tmem_cols = cols;
     a.kappa = bf16_kappa(d);
     a.kpack = kPackSlack;

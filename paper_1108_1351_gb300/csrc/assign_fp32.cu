@@ -515,14 +515,7 @@ int launch_small(const float* X, long long n, const Centers& c, int* labels, Sta
     const bool with_acc = small_smem<D>(c.k, true) <= (size_t)kSmallSmemCap;
     const size_t sm = small_smem<D>(c.k, with_acc);
     if (sm > (size_t)kSmallSmemCap) return KMEANS2_ERR_UNSUPPORTED;
-    static thread_local int configured_for = -1;
-    int dev = 0;
-    KM2_CUDA(cudaGetDevice(&dev));
-    if (configured_for != dev) {
-        KM2_CUDA(cudaFuncSetAttribute(assign_small<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSmallSmemCap));
-        configured_for = dev;
-    }
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_small<D>, kSmallSmemCap));
     int per_sm = 0;
     KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assign_small<D>, kThreads, sm));
     if (per_sm < 1) return KMEANS2_ERR_UNSUPPORTED;

@@ -44,7 +44,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kEpiWarps = 8;
 constexpr int kRows = 128;                 // points per tile (UMMA M)
 constexpr int kStepBytes = kRows * 32;     // one K-step (8 TF32) of a 128-row A tile
-constexpr int kMaxRS = 8, kMaxSA = 4;
+constexpr int kMaxRS = 24, kMaxSA = 4;
 constexpr int kSmemBudget = 210 * 1024;
 constexpr int kWaitTries = 1 << 22;
 constexpr int kWarpFlushTiles = kFlushPoints / 32;   // 32 points per tile and warp
@@ -111,10 +111,13 @@ struct TcCfg {
     static constexpr uint32_t ABYTES = 2u * KD * kStepBytes;   // hi + lo A tiles
 };
 
+constexpr int kRecheckQ = 256;             // flagged points staged per epilogue warp
+
 struct TcLayout {
     int rs, sa, nb;          // raw ring, A ring, accumulators per epilogue group
     int sacc;                // per-warp shared-memory partial sums
-    uint32_t a_off, ones_off, b_off, raw_off, acc_off, acc_bytes, total;
+    int lab_bulk;            // old labels arrive with each raw tile (delta mode, aligned labels)
+    uint32_t a_off, ones_off, b_off, raw_off, lab_off, rq_off, acc_off, acc_bytes, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
@@ -127,6 +130,7 @@ __host__ __device__ inline TcLayout tc_layout(int D, int npad, int k, int rs, in
     L.sa = sa;
     L.nb = 4 * npad <= 512 ? 2 : 1;
     L.sacc = sacc;
+    L.lab_bulk = 0;
     uint32_t o = 0;
     L.a_off = o;
     o += (uint32_t)sa * 2u * KD * kStepBytes;
@@ -137,6 +141,11 @@ __host__ __device__ inline TcLayout tc_layout(int D, int npad, int k, int rs, in
     o = align_up(o, 128);
     L.raw_off = o;
     o += (uint32_t)rs * kRows * (uint32_t)D * 4u;
+    o = align_up(o, 16);
+    L.lab_off = o;                                 // old labels of each raw stage
+    o += (uint32_t)rs * kRows * 4u;
+    L.rq_off = o;                                  // recheck queues of the epilogue warps
+    o += (uint32_t)kEpiWarps * kRecheckQ * 4u;
     o = align_up(o, 16);
     L.acc_off = o;
     L.acc_bytes = align_up((uint32_t)k * (uint32_t)D * 8u + (uint32_t)k * 4u, 16);
@@ -173,7 +182,10 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
     unsigned char* sOnes = smem + L.ones_off;
     unsigned char* sB = smem + L.b_off;
     float* raw = reinterpret_cast<float*>(smem + L.raw_off);
+    int* lab_ring = reinterpret_cast<int*>(smem + L.lab_off);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const int mode = st->mode;
+    const bool lab_bulk = L.lab_bulk != 0 && mode == kModeDelta;
     volatile int* abort_v = &abort_flag;
 
     // ---- B operand: -2c split in TF32 hi / lo per K-step, then ||c||^2 hi / lo
@@ -254,9 +266,14 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                 const long long tile = blockIdx.x + i * gridDim.x;
                 const long long rows = n - tile * kRows < kRows ? n - tile * kRows : kRows;
                 const uint32_t bytes = (uint32_t)rows * (uint32_t)D * 4u;   // D * 4 is a multiple of 16
-                mbar_expect_tx(&bars.raw_full[rs], bytes);
+                // old labels of the tile's first rows & ~3 points (16-byte multiple)
+                const uint32_t lbytes = lab_bulk ? (uint32_t)(rows & ~3ll) * 4u : 0u;
+                mbar_expect_tx(&bars.raw_full[rs], bytes + lbytes);
                 bulk_load(raw + (size_t)rs * kRows * D, X + tile * kRows * D, bytes,
                           &bars.raw_full[rs]);
+                if (lbytes)
+                    bulk_load(lab_ring + (size_t)rs * kRows, labels + tile * kRows, lbytes,
+                              &bars.raw_full[rs]);
                 issued = i + 1;
             }
             // let this CTA's own copies land before it can exit
@@ -346,8 +363,20 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
         const int quarter = warp & 3;                      // TMEM lanes 32 * (warp % 4) ...
         const int row = 32 * quarter + lane;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
-        const int mode = st->mode;
         const float scaleF = st->scaleF, scaleG = st->scaleG;
+        int* rq = reinterpret_cast<int*>(smem + L.rq_off) + ew * kRecheckQ;
+        int rq_n = 0;                                      // warp-uniform queue length
+        // hands the queued flagged points to the global recheck list (one atomic)
+        auto rq_flush = [&]() {
+            if (rq_n == 0) return;
+            __syncwarp();
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&st->recheck_count, rq_n);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int e = lane; e < rq_n; e += 32) list[base + e] = rq[e];
+            __syncwarp();
+            rq_n = 0;
+        };
         const float thr_base = 2.0f * st->cmax2;
         long long* sacc = reinterpret_cast<long long*>(smem + L.acc_off + (size_t)ew * L.acc_bytes);
         int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);
@@ -422,9 +451,19 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
 #pragma unroll
                 for (int t = 0; t < D; ++t) qloc += sq_fixed(x[t], scaleG);
             }
-            recheck_append(flag, (int)p, list, &st->recheck_count);
+            {
+                const unsigned m = __ballot_sync(0xffffffffu, flag);
+                if (m) {
+                    if (rq_n + 32 > kRecheckQ) rq_flush();
+                    if (flag) rq[rq_n + __popc(m & lanemask_lt())] = (int)p;
+                    rq_n += __popc(m);
+                }
+            }
             if (valid && !flag) {
-                const int old = (mode == kModeDelta) ? labels[p] : -1;
+                const bool from_ring = lab_bulk && (long long)row < ((n - tile * kRows) & ~3ll);
+                const int old = (mode == kModeDelta)
+                                    ? (from_ring ? lab_ring[(size_t)rs * kRows + row] : labels[p])
+                                    : -1;
                 if (BI != old) {
 #pragma unroll
                     for (int t = 0; t < D; ++t) {
@@ -482,6 +521,7 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                 }
             }
         }
+        rq_flush();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -526,16 +566,10 @@ int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageS
         set_last_error_text("assign_tc32: shared-memory budget too small for this shape");
         return KMEANS2_ERR_UNSUPPORTED;
     }
+    L.lab_bulk = (reinterpret_cast<uintptr_t>(labels) & 15) == 0 ? 1 : 0;
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * L.nb * npad)) cols <<= 1;
-    static thread_local int configured_for = -1;
-    int dev = 0;
-    KM2_CUDA(cudaGetDevice(&dev));
-    if (configured_for != dev) {
-        KM2_CUDA(cudaFuncSetAttribute(assign_tc32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSmemBudget));
-        configured_for = dev;
-    }
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_tc32<D>, kSmemBudget));
     const long long tiles = (n + kRows - 1) / kRows;
     long long grid = sm_count;
     if (grid > tiles) grid = tiles;

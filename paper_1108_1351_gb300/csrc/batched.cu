@@ -500,15 +500,8 @@ template <int DC>
 int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item,
                         cudaStream_t s, int sm_count)
 {
-    static thread_local int configured_for = -1;
-    int dev = 0;
-    KM2_CUDA(cudaGetDevice(&dev));
     const size_t sm = batch_smem<DC>();
-    if (configured_for != dev) {
-        KM2_CUDA(cudaFuncSetAttribute(batch_assign<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sm));
-        configured_for = dev;
-    }
+    KM2_TRY(set_max_dynamic_smem((const void*)batch_assign<DC>, (int)sm));
     int per_sm = 0;
     KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_assign<DC>, kThreads, sm));
     if (per_sm < 1) per_sm = 1;
