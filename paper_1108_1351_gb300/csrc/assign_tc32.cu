@@ -13,18 +13,21 @@
 // FP32 accumulation and the key packing), labels and the exact fixed-point
 // cluster sums.
 //
-// Warp-specialised pipeline, one CTA per SM, 14 warps:
-//   warp 0      loader: one bulk TMA copy per 128-point tile of raw X rows into
-//               an RS-stage ring (the rows stay there until the tile's
-//               epilogue is done: the sums read them back);
-//   warps 1-4   producers: thread r splits row r into the hi / lo A tiles of an
-//               SA-stage ring (K-major core-matrix layout, tc_common.cuh);
-//   warp 5      MMA issuer: 3 KD + 1 MMAs (M 128, N npad, K 8) per tile into a
-//               TMEM accumulator, then tcgen05.commit hands it on;
-//   warps 6-13  two epilogue groups taking alternate tiles, each with NB (1 or
-//               2) accumulators of npad columns: thread r owns row r (TMEM lane)
-//               and decides it; each warp keeps its own shared-memory partial
-//               sums (when they fit), flushed by the warp alone.
+// Warp-specialised pipeline, one CTA per SM, 14 warps.  The unit of every
+// hand-off is a group of T 128-point tiles (T = 4, 2 or 1 as k grows), so
+// each barrier round trip is paid once per T tiles and each epilogue thread
+// works on T independent rows:
+//   warp 0      loader: T bulk TMA copies per unit (raw X rows, and the old
+//               labels in delta mode) into an RS-stage ring; the rows stay
+//               until the unit's epilogue is done (the sums read them back);
+//   warps 1-4   producers: thread r splits row r of each tile into the hi / lo
+//               A tiles of an SA-stage ring (K-major core-matrix layout);
+//   warp 5      MMA issuer: per tile 3 KD + 1 MMAs (M 128, N npad, K 8) into
+//               column block t of a TMEM accumulator, one commit per unit;
+//   warps 6-13  two epilogue groups taking alternate units, each with NB (1 or
+//               2) accumulators of T x npad columns: thread r owns row r of the
+//               unit's T tiles; flagged points are queued per warp in shared
+//               memory and partial sums kept per warp (when they fit).
 // The B operand (every center's -2c hi / lo per K-step and ||c||^2 hi / lo) is
 // built once per launch and stays in shared memory.  Roles are coupled only by
 // mbarriers; every wait is bounded, and on a timeout the CTA records an error,
@@ -44,10 +47,10 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kEpiWarps = 8;
 constexpr int kRows = 128;                 // points per tile (UMMA M)
 constexpr int kStepBytes = kRows * 32;     // one K-step (8 TF32) of a 128-row A tile
-constexpr int kMaxRS = 24, kMaxSA = 4;
+constexpr int kMaxRS = 12, kMaxSA = 4;
 constexpr int kSmemBudget = 210 * 1024;
 constexpr int kWaitTries = 1 << 22;
-constexpr int kWarpFlushTiles = kFlushPoints / 32;   // 32 points per tile and warp
+constexpr int kRecheckQ = 256;             // flagged points staged per epilogue warp
 
 __device__ __forceinline__ float tf32_hi(float v)
 {
@@ -105,45 +108,79 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     return false;
 }
 
+// Packed-key top-2 of 32 accumulator columns (center indices j0 .. j0 + 31)
+// folded into the running (B1, B2, BI) of a row.
+__device__ __forceinline__ void top2_cols(const uint32_t* r, int j0, float& B1, float& B2, int& BI)
+{
+    float q1[4], q2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = j + 2 * q;
+            const float k0 = pack_key(__uint_as_float(r[jj]), (unsigned)jj);
+            const float k1 = pack_key(__uint_as_float(r[jj + 1]), (unsigned)jj + 1u);
+            const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
+            q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
+            q1[q] = fminf(q1[q], lo);
+        }
+    }
+    const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
+    const float l01 = fminf(q1[0], q1[1]);
+    const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
+    const float l23 = fminf(q1[2], q1[3]);
+    const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
+    const float b1 = fminf(l01, l23);
+    if (b1 < B1) {
+        B2 = fminf(B1, b2);
+        B1 = b1;
+        BI = j0 + (int)(__float_as_uint(b1) & 31u);
+    } else {
+        B2 = fminf(B2, b1);
+    }
+}
+
 template <int D>
 struct TcCfg {
     static constexpr int KD = (D + 7) / 8;                     // data K-steps
-    static constexpr uint32_t ABYTES = 2u * KD * kStepBytes;   // hi + lo A tiles
+    static constexpr uint32_t ABYTES = 2u * KD * kStepBytes;   // hi + lo A tiles of one tile
 };
 
-constexpr int kRecheckQ = 256;             // flagged points staged per epilogue warp
-
 struct TcLayout {
-    int rs, sa, nb;          // raw ring, A ring, accumulators per epilogue group
+    int T;                   // tiles per unit
+    int rs, sa, nb;          // raw ring, A ring (units), accumulators per epilogue group
     int sacc;                // per-warp shared-memory partial sums
-    int lab_bulk;            // old labels arrive with each raw tile (delta mode, aligned labels)
+    int lab_bulk;            // old labels arrive with the raw rows (delta mode, aligned labels)
     uint32_t a_off, ones_off, b_off, raw_off, lab_off, rq_off, acc_off, acc_bytes, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int D, int npad, int k, int rs, int sa, int sacc)
+__host__ __device__ inline TcLayout tc_layout(int D, int T, int npad, int k, int rs, int sa, int sacc)
 {
     const int KD = (D + 7) / 8;
     TcLayout L;
+    L.T = T;
     L.rs = rs;
     L.sa = sa;
-    L.nb = 4 * npad <= 512 ? 2 : 1;
+    L.nb = 4 * T * npad <= 512 ? 2 : 1;
     L.sacc = sacc;
     L.lab_bulk = 0;
     uint32_t o = 0;
     L.a_off = o;
-    o += (uint32_t)sa * 2u * KD * kStepBytes;
+    o += (uint32_t)sa * (uint32_t)T * 2u * KD * kStepBytes;
     L.ones_off = o;
     o += kStepBytes;
     L.b_off = o;
     o += (uint32_t)(2 * KD + 1) * (uint32_t)npad * 32u;
     o = align_up(o, 128);
     L.raw_off = o;
-    o += (uint32_t)rs * kRows * (uint32_t)D * 4u;
+    o += (uint32_t)rs * (uint32_t)T * kRows * (uint32_t)D * 4u;
     o = align_up(o, 16);
     L.lab_off = o;                                 // old labels of each raw stage
-    o += (uint32_t)rs * kRows * 4u;
+    o += (uint32_t)rs * (uint32_t)T * kRows * 4u;
     L.rq_off = o;                                  // recheck queues of the epilogue warps
     o += (uint32_t)kEpiWarps * kRecheckQ * 4u;
     o = align_up(o, 16);
@@ -161,7 +198,7 @@ struct TcBars {
     uint64_t drain;
 };
 
-template <int D>
+template <int D, int T>
 __global__ void __launch_bounds__(kThreads, 1)
 assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
             StageState* st, Accum acc, int* __restrict__ list, float kappa, float kpack,
@@ -187,6 +224,8 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
     const int mode = st->mode;
     const bool lab_bulk = L.lab_bulk != 0 && mode == kModeDelta;
     volatile int* abort_v = &abort_flag;
+    constexpr uint32_t kRawUnit = (uint32_t)T * kRows * D;        // floats per raw stage
+    constexpr uint32_t kAUnit = (uint32_t)T * C::ABYTES;          // bytes per A stage
 
     // ---- B operand: -2c split in TF32 hi / lo per K-step, then ||c||^2 hi / lo
     const int bitems = npad * (2 * KD + 1) * 2;        // (row, tile, 16-byte chunk)
@@ -251,72 +290,89 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
 
+    // local tile i of this CTA is global tile blockIdx.x + i * gridDim.x;
+    // unit u holds local tiles u T .. u T + T - 1 (the last unit may hold fewer)
     const long long ntiles = (n + kRows - 1) / kRows;
     const long long cnt = (long long)blockIdx.x < ntiles
                               ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long units = (cnt + T - 1) / T;
+    auto tile_of = [&](long long u, int t) { return blockIdx.x + (u * T + t) * gridDim.x; };
+    auto tiles_in = [&](long long u) { return (int)(cnt - u * T < T ? cnt - u * T : T); };
 
     if (warp == 0) {
-        // ---------------- loader: raw rows of tile i -> raw stage i % RS
+        // ---------------- loader: raw rows (and old labels) of unit u -> raw stage u % RS
         if (lane == 0) {
             long long issued = 0;
-            for (long long i = 0; i < cnt; ++i) {
-                const int rs = (int)(i % RS);
-                if (!wait_bar(&bars.raw_empty[rs], (uint32_t)(((i / RS) & 1) ^ 1), abort_v, st))
+            for (long long u = 0; u < units; ++u) {
+                const int rs = (int)(u % RS);
+                if (!wait_bar(&bars.raw_empty[rs], (uint32_t)(((u / RS) & 1) ^ 1), abort_v, st))
                     break;
-                const long long tile = blockIdx.x + i * gridDim.x;
-                const long long rows = n - tile * kRows < kRows ? n - tile * kRows : kRows;
-                const uint32_t bytes = (uint32_t)rows * (uint32_t)D * 4u;   // D * 4 is a multiple of 16
-                // old labels of the tile's first rows & ~3 points (16-byte multiple)
-                const uint32_t lbytes = lab_bulk ? (uint32_t)(rows & ~3ll) * 4u : 0u;
-                mbar_expect_tx(&bars.raw_full[rs], bytes + lbytes);
-                bulk_load(raw + (size_t)rs * kRows * D, X + tile * kRows * D, bytes,
-                          &bars.raw_full[rs]);
-                if (lbytes)
-                    bulk_load(lab_ring + (size_t)rs * kRows, labels + tile * kRows, lbytes,
-                              &bars.raw_full[rs]);
-                issued = i + 1;
+                const int nt = tiles_in(u);
+                uint32_t total = 0;
+                for (int t = 0; t < nt; ++t) {
+                    const long long tile = tile_of(u, t);
+                    const long long rows = n - tile * kRows < kRows ? n - tile * kRows : kRows;
+                    total += (uint32_t)rows * (uint32_t)D * 4u;               // D * 4: multiple of 16
+                    if (lab_bulk) total += (uint32_t)(rows & ~3ll) * 4u;     // 16-byte multiple
+                }
+                mbar_expect_tx(&bars.raw_full[rs], total);
+                for (int t = 0; t < nt; ++t) {
+                    const long long tile = tile_of(u, t);
+                    const long long rows = n - tile * kRows < kRows ? n - tile * kRows : kRows;
+                    bulk_load(raw + (size_t)rs * kRawUnit + (size_t)t * kRows * D, X + tile * kRows * D,
+                              (uint32_t)rows * (uint32_t)D * 4u, &bars.raw_full[rs]);
+                    const uint32_t lbytes = lab_bulk ? (uint32_t)(rows & ~3ll) * 4u : 0u;
+                    if (lbytes)
+                        bulk_load(lab_ring + ((size_t)rs * T + t) * kRows, labels + tile * kRows,
+                                  lbytes, &bars.raw_full[rs]);
+                }
+                issued = u + 1;
             }
             // let this CTA's own copies land before it can exit
-            for (long long i = issued > RS ? issued - RS : 0; i < issued; ++i)
-                tc::mbar_wait(&bars.raw_full[i % RS], (uint32_t)((i / RS) & 1), kWaitTries);
+            for (long long u = issued > RS ? issued - RS : 0; u < issued; ++u)
+                tc::mbar_wait(&bars.raw_full[u % RS], (uint32_t)((u / RS) & 1), kWaitTries);
         }
     } else if (warp <= 4) {
-        // ---------------- producers: thread r splits row r of tile i into A stage i % SA
+        // ---------------- producers: thread r splits row r of each tile of unit u
         const int r = tid - 32;
-        for (long long i = 0; i < cnt; ++i) {
-            const int rs = (int)(i % RS), sa = (int)(i % SA);
-            bool ok = wait_bar(&bars.raw_full[rs], (uint32_t)((i / RS) & 1), abort_v, st);
-            ok = ok && wait_bar(&bars.a_empty[sa], (uint32_t)(((i / SA) & 1) ^ 1), abort_v, st);
+        for (long long u = 0; u < units; ++u) {
+            const int rs = (int)(u % RS), sa = (int)(u % SA);
+            bool ok = wait_bar(&bars.raw_full[rs], (uint32_t)((u / RS) & 1), abort_v, st);
+            ok = ok && wait_bar(&bars.a_empty[sa], (uint32_t)(((u / SA) & 1) ^ 1), abort_v, st);
             if (!__all_sync(0xffffffffu, ok)) break;
-            const long long tile = blockIdx.x + i * gridDim.x;
-            const bool valid = tile * kRows + r < n;
-            float x[8 * KD];
-            const float* src = raw + (size_t)rs * kRows * D + (size_t)r * D;
+            const int nt = tiles_in(u);
 #pragma unroll
-            for (int q = 0; q < D / 4; ++q) {
-                const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * q)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
-            }
+            for (int t = 0; t < T; ++t) {
+                if (t >= nt) break;
+                const bool valid = tile_of(u, t) * kRows + r < n;
+                float x[8 * KD];
+                const float* src = raw + (size_t)rs * kRawUnit + ((size_t)t * kRows + r) * D;
 #pragma unroll
-            for (int t = D; t < 8 * KD; ++t) x[t] = 0.f;
-            unsigned char* a = sA + (size_t)sa * C::ABYTES;
+                for (int q = 0; q < D / 4; ++q) {
+                    const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * q)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+                }
 #pragma unroll
-            for (int s = 0; s < KD; ++s) {
+                for (int e = D; e < 8 * KD; ++e) x[e] = 0.f;
+                unsigned char* a = sA + (size_t)sa * kAUnit + (size_t)t * C::ABYTES;
 #pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                    float h[4], l[4];
+                for (int s = 0; s < KD; ++s) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float v = x[8 * s + 4 * kc + q];
-                        h[q] = tf32_hi(v);
-                        l[q] = v - h[q];
+                    for (int kc = 0; kc < 2; ++kc) {
+                        float h[4], l[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float v = x[8 * s + 4 * kc + q];
+                            h[q] = tf32_hi(v);
+                            l[q] = v - h[q];
+                        }
+                        const uint32_t off = tc::tile_offset(r, kc);
+                        *reinterpret_cast<float4*>(a + (size_t)s * kStepBytes + off) =
+                            make_float4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<float4*>(a + (size_t)(KD + s) * kStepBytes + off) =
+                            make_float4(l[0], l[1], l[2], l[3]);
                     }
-                    const uint32_t off = tc::tile_offset(r, kc);
-                    *reinterpret_cast<float4*>(a + (size_t)s * kStepBytes + off) =
-                        make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4*>(a + (size_t)(KD + s) * kStepBytes + off) =
-                        make_float4(l[0], l[1], l[2], l[3]);
                 }
             }
             tc::fence_proxy_async();        // generic writes -> visible to the tensor core
@@ -328,26 +384,29 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc(2u, (uint32_t)npad, (uint32_t)kRows);
             uint32_t phase = 0u;             // bit b: parity of accumulator b's next use
-            for (long long i = 0; i < cnt; ++i) {
-                const int sa = (int)(i % SA);
-                const int b = (int)(i & 1) * NB + (int)((i >> 1) % NB);
-                if (!wait_bar(&bars.a_full[sa], (uint32_t)((i / SA) & 1), abort_v, st)) break;
+            for (long long u = 0; u < units; ++u) {
+                const int sa = (int)(u % SA);
+                const int b = (int)(u & 1) * NB + (int)((u >> 1) % NB);
+                if (!wait_bar(&bars.a_full[sa], (uint32_t)((u / SA) & 1), abort_v, st)) break;
                 if (!wait_bar(&bars.acc_empty[b], ((phase >> b) & 1u) ^ 1u, abort_v, st)) break;
                 tc::fence_after_sync();
-                const uint32_t d_tmem = tmem + (uint32_t)(b * npad);
-                const uint32_t ab = sbase + L.a_off + (uint32_t)sa * C::ABYTES;
+                const int nt = tiles_in(u);
+                for (int t = 0; t < nt; ++t) {
+                    const uint32_t d_tmem = tmem + (uint32_t)((b * T + t) * npad);
+                    const uint32_t ab = sbase + L.a_off + (uint32_t)sa * kAUnit + (uint32_t)t * C::ABYTES;
 #pragma unroll
-                for (int s = 0; s < KD; ++s) {
-                    const uint32_t ah = ab + (uint32_t)s * kStepBytes;
-                    const uint32_t al = ab + (uint32_t)(KD + s) * kStepBytes;
-                    const uint32_t bh = sbase + L.b_off + (uint32_t)((2 * s + 0) * npad * 32);
-                    const uint32_t bl = sbase + L.b_off + (uint32_t)((2 * s + 1) * npad * 32);
-                    tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bh), idesc, s > 0 ? 1u : 0u);
-                    tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
-                    tc::mma_tf32(d_tmem, tc::smem_desc(al), tc::smem_desc(bh), idesc, 1u);
+                    for (int s = 0; s < KD; ++s) {
+                        const uint32_t ah = ab + (uint32_t)s * kStepBytes;
+                        const uint32_t al = ab + (uint32_t)(KD + s) * kStepBytes;
+                        const uint32_t bh = sbase + L.b_off + (uint32_t)((2 * s + 0) * npad * 32);
+                        const uint32_t bl = sbase + L.b_off + (uint32_t)((2 * s + 1) * npad * 32);
+                        tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bh), idesc, s > 0 ? 1u : 0u);
+                        tc::mma_tf32(d_tmem, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
+                        tc::mma_tf32(d_tmem, tc::smem_desc(al), tc::smem_desc(bh), idesc, 1u);
+                    }
+                    const uint32_t bn = sbase + L.b_off + (uint32_t)(2 * KD * npad * 32);
+                    tc::mma_tf32(d_tmem, tc::smem_desc(sbase + L.ones_off), tc::smem_desc(bn), idesc, 1u);
                 }
-                const uint32_t bn = sbase + L.b_off + (uint32_t)(2 * KD * npad * 32);
-                tc::mma_tf32(d_tmem, tc::smem_desc(sbase + L.ones_off), tc::smem_desc(bn), idesc, 1u);
                 tc::mma_commit(&bars.acc_full[b]);
                 phase ^= 1u << b;
                 tc::mma_commit(&bars.a_empty[sa]);
@@ -357,13 +416,14 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
             tc::mbar_wait(&bars.drain, 0u, kWaitTries);
         }
     } else {
-        // ---------------- epilogue group g: tiles i = g, g + 2, ...
+        // ---------------- epilogue group g: units u = g, g + 2, ...
         const int ew = warp - 6;
         const int g = ew >> 2;
         const int quarter = warp & 3;                      // TMEM lanes 32 * (warp % 4) ...
         const int row = 32 * quarter + lane;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
         const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float thr_base = 2.0f * st->cmax2;
         int* rq = reinterpret_cast<int*>(smem + L.rq_off) + ew * kRecheckQ;
         int rq_n = 0;                                      // warp-uniform queue length
         // hands the queued flagged points to the global recheck list (one atomic)
@@ -377,52 +437,51 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
             __syncwarp();
             rq_n = 0;
         };
-        const float thr_base = 2.0f * st->cmax2;
         long long* sacc = reinterpret_cast<long long*>(smem + L.acc_off + (size_t)ew * L.acc_bytes);
         int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);
+        // per-warp partials hold at most 2^16 points: fold them every 2^16 / (32 T) units
+        const long long flush_units = kFlushPoints / (32 * T);
         uint32_t phase = 0u;                 // bit s: parity of accumulator g NB + s's next use
         long long qloc = 0;
         long long done = 0;
-        for (long long i = g; i < cnt; i += 2) {
-            const int slot = (int)((i >> 1) % NB);
+        for (long long u = g; u < units; u += 2) {
+            const int slot = (int)((u >> 1) % NB);
             const int b = g * NB + slot;
-            const int rs = (int)(i % RS);
+            const int rs = (int)(u % RS);
             bool w = wait_bar(&bars.acc_full[b], (phase >> slot) & 1u, abort_v, st);
-            w = w && wait_bar(&bars.raw_full[rs], (uint32_t)((i / RS) & 1), abort_v, st);
+            w = w && wait_bar(&bars.raw_full[rs], (uint32_t)((u / RS) & 1), abort_v, st);
             if (!__all_sync(0xffffffffu, w)) break;
             tc::fence_after_sync();
-            float B1 = INFINITY, B2 = INFINITY;
-            int BI = 0;
-            for (int c0 = 0; c0 < npad; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * npad + c0), v);
-                float q1[4], q2[4];
+            const int nt = tiles_in(u);
+            float B1[T], B2[T];
+            int BI[T];
+            // top-2 of every tile's row, the next 32 columns loading while the
+            // current ones are compared
+            {
+                const uint32_t cb = tmem + lane_addr + (uint32_t)(b * T * npad);
+                const int chunks = nt * (npad / 32);          // 32-column blocks of this unit
+                uint32_t ra[32], rb[32];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
+                for (int t = 0; t < T; ++t) { B1[t] = INFINITY; B2[t] = INFINITY; BI[t] = 0; }
+                tc::tmem_ld32_async(cb, ra);
+                tc::tmem_wait_ld();
+                for (int q = 0; q < chunks; q += 2) {
+                    if (q + 1 < chunks) tc::tmem_ld32_async(cb + (uint32_t)((q + 1) * 32), rb);
+                    {
+                        const int t = (q * 32) / npad, c0 = (q * 32) % npad;
 #pragma unroll
-                for (int j = 0; j < 32; j += 8) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jj = j + 2 * q;
-                        const float k0 = pack_key(v[jj], (unsigned)jj);
-                        const float k1 = pack_key(v[jj + 1], (unsigned)jj + 1u);
-                        const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                        q2[q] = fmin3(q2[q], hi, fmaxf(q1[q], lo));
-                        q1[q] = fminf(q1[q], lo);
+                        for (int tt = 0; tt < T; ++tt)
+                            if (tt == t) top2_cols(ra, c0, B1[tt], B2[tt], BI[tt]);
                     }
-                }
-                const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
-                const float l01 = fminf(q1[0], q1[1]);
-                const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
-                const float l23 = fminf(q1[2], q1[3]);
-                const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
-                const float b1 = fminf(l01, l23);
-                if (b1 < B1) {
-                    B2 = fminf(B1, b2);
-                    B1 = b1;
-                    BI = c0 | (int)(__float_as_uint(b1) & 31u);
-                } else {
-                    B2 = fminf(B2, b1);
+                    tc::tmem_wait_ld();
+                    if (q + 1 < chunks) {
+                        if (q + 2 < chunks) tc::tmem_ld32_async(cb + (uint32_t)((q + 2) * 32), ra);
+                        const int t = ((q + 1) * 32) / npad, c0 = ((q + 1) * 32) % npad;
+#pragma unroll
+                        for (int tt = 0; tt < T; ++tt)
+                            if (tt == t) top2_cols(rb, c0, B1[tt], B2[tt], BI[tt]);
+                        tc::tmem_wait_ld();
+                    }
                 }
             }
             tc::fence_before_sync();
@@ -430,73 +489,79 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
             if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
             phase ^= 1u << slot;
 
-            // ---- decide row `row` of tile i from its raw FP32 values
-            const long long tile = blockIdx.x + i * gridDim.x;
-            const long long p = tile * kRows + row;
-            const bool valid = p < n;
-            float x[D];
-            const float* src = raw + (size_t)rs * kRows * D + (size_t)row * D;
+            // ---- decide row `row` of each tile from its raw FP32 values
 #pragma unroll
-            for (int q = 0; q < D / 4; ++q) {
-                const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * q)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
-            }
-            float xn2 = 0.f;
+            for (int t = 0; t < T; ++t) {
+                if (t >= nt) break;
+                const long long tile = tile_of(u, t);
+                const long long p = tile * kRows + row;
+                const bool valid = p < n;
+                float x[D];
+                const float* src = raw + (size_t)rs * kRawUnit + ((size_t)t * kRows + row) * D;
 #pragma unroll
-            for (int t = 0; t < D; ++t) xn2 = fmaf(x[t], x[t], xn2);
-            const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1) + fabsf(B2));
-            const bool flag = valid && (B2 - B1 <= thr);
-            if (mode == kModeFull && valid) {
-#pragma unroll
-                for (int t = 0; t < D; ++t) qloc += sq_fixed(x[t], scaleG);
-            }
-            {
-                const unsigned m = __ballot_sync(0xffffffffu, flag);
-                if (m) {
-                    if (rq_n + 32 > kRecheckQ) rq_flush();
-                    if (flag) rq[rq_n + __popc(m & lanemask_lt())] = (int)p;
-                    rq_n += __popc(m);
+                for (int q = 0; q < D / 4; ++q) {
+                    const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * q)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
                 }
-            }
-            if (valid && !flag) {
-                const bool from_ring = lab_bulk && (long long)row < ((n - tile * kRows) & ~3ll);
-                const int old = (mode == kModeDelta)
-                                    ? (from_ring ? lab_ring[(size_t)rs * kRows + row] : labels[p])
-                                    : -1;
-                if (BI != old) {
+                float xn2 = 0.f;
 #pragma unroll
-                    for (int t = 0; t < D; ++t) {
-                        const long long val = to_fixed(x[t], scaleF);
-                        if (L.sacc) {
-                            atomicAdd(reinterpret_cast<unsigned long long*>(sacc + BI * D + t),
-                                      (unsigned long long)val);
-                            if (old >= 0)
-                                atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + t),
-                                          (unsigned long long)(-val));
-                        } else {
-                            split_add(acc.s_lo + (long long)BI * D + t,
-                                      acc.s_hi + (long long)BI * D + t, val);
-                            if (old >= 0)
-                                split_add(acc.s_lo + (long long)old * D + t,
-                                          acc.s_hi + (long long)old * D + t, -val);
+                for (int e = 0; e < D; ++e) xn2 = fmaf(x[e], x[e], xn2);
+                const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1[t]) + fabsf(B2[t]));
+                const bool flag = valid && (B2[t] - B1[t] <= thr);
+                if (mode == kModeFull && valid) {
+#pragma unroll
+                    for (int e = 0; e < D; ++e) qloc += sq_fixed(x[e], scaleG);
+                }
+                {
+                    const unsigned m = __ballot_sync(0xffffffffu, flag);
+                    if (m) {
+                        if (rq_n + 32 > kRecheckQ) rq_flush();
+                        if (flag) rq[rq_n + __popc(m & lanemask_lt())] = (int)p;
+                        rq_n += __popc(m);
+                    }
+                }
+                if (valid && !flag) {
+                    const bool from_ring = lab_bulk && (long long)row < ((n - tile * kRows) & ~3ll);
+                    const int old = (mode == kModeDelta)
+                                        ? (from_ring ? lab_ring[((size_t)rs * T + t) * kRows + row]
+                                                     : labels[p])
+                                        : -1;
+                    const int lab = BI[t];
+                    if (lab != old) {
+#pragma unroll
+                        for (int e = 0; e < D; ++e) {
+                            const long long val = to_fixed(x[e], scaleF);
+                            if (L.sacc) {
+                                atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * D + e),
+                                          (unsigned long long)val);
+                                if (old >= 0)
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * D + e),
+                                              (unsigned long long)(-val));
+                            } else {
+                                split_add(acc.s_lo + (long long)lab * D + e,
+                                          acc.s_hi + (long long)lab * D + e, val);
+                                if (old >= 0)
+                                    split_add(acc.s_lo + (long long)old * D + e,
+                                              acc.s_hi + (long long)old * D + e, -val);
+                            }
                         }
+                        if (L.sacc) {
+                            atomicAdd(scnt + lab, 1);
+                            if (old >= 0) atomicAdd(scnt + old, -1);
+                        } else {
+                            atomicAdd(acc.cnt + lab, 1ull);
+                            if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                        }
+                        labels[p] = lab;
                     }
-                    if (L.sacc) {
-                        atomicAdd(scnt + BI, 1);
-                        if (old >= 0) atomicAdd(scnt + old, -1);
-                    } else {
-                        atomicAdd(acc.cnt + BI, 1ull);
-                        if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
-                    }
-                    labels[p] = BI;
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.raw_empty[rs]);
-            // static flush schedule: at most kWarpFlushTiles tiles (2^16 points) per partial
+            // static flush schedule: at most 2^16 points per partial
             ++done;
-            if (done % kWarpFlushTiles == 0 || i + 2 >= cnt) {
+            if (done % flush_units == 0 || u + 2 >= units) {
                 long long qs = qloc;
                 for (int o = 16; o; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
                 if (lane == 0 && qs) split_add(&st->q_lo, &st->q_hi, qs);
@@ -546,12 +611,11 @@ inline float tc32_kappa(int KD)
 
 namespace {
 
-template <int D>
-int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageState* st,
-              const Accum& acc, int* list, cudaStream_t s, int sm_count)
+template <int D, int T>
+int launch_tc_t(const float* X, long long n, const Centers& c, int* labels, StageState* st,
+                const Accum& acc, int* list, cudaStream_t s, int sm_count, int npad)
 {
     using C = TcCfg<D>;
-    const int npad = (c.k + 31) / 32 * 32;
     // ring depths and per-warp partial sums, deepest first, within the budget
     TcLayout L{};
     bool found = false;
@@ -559,7 +623,7 @@ int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageS
         for (int rs = kMaxRS; rs >= 3 && !found; --rs)
             for (int sa = kMaxSA; sa >= 2 && !found; --sa) {
                 if (sa > rs - 1) continue;
-                L = tc_layout(D, npad, c.k, rs, sa, sacc);
+                L = tc_layout(D, T, npad, c.k, rs, sa, sacc);
                 found = L.total <= (uint32_t)kSmemBudget;
             }
     if (!found) {
@@ -568,18 +632,29 @@ int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageS
     }
     L.lab_bulk = (reinterpret_cast<uintptr_t>(labels) & 15) == 0 ? 1 : 0;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * L.nb * npad)) cols <<= 1;
-    KM2_TRY(set_max_dynamic_smem((const void*)assign_tc32<D>, kSmemBudget));
+    while (cols < (uint32_t)(2 * L.nb * T * npad)) cols <<= 1;
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_tc32<D, T>, kSmemBudget));
     const long long tiles = (n + kRows - 1) / kRows;
     long long grid = sm_count;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
     ++g_launches;
-    assign_tc32<D><<<(int)grid, kThreads, L.total, s>>>(X, n, c, labels, st, acc, list,
-                                                        tc32_kappa(C::KD), kPackSlack, npad, cols,
-                                                        L);
+    assign_tc32<D, T><<<(int)grid, kThreads, L.total, s>>>(X, n, c, labels, st, acc, list,
+                                                           tc32_kappa(C::KD), kPackSlack, npad,
+                                                           cols, L);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
+}
+
+// Tiles per unit: four while a unit's accumulator stays within 128 columns.
+template <int D>
+int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageState* st,
+              const Accum& acc, int* list, cudaStream_t s, int sm_count)
+{
+    const int npad = (c.k + 31) / 32 * 32;
+    if (npad <= 32) return launch_tc_t<D, 4>(X, n, c, labels, st, acc, list, s, sm_count, npad);
+    if (npad <= 64) return launch_tc_t<D, 2>(X, n, c, labels, st, acc, list, s, sm_count, npad);
+    return launch_tc_t<D, 1>(X, n, c, labels, st, acc, list, s, sm_count, npad);
 }
 
 }  // namespace
