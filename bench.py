@@ -402,45 +402,45 @@ def run_ours(args, cfg):
 SERVE = dict(rate=200.0, duration=60.0, seed=0, f=0.1, tol=1e-6, max_iter=100)
 
 
-def _serve_trace(trace, srv, dev, stream, *, drain_cap: float, data_cap_bytes: int):
-    """Replay the arrival trace against one server: a client thread generates
-    each job's data on the device at its arrival time and submits it; the main
-    thread collects finished jobs.  Latency = completion - scheduled arrival,
-    both on the server's clock.  Jobs still unfinished drain_cap seconds after
-    the last arrival are reported as censored (latency >= their age)."""
-    import torch
+def _serve_trace(trace, srv, dev, *, drain_cap: float):
+    """Replay the arrival trace against one server: a client thread submits each
+    job at its arrival time as a lazy job (its points are generated on the
+    device only when the server admits it, so waiting jobs hold no device
+    memory); the main thread collects finished jobs.  Latency = completion -
+    scheduled arrival, both on the server's clock.  Jobs still unfinished
+    drain_cap seconds after the last arrival are reported as censored
+    (latency >= their age)."""
     from paper_1108_1351_gb300 import synth
 
-    outstanding = {}            # ticket -> (job spec, scheduled arrival, bytes)
+    outstanding = {}            # ticket -> (job spec, scheduled arrival)
     lock = threading.Lock()
-    state = {"bytes": 0, "submitted": 0, "late": 0.0, "error": None}
+    state = {"submitted": 0, "late": 0.0, "error": None}
     stop = threading.Event()
     start = srv.now() + 0.5
 
+    def make_for(js):
+        def make(X):
+            X.copy_(synth.iso_gaussian_mixture(js.n, js.d, js.k, js.seed, lo=-20.0, hi=20.0,
+                                               device=dev))
+        return make
+
     def client():
         try:
-            with torch.cuda.device(dev), torch.cuda.stream(stream):
-                for js in trace:
-                    t_sched = start + js.t_arrival
-                    while not stop.is_set():
-                        with lock:
-                            room = state["bytes"] + js.n * js.d * 4 <= data_cap_bytes or not outstanding
-                        now = srv.now()
-                        if room and now >= t_sched:
-                            break
-                        time.sleep(min(0.002, max(0.0, t_sched - now)) if room else 0.002)
-                    if stop.is_set():
-                        return
-                    state["late"] = max(state["late"], srv.now() - t_sched)
-                    X = synth.iso_gaussian_mixture(js.n, js.d, js.k, js.seed, lo=-20.0, hi=20.0,
-                                                   device=dev)
-                    stream.synchronize()
-                    t = srv.submit(X, js.k, SERVE["f"], js.seed, SERVE["tol"], SERVE["max_iter"])
-                    with lock:
-                        outstanding[t] = (js, t_sched, js.n * js.d * 4)
-                        state["bytes"] += js.n * js.d * 4
-                        state["submitted"] += 1
-                    del X
+            for js in trace:
+                t_sched = start + js.t_arrival
+                while not stop.is_set():
+                    now = srv.now()
+                    if now >= t_sched:
+                        break
+                    time.sleep(min(0.002, t_sched - now))
+                if stop.is_set():
+                    return
+                state["late"] = max(state["late"], srv.now() - t_sched)
+                with lock:      # recorded before the collector can see it finish
+                    t = srv.submit_lazy(js.n, js.d, js.k, SERVE["f"], js.seed, SERVE["tol"],
+                                        SERVE["max_iter"], make_for(js))
+                    outstanding[t] = (js, t_sched)
+                    state["submitted"] += 1
         except Exception as e:      # reported by the collector
             state["error"] = repr(e)
 
@@ -449,30 +449,24 @@ def _serve_trace(trace, srv, dev, stream, *, drain_cap: float, data_cap_bytes: i
     done = []
     last_arrival = start + (trace[-1].t_arrival if trace else 0.0)
     while True:
-        with lock:
-            tickets = list(outstanding)
-        for t in tickets:
-            sv = srv.poll(t)
-            if sv is None:
-                continue
+        sv = srv.wait_any(0.05)          # blocks in the library, without the GIL
+        if sv is not None:
             with lock:
-                js, t_sched, b = outstanding.pop(t)
-                state["bytes"] -= b
+                js, t_sched = outstanding.pop(sv.ticket)
             done.append((js, t_sched, sv))
+            continue
         if state["error"]:
             raise RuntimeError(state["error"])
         if not th.is_alive() and not outstanding and state["submitted"] == len(trace):
             break
         if srv.now() > last_arrival + drain_cap:
             break
-        time.sleep(0.001)
+        time.sleep(0.002)
     t_end = srv.now()
     stop.set()
     th.join(timeout=120)
-    censored = []
     with lock:
-        for t, (js, t_sched, b) in outstanding.items():
-            censored.append(t_end - t_sched)
+        censored = [t_end - t_sched for (js, t_sched) in outstanding.values()]
     never = len(trace) - state["submitted"]
     return done, censored, never, start, t_end, state["late"]
 
@@ -509,9 +503,7 @@ def run_serve(args):
     km.load()
     trace = synth.arrival_trace(rate=SERVE["rate"], duration=args.duration, seed=SERVE["seed"] + rank)
     free, total = torch.cuda.mem_get_info(dev)
-    budget = int(free * 0.45)
-    data_cap = int(free * 0.3)
-    stream = torch.cuda.Stream(dev)
+    budget = int(free * 0.8)
     # warm-up: one small job of each dimension through a throwaway server
     with km.Server(hbm_budget=budget, max_slots=2) as srv:
         for d in (4, 16, 64, 128):
@@ -525,7 +517,7 @@ def run_serve(args):
         with km.Server(hbm_budget=budget, max_slots=slots, precision=prec, policy=policy,
                        aging_s=args.aging) as srv:
             done, censored, never, start, t_end, late = _serve_trace(
-                trace, srv, dev, stream, drain_cap=args.drain_cap, data_cap_bytes=data_cap)
+                trace, srv, dev, drain_cap=args.drain_cap)
             summ = _latency_summary(done, censored, never, start, t_end)
             st = srv.stats()
         summ.update({"slots": slots, "precision": prec, "policy": policy,
@@ -619,6 +611,59 @@ def run_sweep(args):
     return 0
 
 
+def run_streamed(args, cfg):
+    """Host-resident X streamed through the GPU each slow-stage iteration
+    (kmeans2_fit_streamed), on the default workload held in pinned host
+    memory, with the resident fit on the same data beside it."""
+    import torch
+    import paper_1108_1351_gb300 as km
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.load()
+    n, d, k = cfg["n"], cfg["d"], cfg["k"]
+    Xd = _gen(cfg, dev, cfg["seed"] + rank)
+    Xh = torch.empty((n, d), dtype=torch.float32, pin_memory=True)
+    Xh.copy_(Xd)
+    args_fit = (k, cfg["f"], cfg["seed"] + rank, cfg["tol"], cfg["max_iter"])
+    resident = km.fit(Xd, *args_fit, precision="fp32")
+    torch.cuda.synchronize()
+    del Xd
+    torch.cuda.empty_cache()
+    for _ in range(args.warmup):
+        r = km.fit_streamed(Xh, *args_fit, args.chunk_points)
+    clk = ClockSampler(None)
+    clk.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = km.fit_streamed(Xh, *args_fit, args.chunk_points)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / args.steps
+    clocks = clk.stop()
+    same = (r.J == resident.J and (r.iters_fast, r.iters_slow) ==
+            (resident.iters_fast, resident.iters_slow))
+    t_ms, evals = reduce_over_ranks(1e3 * t, r.distance_evals, ws, dev)
+    if rank != 0:
+        return 0
+    passes = r.iters_slow + 1                 # the max-|x| pass and every slow iteration
+    line = {"metric": METRIC, "value": evals / (t_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "streamed", "n": n, "d": d, "k": k,
+                       "chunk_points": args.chunk_points, "X_host_gb": n * d * 4 / 1e9,
+                       "host_memory": "pinned"},
+            "time_to_converge_s": t_ms / 1e3,
+            "h2d_gb_per_s": passes * n * d * 4 / (t_ms * 1e-3) / 1e9,
+            "resident_time_to_converge_s": resident.seconds,
+            "identical_to_resident": bool(same),
+            "fit": {"J": r.J, "iters_fast": r.iters_fast, "iters_slow": r.iters_slow},
+            "roofline": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 BATCH = dict(count=4096, seed=0, f=0.1, tol=1e-6, max_iter=100)
 
 
@@ -637,7 +682,9 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     km.load()
-    specs = synth.instance_specs(args.instances, seed=BATCH["seed"] + rank * args.instances)
+    dims = tuple(int(v) for v in args.batch_dims.split(",")) if args.batch_dims else (2, 8, 32, 64)
+    specs = synth.instance_specs(args.instances, seed=BATCH["seed"] + rank * args.instances,
+                                 dims=dims)
     Xs = [synth.instance_data(s, device=dev) for s in specs]
     torch.cuda.synchronize()
     ks = [s.k for s in specs]
@@ -700,7 +747,7 @@ def run_batched(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "batched", "instances": len(specs), "points": npts,
-                   "n": "log-U[1e3, 1e6]", "d": [2, 8, 32, 64], "k": "U[2, 256]",
+                   "n": "log-U[1e3, 1e6]", "d": list(dims), "k": "U[2, 256]",
                    "subset_fraction": BATCH["f"], "tol": BATCH["tol"],
                    "max_iter": BATCH["max_iter"],
                    "l2": "inputs larger than L2 (%.1f GB)" % (sum(s.n * s.d for s in specs) * 4e-9)},
@@ -721,12 +768,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="aniso8",
-                    choices=sorted(CONFIGS) + ["serve", "batched", "sweep"])
+                    choices=sorted(CONFIGS) + ["serve", "batched", "sweep", "streamed"])
+    ap.add_argument("--chunk-points", type=int, default=1 << 26,
+                    help="streamed: rows per streamed chunk")
     ap.add_argument("--sweep-n", type=int, default=10_000_000, help="sweep: points")
     ap.add_argument("--sweep-d", type=int, default=12, help="sweep: dimensions")
     ap.add_argument("--sweep-k", type=int, default=16, help="sweep: clusters")
     ap.add_argument("--instances", type=int, default=BATCH["count"],
                     help="batched: number of independent instances")
+    ap.add_argument("--batch-dims", default="",
+                    help="batched: comma-separated dimensions to draw from (default 2,8,32,64)")
     ap.add_argument("--duration", type=float, default=SERVE["duration"],
                     help="serve: seconds of Poisson arrivals")
     ap.add_argument("--serve-slots", type=int, default=8, help="serve: jobs running at once")
@@ -741,6 +792,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
+    if args.config == "streamed":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the streamed workload compares "
+                              "with the resident GPU fit in the same line"}))
+            return 0
+        return run_streamed(args, CONFIGS["aniso8"])
     if args.config == "sweep":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the sweep compares two GPU "

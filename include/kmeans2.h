@@ -166,6 +166,131 @@ KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, dou
                 uint64_t seed, double tol, int32_t max_iter, double* centers_out,
                 int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt);
 
+/*
+ * kmeans2_fit_streamed -- kmeans2_fit for data that stays in HOST memory (for
+ * instance larger than the GPU's HBM; Abstract and Section 6: the method is
+ * aimed at very large data sets).  Same method, arguments and results as
+ * kmeans2_fit, and the same results bit for bit: S_s is gathered on the host
+ * and copied to the device once (the fast stage runs resident); every
+ * iteration of the slow stage streams X through the device in chunks of
+ * chunk_points rows (two device buffers, copies on a second stream
+ * overlapping the distance kernel of the previous chunk), with the near-tie
+ * recheck of each chunk done while it is resident and the exact integer
+ * cluster sums accumulated across chunks.  The device holds the labels (n
+ * int32, unless labels_out is device memory), two chunks, S_s and the
+ * workspace.  Pinned host memory (cudaHostRegister / cudaMallocHost) makes
+ * the copies asynchronous; pageable memory works, synchronously.
+ *
+ *  X             n*d FP32 points in host memory.
+ *  chunk_points  rows per chunk, >= 1.
+ *  opt           precision must be FP32 or AUTO (the CUDA-core form);
+ *                use_graph is ignored (the slow stage is host-driven).
+ * Errors as kmeans2_fit; KMEANS2_ERR_INVALID if X is device memory or
+ * chunk_points < 1, KMEANS2_ERR_UNSUPPORTED for a tensor-core precision.
+ */
+KMEANS2_API int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k,
+                                     double subset_fraction, uint64_t seed, double tol,
+                                     int32_t max_iter, int64_t chunk_points, double* centers_out,
+                                     int32_t* labels_out, kmeans2_result* res,
+                                     const kmeans2_options* opt);
+
+/* ---------------------------------------------------------------- data-parallel shards
+ *
+ * The method split over the rows of S_n the way a group of GPUs runs it (one
+ * rank per GPU): each rank keeps its rows, their labels, its exact integer
+ * cluster sums and near-tie list, and a replicated copy of the centers.  Per
+ * Lloyd iteration (Section 4.1) the ranks all-reduce the integer partials of
+ * the centroid update -- sum_i x_i split into two int64 words, N_j and, in a
+ * stage's first iteration, sum ||x||^2 -- and every rank runs the same
+ * finalize on the totals.  Integer sums do not depend on the order of the
+ * reduction, so labels, centers, J and iteration counts equal those of
+ * kmeans2_fit on the whole of X, bit for bit, for any number of ranks and any
+ * split.  S_s needs no exchange (its keys depend only on global positions);
+ * the initial centers and each stage's max |x| are one small all-reduce each.
+ *
+ * The caller owns the exchange: kmeans2_shard_advance runs the rank's kernels
+ * up to the next exchange point and says what to all-reduce, in place, in the
+ * caller's exchange buffer (NCCL or any collective library; every rank gets
+ * the same descriptor at the same step).  Then it is called again.
+ */
+typedef struct kmeans2_shard kmeans2_shard;
+
+#define KMEANS2_XCHG_SUM_I64 0   /* int64 sum (two's complement wrap-around) */
+#define KMEANS2_XCHG_MAX_I64 1   /* int64 maximum */
+#define KMEANS2_XCHG_SUM_F64 2   /* FP64 sum; exact in any order for this use */
+
+typedef struct kmeans2_exchange {
+    int32_t op;          /* KMEANS2_XCHG_* */
+    int32_t reserved;
+    int64_t count;       /* 8-byte elements of the exchange buffer to reduce, from element 0 */
+} kmeans2_exchange;
+
+/* 8-byte elements the exchange buffer must hold for (d, k): 2 k d + k + 5;
+ * -1 for d < 1 or k < 1. */
+KMEANS2_API int64_t kmeans2_shard_exchange_elems(int32_t d, int32_t k);
+
+/*
+ * kmeans2_shard_create -- one rank's session of a data-parallel fit.
+ *
+ *  X_local       n_local*d FP32 rows of S_n (host or device; copied to the
+ *                device when host or misaligned), global rows
+ *                [row0, row0 + n_local).  n_local may be 0 (X_local NULL).
+ *  n_total       n of the whole data set; the ranks' row ranges must
+ *                partition [0, n_total).
+ *  subset_fraction, seed, tol, max_iter, opt   as kmeans2_fit, identical on
+ *                every rank (opt->stream, trajectories and profile are per rank).
+ *  exchange_buf  device memory, 8-byte aligned, kmeans2_shard_exchange_elems
+ *                elements; owned by the caller, alive until destroy.
+ *  out           receives the session; destroy it with kmeans2_shard_destroy.
+ * Draws S_s (all n_total keys) and gathers this rank's part of it.
+ * Errors: KMEANS2_ERR_INVALID (arguments as kmeans2_fit, row range outside
+ * [0, n_total), exchange buffer not device memory), KMEANS2_ERR_NOMEM,
+ * KMEANS2_ERR_UNSUPPORTED, KMEANS2_ERR_CUDA.
+ */
+KMEANS2_API int kmeans2_shard_create(const float* X_local, int64_t n_local, int64_t row0,
+                                     int64_t n_total, int32_t d, int32_t k,
+                                     double subset_fraction, uint64_t seed, double tol,
+                                     int32_t max_iter, void* exchange_buf,
+                                     const kmeans2_options* opt, kmeans2_shard** out);
+
+/*
+ * kmeans2_shard_advance -- run this rank to its next exchange point.
+ * Returns KMEANS2_PENDING with *next set: the first next->count elements of
+ * the exchange buffer are ready (the rank's stream is synchronised) and must
+ * be all-reduced across ranks with next->op, in place, before the next call.
+ * Returns KMEANS2_OK once the fit has finished (every rank at the same call),
+ * or a negative status (the same on every rank for data errors such as
+ * KMEANS2_ERR_NONFINITE; a device-side timeout on one rank reaches the others
+ * through the next exchange).  After an error the session only reports it.
+ */
+KMEANS2_API int kmeans2_shard_advance(kmeans2_shard* sh, kmeans2_exchange* next);
+
+/* Results of a finished session: centers (k*d FP64, host or device; the same
+ * on every rank), this rank's n_local labels (host or device), and res (J,
+ * iteration counts and distance_evals are global; rechecked_points counts
+ * this rank's points).  Any output may be NULL.  KMEANS2_ERR_INVALID before
+ * the fit has finished; the session's error after a failure. */
+KMEANS2_API int kmeans2_shard_result(kmeans2_shard* sh, double* centers_out, int32_t* labels_out,
+                                     kmeans2_result* res);
+
+/* Waits for the rank's stream and frees the session (NULL is a no-op). */
+KMEANS2_API void kmeans2_shard_destroy(kmeans2_shard* sh);
+
+/*
+ * kmeans2_fit_sharded -- kmeans2_fit run as `shards` ranks on this one GPU:
+ * the rows of X are split into contiguous blocks (boundaries on multiples of
+ * 4 rows), one session per block, and each exchange is reduced in rank order
+ * by a kernel over the sessions' buffers.  Results equal kmeans2_fit bit for
+ * bit; a rank whose centers differ from rank 0's at the end is reported as
+ * KMEANS2_ERR_CUDA ("shard replicas diverged").  res->rechecked_points sums
+ * the ranks.  Arguments as kmeans2_fit; 1 <= shards <= 64.
+ */
+KMEANS2_API int kmeans2_fit_sharded(const float* X, int64_t n, int32_t d, int32_t k,
+                                    double subset_fraction, uint64_t seed, double tol,
+                                    int32_t max_iter, int32_t shards, double* centers_out,
+                                    int32_t* labels_out, kmeans2_result* res,
+                                    const kmeans2_options* opt);
+
 /* One independent clustering problem: an entry of a batch (kmeans2_fit_batched)
    or a request to a server (kmeans2_server_submit).  The limits in brackets
    are the batched form's; a server job takes any shape kmeans2_fit takes. */
@@ -287,6 +412,36 @@ KMEANS2_API int kmeans2_server_poll(kmeans2_server* srv, uint64_t ticket, kmeans
    for the job to finish; KMEANS2_PENDING if it has not. */
 KMEANS2_API int kmeans2_server_wait(kmeans2_server* srv, uint64_t ticket, double timeout_s,
                                     kmeans2_result* res, kmeans2_ticket_times* times);
+
+/*
+ * Lazy input: a job whose points are produced only when it is admitted, so
+ * that waiting jobs hold no device memory (a request queue under overload).
+ *
+ *  materialize(user, X, stream)  called on the worker thread, with the server's
+ *      device current, once the job is admitted: it must enqueue on `stream`
+ *      (a cudaStream_t) the writing of the job's n*d FP32 points to X (device
+ *      memory owned by the server, 16-byte aligned, valid until the job is
+ *      done) and return 0, or return nonzero to fail the job
+ *      (KMEANS2_ERR_INVALID).
+ *  consume(user, centers, labels, stream)  may be NULL: called after the fit
+ *      with its device centers (k*d FP64) and labels (n int32), which the
+ *      server frees when consume returns; copies must be enqueued on `stream`.
+ *  job->X, centers_out and labels_out are ignored (NULL); the job's footprint
+ *  counts the n*d*4 bytes of X.  Otherwise as kmeans2_server_submit.
+ */
+typedef int (*kmeans2_materialize_fn)(void* user, float* X, void* stream);
+typedef void (*kmeans2_consume_fn)(void* user, const double* centers, const int32_t* labels,
+                                   void* stream);
+KMEANS2_API int kmeans2_server_submit_lazy(kmeans2_server* srv, const kmeans2_job* job,
+                                           kmeans2_materialize_fn materialize,
+                                           kmeans2_consume_fn consume, void* user,
+                                           uint64_t* ticket);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for some job to finish that
+   no earlier call returned, and writes its ticket: KMEANS2_OK, or
+   KMEANS2_PENDING on timeout.  The ticket is then collected with
+   kmeans2_server_poll. */
+KMEANS2_API int kmeans2_server_wait_any(kmeans2_server* srv, double timeout_s, uint64_t* ticket);
 
 /* Counters of the server; returns KMEANS2_ERR_INVALID for NULL arguments. */
 KMEANS2_API int kmeans2_server_stats_get(kmeans2_server* srv, kmeans2_server_stats* out);

@@ -118,7 +118,25 @@ class TicketTimes(ctypes.Structure):
                 ("t_done", ctypes.c_double)]
 
 
+class Exchange(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("count", ctypes.c_int64)]
+
+
 PENDING = 1
+XCHG_SUM_I64, XCHG_MAX_I64, XCHG_SUM_F64 = 0, 1, 2
+
+MATERIALIZE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+CONSUME_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p)
+
+
+class _DeviceView:
+    """__cuda_array_interface__ of library-owned device memory (zero-copy view)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
 
 
 def load():
@@ -138,6 +156,23 @@ def load():
         lib.kmeans2_fit.restype = ctypes.c_int
         lib.kmeans2_fit.argtypes = [P, i64, i32, i32, f64, u64, f64, i32, P, P,
                                     ctypes.POINTER(Result), ctypes.POINTER(Options)]
+        lib.kmeans2_fit_streamed.restype = ctypes.c_int
+        lib.kmeans2_fit_streamed.argtypes = [P, i64, i32, i32, f64, u64, f64, i32, i64, P, P,
+                                             ctypes.POINTER(Result), ctypes.POINTER(Options)]
+        lib.kmeans2_fit_sharded.restype = ctypes.c_int
+        lib.kmeans2_fit_sharded.argtypes = [P, i64, i32, i32, f64, u64, f64, i32, i32, P, P,
+                                            ctypes.POINTER(Result), ctypes.POINTER(Options)]
+        lib.kmeans2_shard_exchange_elems.restype = i64
+        lib.kmeans2_shard_exchange_elems.argtypes = [i32, i32]
+        lib.kmeans2_shard_create.restype = ctypes.c_int
+        lib.kmeans2_shard_create.argtypes = [P, i64, i64, i64, i32, i32, f64, u64, f64, i32, P,
+                                             ctypes.POINTER(Options), ctypes.POINTER(P)]
+        lib.kmeans2_shard_advance.restype = ctypes.c_int
+        lib.kmeans2_shard_advance.argtypes = [P, ctypes.POINTER(Exchange)]
+        lib.kmeans2_shard_result.restype = ctypes.c_int
+        lib.kmeans2_shard_result.argtypes = [P, P, P, ctypes.POINTER(Result)]
+        lib.kmeans2_shard_destroy.restype = None
+        lib.kmeans2_shard_destroy.argtypes = [P]
         lib.kmeans_step.restype = ctypes.c_int
         lib.kmeans_step.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, ctypes.POINTER(Options)]
         lib.kmeans2_fit_batched.restype = ctypes.c_int
@@ -151,6 +186,11 @@ def load():
         lib.kmeans2_server_create.argtypes = [u64, i32, ctypes.POINTER(Options)]
         lib.kmeans2_server_submit.restype = ctypes.c_int
         lib.kmeans2_server_submit.argtypes = [P, ctypes.POINTER(Job), ctypes.POINTER(u64)]
+        lib.kmeans2_server_submit_lazy.restype = ctypes.c_int
+        lib.kmeans2_server_submit_lazy.argtypes = [P, ctypes.POINTER(Job), MATERIALIZE_FN,
+                                                   CONSUME_FN, P, ctypes.POINTER(u64)]
+        lib.kmeans2_server_wait_any.restype = ctypes.c_int
+        lib.kmeans2_server_wait_any.argtypes = [P, f64, ctypes.POINTER(u64)]
         lib.kmeans2_server_poll.restype = ctypes.c_int
         lib.kmeans2_server_poll.argtypes = [P, u64, ctypes.POINTER(Result),
                                             ctypes.POINTER(TicketTimes)]
@@ -319,6 +359,169 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                      traj=traj)
 
 
+def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
+                 chunk_points: int, *, tol_fast: float = 0.0, init_centers=None,
+                 start_stage: int = 0, stream=None, centers_out=None,
+                 labels_out=None) -> "FitResult":
+    """Two-stage k-means on host-resident X streamed through the GPU in chunks
+    of chunk_points rows (kmeans2_fit_streamed); same results as fit().
+    X: a numpy array or a CPU tensor (pinned for asynchronous copies).
+    Outputs are host arrays unless given."""
+    lib = load()
+    if _is_torch(X) and X.is_cuda:
+        raise TypeError("fit_streamed takes host-resident X")
+    X = _as_points(X)
+    n, d = X.shape
+    C0 = _as_centers(init_centers, X) if init_centers is not None else None
+    cen = centers_out if centers_out is not None else np.empty((k, d), dtype=np.float64)
+    lab = labels_out if labels_out is not None else np.empty((n,), dtype=np.int32)
+    opt = Options()
+    lib.kmeans2_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION["fp32"]
+    opt.tol_fast = tol_fast
+    opt.init_centers = _ptr(C0) if C0 is not None else None
+    opt.start_stage = start_stage
+    dev = torch.device("cuda", torch.cuda.current_device())
+    opt.stream = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    res = Result()
+    with torch.cuda.device(dev):
+        rc = lib.kmeans2_fit_streamed(_ptr(X), n, d, k, subset_fraction, seed & (2**64 - 1), tol,
+                                      max_iter, int(chunk_points), _ptr(cen), _ptr(lab),
+                                      ctypes.byref(res), ctypes.byref(opt))
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans2_fit_streamed")
+    return _fit_result(res, cen, lab)
+
+
+def fit_sharded(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
+                shards: int, *, tol_fast: float = 0.0, precision: str = "auto",
+                init_centers=None, start_stage: int = 0, stream=None, centers_out=None,
+                labels_out=None) -> FitResult:
+    """fit() run as `shards` data-parallel ranks on this GPU (kmeans2_fit_sharded):
+    row blocks with their own sums and labels, partials all-reduced in rank
+    order each iteration.  Equal to fit() bit for bit."""
+    lib = load()
+    X = _as_points(X)
+    n, d = X.shape
+    C0 = _as_centers(init_centers, X)
+    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
+    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    opt = Options()
+    lib.kmeans2_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION[precision]
+    opt.tol_fast = tol_fast
+    opt.init_centers = _ptr(C0)
+    opt.start_stage = start_stage
+    opt.stream = _stream_of(X, stream)
+    res = Result()
+    with _device_of(X):
+        rc = lib.kmeans2_fit_sharded(_ptr(X), n, d, k, subset_fraction, seed & (2**64 - 1), tol,
+                                     max_iter, int(shards), _ptr(cen), _ptr(lab),
+                                     ctypes.byref(res), ctypes.byref(opt))
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans2_fit_sharded")
+    return _fit_result(res, cen, lab)
+
+
+class Shard:
+    """One rank's session of a data-parallel fit (kmeans2_shard_*).
+
+    ``advance()`` runs the rank to its next exchange point and returns
+    ``(op, buf)``: buf (a view of the session's device exchange buffer, int64
+    or float64) must be all-reduced across ranks with op ("sum" or "max") in
+    place before the next ``advance()``; None once the fit has finished."""
+
+    def __init__(self, X_local, row0: int, n_total: int, k: int, subset_fraction: float,
+                 seed: int, tol: float, max_iter: int, *, tol_fast: float = 0.0,
+                 precision: str = "auto", init_centers=None, start_stage: int = 0, stream=None):
+        lib = load()
+        if not (_is_torch(X_local) and X_local.is_cuda):
+            raise TypeError("Shard takes a CUDA tensor of this rank's rows")
+        self.X = _as_points(X_local)
+        self.n_local, self.d = self.X.shape
+        self.k = int(k)
+        self.device = self.X.device
+        E = int(lib.kmeans2_shard_exchange_elems(self.d, self.k))
+        self.xbuf = torch.zeros(E, dtype=torch.int64, device=self.device)
+        self._C0 = _as_centers(init_centers, self.X)
+        opt = Options()
+        lib.kmeans2_default_options(ctypes.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.tol_fast = tol_fast
+        opt.init_centers = _ptr(self._C0)
+        opt.start_stage = start_stage
+        opt.stream = _stream_of(self.X, stream)
+        h = ctypes.c_void_p()
+        with _device_of(self.X):
+            rc = lib.kmeans2_shard_create(_ptr(self.X) if self.n_local else None, self.n_local,
+                                          int(row0), int(n_total), self.d, self.k,
+                                          subset_fraction, seed & (2**64 - 1), tol, max_iter,
+                                          self.xbuf.data_ptr(), ctypes.byref(opt),
+                                          ctypes.byref(h))
+        if rc != 0:
+            raise KMeans2Error(rc, "kmeans2_shard_create")
+        self._h = h
+
+    def advance(self):
+        x = Exchange()
+        with _device_of(self.X):
+            rc = load().kmeans2_shard_advance(self._h, ctypes.byref(x))
+        if rc == 0:
+            return None
+        if rc != PENDING:
+            raise KMeans2Error(rc, "kmeans2_shard_advance")
+        buf = self.xbuf.view(torch.float64) if x.op == XCHG_SUM_F64 else self.xbuf
+        return ("max" if x.op == XCHG_MAX_I64 else "sum"), buf[:x.count]
+
+    def result(self) -> FitResult:
+        cen = torch.empty((self.k, self.d), dtype=torch.float64, device=self.device)
+        lab = torch.empty((self.n_local,), dtype=torch.int32, device=self.device)
+        res = Result()
+        with _device_of(self.X):
+            rc = load().kmeans2_shard_result(self._h, cen.data_ptr(), lab.data_ptr(),
+                                             ctypes.byref(res))
+        if rc != 0:
+            raise KMeans2Error(rc, "kmeans2_shard_result")
+        return _fit_result(res, cen, lab)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kmeans2_shard_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fit_data_parallel(X_local, row0: int, n_total: int, k: int, subset_fraction: float,
+                      seed: int, tol: float, max_iter: int, *, group=None, shard_factory=None,
+                      **kw) -> FitResult:
+    """The fit of the rows [row0, row0 + len(X_local)) of a data set split over
+    the ranks of a torch.distributed group (one rank per GPU): each rank runs
+    its Shard and every exchange is one all_reduce over the group.  Returns
+    this rank's labels and the replicated centers; all equal fit() on the
+    whole data.  ``shard_factory`` replaces Shard (same constructor and
+    methods)."""
+    import torch.distributed as dist
+
+    make = shard_factory or Shard
+    sh = make(X_local, row0, n_total, k, subset_fraction, seed, tol, max_iter, **kw)
+    ops = {"sum": dist.ReduceOp.SUM, "max": dist.ReduceOp.MAX}
+    try:
+        while True:
+            x = sh.advance()
+            if x is None:
+                break
+            op, buf = x
+            dist.all_reduce(buf, op=ops[op], group=group)
+        return sh.result()
+    finally:
+        sh.close()
+
+
 def _fit_result(r, cen, lab, traj=None) -> FitResult:
     return FitResult(centers=cen, labels=lab, J=r.J, iters_fast=r.iters_fast,
                      iters_slow=r.iters_slow, converged_fast=bool(r.converged_fast),
@@ -401,11 +604,59 @@ class Server:
             self._refs[t.value] = (X, cen, lab)
         return t.value
 
+    def submit_lazy(self, n: int, d: int, k: int, subset_fraction: float, seed: int, tol: float,
+                    max_iter: int, make, consume=None) -> int:
+        """Queue a job whose points are produced only at admission:
+        ``make(X)`` fills the (n, d) float32 CUDA tensor X in place on the
+        current stream (the worker's); ``consume(centers, labels)``, if given,
+        receives the fit's device outputs (valid during the call; copy them
+        on the current stream)."""
+        lib = load()
+        dev = self.device
+
+        def _run(stream, fn):
+            with torch.cuda.device(dev):
+                st = torch.cuda.ExternalStream(int(stream or 0), device=dev)
+                with torch.cuda.stream(st):
+                    fn()
+
+        def _mat(user, xptr, stream):
+            try:
+                X = torch.as_tensor(_DeviceView(xptr, (n, d), "<f4"), device=dev)
+                _run(stream, lambda: make(X))
+                return 0
+            except Exception:       # the library fails the job
+                return 1
+
+        def _con(user, cptr, lptr, stream):
+            try:
+                C = torch.as_tensor(_DeviceView(cptr, (k, d), "<f8"), device=dev)
+                L = torch.as_tensor(_DeviceView(lptr, (n,), "<i4"), device=dev)
+                _run(stream, lambda: consume(C, L))
+            except Exception:
+                pass
+
+        cb_m = MATERIALIZE_FN(_mat)
+        cb_c = CONSUME_FN(_con) if consume is not None else CONSUME_FN()
+        job = Job(X=None, n=int(n), d=int(d), k=int(k), subset_fraction=float(subset_fraction),
+                  seed=int(seed) & (2**64 - 1), tol=float(tol), max_iter=int(max_iter),
+                  reserved=0, centers_out=None, labels_out=None)
+        t = ctypes.c_uint64(0)
+        with self._mu:
+            rc = lib.kmeans2_server_submit_lazy(self._h, ctypes.byref(job), cb_m, cb_c, None,
+                                                ctypes.byref(t))
+            if rc != 0:
+                raise KMeans2Error(rc, "kmeans2_server_submit_lazy")
+            self._refs[t.value] = (cb_m, cb_c, None)
+        return t.value
+
     def _collect(self, ticket, rc, r, tt):
         if rc == PENDING:
             return None
         with self._mu:
             X, cen, lab = self._refs.pop(ticket, (None, None, None))
+        if not (_is_torch(cen) or isinstance(cen, np.ndarray)):
+            cen = lab = None            # lazy job: the outputs went to its consume callback
         res = _fit_result(r, cen, lab) if rc == 0 else None
         return Served(ticket=ticket, status=rc, result=res, t_submit=tt.t_submit,
                       t_admit=tt.t_admit, t_done=tt.t_done)
@@ -424,6 +675,15 @@ class Server:
         if rc == -1 and ticket not in self._refs:
             raise KMeans2Error(rc, "kmeans2_server_wait")
         return self._collect(ticket, rc, r, tt)
+
+    def wait_any(self, timeout: float = -1.0) -> "Served | None":
+        """The next finished job not yet returned by wait_any (collected), or
+        None if none finishes within `timeout` seconds."""
+        t = ctypes.c_uint64(0)
+        rc = load().kmeans2_server_wait_any(self._h, float(timeout), ctypes.byref(t))
+        if rc != 0:
+            return None
+        return self.poll(t.value)
 
     def stats(self) -> dict:
         st = ServerStats()

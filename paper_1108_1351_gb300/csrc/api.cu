@@ -111,7 +111,7 @@ int DeviceScratch::alloc(void** p, size_t bytes, cudaStream_t s)
     return KMEANS2_OK;
 }
 
-namespace {
+// ---------------------------------------------------------------- stage plumbing
 
 __global__ void fill_f32_kernel(float* p, long long count, float v)
 {
@@ -142,22 +142,6 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-struct Workspace {
-    int form = KMEANS2_PRECISION_FP32;   // distance-kernel form used by this call
-    Centers c{};
-    Accum acc{};
-    StageState* st = nullptr;
-    int* list = nullptr;
-    double* clus = nullptr;
-    double* traj_J = nullptr;      // max_iter
-    double* traj_shift = nullptr;  // max_iter
-    int max_iter = 0;
-    DeviceScratch* ws = nullptr;   // the call's scratch (per-stage buffers)
-    // BF16 form: the stage's points as BF16 tiles, their ||x||^2, the centers' chunks
-    unsigned char* xt = nullptr;
-    float* xn2 = nullptr;
-    unsigned char* cb = nullptr;
-};
 
 int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, int d,
                     int max_iter, cudaStream_t s)
@@ -419,11 +403,6 @@ int device_view(const float* X, long long count, const float** out, DeviceScratc
     return KMEANS2_OK;
 }
 
-struct Resolved {
-    cudaStream_t stream;
-    kmeans2_options opt;
-};
-
 Resolved resolve_options(const kmeans2_options* opt)
 {
     Resolved r;
@@ -438,7 +417,7 @@ Resolved resolve_options(const kmeans2_options* opt)
     return r;
 }
 
-}  // namespace
+
 
 // ---------------------------------------------------------------- fixed scratch
 // Scratch of kmeans_step_noalloc: one file-scope device array, present on every
@@ -761,6 +740,214 @@ int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_f
     rr.distance_evals = (int64_t)rr.iters_fast * m * k + (int64_t)rr.iters_slow * n * k;
 
     KM2_CUDA(cudaMemcpyAsync(centers_out, w.c.c64, sizeof(double) * (size_t)k * d,
+                             is_device_ptr(centers_out) ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyDeviceToHost, s));
+    if (!lab_dev)
+        KM2_CUDA(cudaMemcpyAsync(labels_out, labels, sizeof(int) * (size_t)n,
+                                 is_device_ptr(labels_out) ? cudaMemcpyDeviceToDevice
+                                                           : cudaMemcpyDeviceToHost, s));
+    KM2_CUDA(cudaStreamSynchronize(s));
+    rr.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = rr;
+    if (o.profile) o.profile->kernel_launches += g_launches - launches0;
+    return KMEANS2_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host-resident X streamed through two device chunk buffers: copies run on a
+// stream of their own and overlap the kernels of the previous chunk.
+struct ChunkStreamer {
+    const float* X = nullptr;
+    long long n = 0, chunk = 0, nchunks = 0;
+    int d = 0;
+    float* buf[2] = {nullptr, nullptr};
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+
+    long long rows(long long c) const { return c + 1 < nchunks ? chunk : n - c * chunk; }
+
+    int init(const float* X_, long long n_, int d_, long long chunk_, cudaStream_t s,
+             DeviceScratch& ws)
+    {
+        X = X_;
+        n = n_;
+        d = d_;
+        chunk = chunk_ < n_ ? chunk_ : n_;
+        nchunks = (n + chunk - 1) / chunk;
+        for (int b = 0; b < 2; ++b)
+            KM2_TRY(ws.alloc((void**)&buf[b], (size_t)chunk * d * sizeof(float), s));
+        KM2_CUDA(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            KM2_CUDA(cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming));
+            KM2_CUDA(cudaEventCreateWithFlags(&used[b], cudaEventDisableTiming));
+            KM2_CUDA(cudaEventRecord(used[b], s));      // both buffers start free
+        }
+        return KMEANS2_OK;
+    }
+    // Copy chunk c into buffer c % 2 once the kernels that read it last are done.
+    int fetch(long long c)
+    {
+        const int b = (int)(c & 1);
+        KM2_CUDA(cudaStreamWaitEvent(copy, used[b], 0));
+        KM2_CUDA(cudaMemcpyAsync(buf[b], X + (size_t)(c * chunk) * d, (size_t)rows(c) * d * sizeof(float),
+                                 cudaMemcpyHostToDevice, copy));
+        KM2_CUDA(cudaEventRecord(copied[b], copy));
+        return KMEANS2_OK;
+    }
+    ~ChunkStreamer()
+    {
+        if (copy) cudaStreamSynchronize(copy);
+        for (int b = 0; b < 2; ++b) {
+            if (copied[b]) cudaEventDestroy(copied[b]);
+            if (used[b]) cudaEventDestroy(used[b]);
+        }
+        if (copy) cudaStreamDestroy(copy);
+    }
+};
+
+// One pass over all chunks: before(c) gets each chunk once it is resident in
+// buffer c % 2 (on stream s), then the buffer is released for the next copy.
+template <class Fn>
+int stream_pass(ChunkStreamer& cs, cudaStream_t s, Fn&& on_chunk)
+{
+    KM2_TRY(cs.fetch(0));
+    for (long long c = 0; c < cs.nchunks; ++c) {
+        if (c + 1 < cs.nchunks) KM2_TRY(cs.fetch(c + 1));
+        const int b = (int)(c & 1);
+        KM2_CUDA(cudaStreamWaitEvent(s, cs.copied[b], 0));
+        KM2_TRY(on_chunk(c, cs.buf[b], cs.rows(c)));
+        KM2_CUDA(cudaEventRecord(cs.used[b], s));
+    }
+    return KMEANS2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double subset_fraction,
+                         uint64_t seed, double tol, int32_t max_iter, int64_t chunk_points,
+                         double* centers_out, int32_t* labels_out, kmeans2_result* res,
+                         const kmeans2_options* opt)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = g_launches;
+    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) || chunk_points < 1 ||
+        !(subset_fraction > 0.0 && subset_fraction <= 1.0) || !(tol >= 0.0) || max_iter < 1)
+        return KMEANS2_ERR_INVALID;
+    if (is_device_ptr(X)) {
+        set_last_error_text("kmeans2_fit_streamed: X must be host memory (use kmeans2_fit)");
+        return KMEANS2_ERR_INVALID;
+    }
+    Resolved r = resolve_options(opt);
+    const kmeans2_options& o = r.opt;
+    if (o.start_stage != 0 && o.start_stage != 1) return KMEANS2_ERR_INVALID;
+    if (o.start_stage == 1 && !o.init_centers) return KMEANS2_ERR_INVALID;
+    if (o.precision != KMEANS2_PRECISION_FP32 && o.precision != KMEANS2_PRECISION_AUTO) {
+        set_last_error_text("kmeans2_fit_streamed runs the CUDA-core FP32 form only");
+        return KMEANS2_ERR_UNSUPPORTED;
+    }
+    const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
+    cudaStream_t s = r.stream;
+    DeviceScratch ws(s);
+    const long long m = kmeans2_subset_size(n, k, subset_fraction);
+    const long long chunk = chunk_points < n ? chunk_points : n;
+
+    Workspace w;
+    w.form = KMEANS2_PRECISION_FP32;
+    KM2_TRY(alloc_workspace(w, ws, std::max(m, chunk), k, d, max_iter, s));
+    bool lab_dev = is_device_ptr(labels_out) && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
+    int* labels = lab_dev ? labels_out : nullptr;
+    if (!labels) KM2_TRY(ws.alloc((void**)&labels, sizeof(int) * (size_t)n, s));
+
+    kmeans2_result rr;
+    std::memset(&rr, 0, sizeof(rr));
+    rr.precision_used = KMEANS2_PRECISION_FP32;
+    rr.subset_size = m;
+    if (o.init_centers)
+        KM2_CUDA(cudaMemcpyAsync(w.c.c64, o.init_centers, sizeof(double) * (size_t)k * d,
+                                 is_device_ptr(o.init_centers) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice, s));
+    if (o.start_stage == 0) {
+        // fast stage: S_s gathered on the host, copied once, run resident
+        long long* subset = nullptr;
+        long long* pos = nullptr;
+        float* Xs = nullptr;
+        int* labels_s = nullptr;
+        KM2_TRY(ws.alloc((void**)&subset, sizeof(long long) * (size_t)m, s));
+        KM2_TRY(ws.alloc((void**)&pos, sizeof(long long) * (size_t)k, s));
+        KM2_TRY(ws.alloc((void**)&Xs, sizeof(float) * (size_t)m * d, s));
+        KM2_TRY(ws.alloc((void**)&labels_s, sizeof(int) * (size_t)m, s));
+        KM2_TRY(sample_device(n, k, m, seed, subset, pos, s, ws));
+        std::vector<long long> idx((size_t)m);
+        KM2_CUDA(cudaMemcpyAsync(idx.data(), subset, sizeof(long long) * (size_t)m,
+                                 cudaMemcpyDeviceToHost, s));
+        KM2_CUDA(cudaStreamSynchronize(s));
+        float* hs = nullptr;
+        KM2_CUDA(cudaMallocHost((void**)&hs, sizeof(float) * (size_t)m * d));
+        for (long long i = 0; i < m; ++i)
+            std::memcpy(hs + (size_t)i * d, X + (size_t)idx[(size_t)i] * d, sizeof(float) * (size_t)d);
+        cudaError_t e = cudaMemcpyAsync(Xs, hs, sizeof(float) * (size_t)m * d, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeHost(hs);
+        if (e != cudaSuccess) { set_last_error("kmeans2_fit_streamed: S_s copy", e); return KMEANS2_ERR_CUDA; }
+        KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
+        KM2_TRY(launch_maxabs(Xs, m, d, w.st, s, ws.sm_count));
+        if (!o.init_centers) KM2_TRY(launch_init_centers(Xs, d, pos, k, w.c.c64, s));
+        StageState fs;
+        KM2_TRY(run_stage(Xs, m, d, w, labels_s, tol_fast, max_iter, o.use_graph != 0, s, ws.sm_count,
+                          fs, o.traj_J_fast, o.traj_shift_fast, nullptr));
+        rr.iters_fast = fs.iter;
+        rr.converged_fast = fs.converged;
+        rr.shift_fast = fs.shift;
+        rr.rechecked_points += fs.rechecked_total;
+    }
+
+    // slow stage on S_n from the fast stage's final centers, X streamed per pass
+    ChunkStreamer cs;
+    KM2_TRY(cs.init(X, n, d, chunk, s, ws));
+    const size_t kd = (size_t)k * d;
+    KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
+    KM2_TRY(stream_pass(cs, s, [&](long long, const float* Xc, long long rows) {
+        return launch_maxabs(Xc, rows, d, w.st, s, ws.sm_count);
+    }));
+    KM2_CUDA(cudaMemsetAsync(w.acc.s_lo, 0, kd * 8, s));
+    KM2_CUDA(cudaMemsetAsync(w.acc.s_hi, 0, kd * 8, s));
+    KM2_CUDA(cudaMemsetAsync(w.acc.cnt, 0, (size_t)k * 8, s));
+    KM2_TRY(launch_center_prep(w.c, w.st, s));
+    KM2_TRY(launch_stage_init(w.st, d, tol, max_iter, s));
+    StageState ss;
+    std::memset(&ss, 0, sizeof(ss));
+    for (int it = 0; it < max_iter; ++it) {
+        KM2_TRY(stream_pass(cs, s, [&](long long c, const float* Xc, long long rows) {
+            int* lab = labels + c * chunk;
+            KM2_TRY(launch_assign(Xc, rows, d, w, lab, s, ws.sm_count));
+            KM2_TRY(launch_recheck(Xc, d, w.c, lab, w.list, w.st, w.acc, s, ws.sm_count));
+            return launch_recheck_reset(w.st, s);
+        }));
+        KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, 0ull, 0, s));
+        KM2_CUDA(cudaMemcpyAsync(&ss, w.st, sizeof(StageState), cudaMemcpyDeviceToHost, s));
+        KM2_CUDA(cudaStreamSynchronize(s));
+        if (ss.error) return map_stage_error(ss.error);
+        if (ss.done) break;
+    }
+    if (o.traj_J_slow && ss.iter > 0)
+        KM2_CUDA(cudaMemcpyAsync(o.traj_J_slow, w.traj_J, sizeof(double) * ss.iter,
+                                 cudaMemcpyDeviceToHost, s));
+    if (o.traj_shift_slow && ss.iter > 0)
+        KM2_CUDA(cudaMemcpyAsync(o.traj_shift_slow, w.traj_shift, sizeof(double) * ss.iter,
+                                 cudaMemcpyDeviceToHost, s));
+    rr.iters_slow = ss.iter;
+    rr.converged_slow = ss.converged;
+    rr.shift_slow = ss.shift;
+    rr.J = ss.J;
+    rr.empty_clusters = ss.empty;
+    rr.rechecked_points += ss.rechecked_total;
+    rr.distance_evals = (int64_t)rr.iters_fast * m * k + (int64_t)rr.iters_slow * n * k;
+    KM2_CUDA(cudaMemcpyAsync(centers_out, w.c.c64, sizeof(double) * kd,
                              is_device_ptr(centers_out) ? cudaMemcpyDeviceToDevice
                                                         : cudaMemcpyDeviceToHost, s));
     if (!lab_dev)

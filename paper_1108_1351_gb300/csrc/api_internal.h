@@ -87,6 +87,9 @@ int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* 
                     int use_cond, cudaStream_t s);
 int launch_recheck(const float* X, int d, const Centers& c, int* labels, const int* list,
                    StageState* st, const Accum& acc, cudaStream_t s, int sm_count);
+// Folds this pass's recheck count into the stage total and empties the list
+// (between the chunks of a streamed pass, whose indices are chunk-relative).
+int launch_recheck_reset(StageState* st, cudaStream_t s);
 
 // assign_tc32.cu: tensor-core (3xTF32) form for FP32 data, d in {4, 8, 16, 32}, k <= 256
 int assign_tc32_supported(int d, int k, const float* X);
@@ -110,5 +113,46 @@ int assign_fp32_supported(int d, int k);
 int launch_assign_fp32(const float* X, long long n, int d, const Centers& c, int* labels,
                        StageState* st, const Accum& acc, int* list, cudaStream_t s,
                        int sm_count);
+
+// ---------------------------------------------------------------- stage plumbing (api.cu)
+// Per-stage device state of one fit: centers, exact sums, loop state, near-tie list.
+struct Workspace {
+    int form = KMEANS2_PRECISION_FP32;   // distance-kernel form used by this call
+    Centers c{};
+    Accum acc{};
+    StageState* st = nullptr;
+    int* list = nullptr;
+    double* clus = nullptr;
+    double* traj_J = nullptr;      // max_iter
+    double* traj_shift = nullptr;  // max_iter
+    int max_iter = 0;
+    DeviceScratch* ws = nullptr;   // the call's scratch (per-stage buffers)
+    // BF16 form: the stage's points as BF16 tiles, their ||x||^2, the centers' chunks
+    unsigned char* xt = nullptr;
+    float* xn2 = nullptr;
+    unsigned char* cb = nullptr;
+};
+
+int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, int d,
+                    int max_iter, cudaStream_t s);
+// BF16 form: per-stage BF16 tiles and ||x||^2 of the stage's points (no-op otherwise).
+int prepare_stage_points(const float* X, long long n, int d, Workspace& w, DeviceScratch& ws,
+                         cudaStream_t s);
+// The fused distance kernel of w.form over n points.
+int launch_assign(const float* X, long long n, int d, Workspace& w, int* labels, cudaStream_t s,
+                  int sm_count);
+// Resolves a requested precision to the form this shape runs in.
+int choose_form(int requested, int d, int k, const float* X, int* form);
+int map_stage_error(int err);
+bool valid_shape(long long n, int d, int k);
+bool is_device_ptr(const void* p);
+// Device-resident, 16-byte aligned view of X (staged through scratch when needed).
+int device_view(const float* X, long long count, const float** out, DeviceScratch& ws,
+                cudaStream_t s);
+struct Resolved {
+    cudaStream_t stream;
+    kmeans2_options opt;
+};
+Resolved resolve_options(const kmeans2_options* opt);
 
 }  // namespace km2

@@ -150,16 +150,17 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
 }
 
 // Packed-key top-2 of 32 accumulator columns (center indices j0 .. j0 + 31)
-// folded into the running (B1, B2, BI) of a row.
+// folded into the running (B1, B2, BI) of a row.  Eight independent chains
+// of two column pairs each keep the dependent path short.
 __device__ __forceinline__ void top2_cols(const uint32_t* r, int j0, float& B1, float& B2, int& BI)
 {
-    float q1[4], q2[4];
+    float q1[8], q2[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
+    for (int q = 0; q < 8; ++q) { q1[q] = INFINITY; q2[q] = INFINITY; }
 #pragma unroll
-    for (int j = 0; j < 32; j += 8) {
+    for (int j = 0; j < 32; j += 16) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             const int jj = j + 2 * q;
             const float k0 = pack_key(__uint_as_float(r[jj]), (unsigned)jj);
             const float k1 = pack_key(__uint_as_float(r[jj + 1]), (unsigned)jj + 1u);
@@ -168,12 +169,17 @@ __device__ __forceinline__ void top2_cols(const uint32_t* r, int j0, float& B1, 
             q1[q] = fminf(q1[q], lo);
         }
     }
-    const float m01 = fmin3(q2[0], q2[1], fmaxf(q1[0], q1[1]));
-    const float l01 = fminf(q1[0], q1[1]);
-    const float m23 = fmin3(q2[2], q2[3], fmaxf(q1[2], q1[3]));
-    const float l23 = fminf(q1[2], q1[3]);
-    const float b2 = fmin3(m01, m23, fmaxf(l01, l23));
-    const float b1 = fminf(l01, l23);
+    // pairwise merge of the chains: (a1, a2) + (b1, b2) -> (min, second)
+#pragma unroll
+    for (int w = 4; w >= 1; w >>= 1) {
+#pragma unroll
+        for (int q = 0; q < w; ++q) {
+            const float m = fmin3(q2[q], q2[q + w], fmaxf(q1[q], q1[q + w]));
+            q1[q] = fminf(q1[q], q1[q + w]);
+            q2[q] = m;
+        }
+    }
+    const float b1 = q1[0], b2 = q2[0];
     if (b1 < B1) {
         B2 = fminf(B1, b2);
         B1 = b1;

@@ -300,6 +300,20 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     const long long i = base + (long long)p * kThreads + tid;
+                    if constexpr (DC % 4 == 0) {
+                        if ((d & 3) == 0) {
+                            // rows are 16-byte aligned: one 128-bit load per 4 coordinates
+#pragma unroll
+                            for (int q = 0; q < DC / 4; ++q) {
+                                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (i < npts && 4 * q < d)
+                                    v = __ldg(reinterpret_cast<const float4*>(X + i * d) + q);
+                                x[p][4 * q] = v.x; x[p][4 * q + 1] = v.y;
+                                x[p][4 * q + 2] = v.z; x[p][4 * q + 3] = v.w;
+                            }
+                            continue;
+                        }
+                    }
 #pragma unroll
                     for (int t = 0; t < DC; ++t) x[p][t] = (i < npts && t < d) ? __ldg(X + i * d + t) : 0.0f;
                 }
@@ -411,12 +425,13 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
 
 __global__ void __launch_bounds__(kThreads) batch_recheck_kernel(BatchInst* insts)
 {
+    __shared__ float cache[kThreads / 32][256];     // k <= 256 in the batched form
     BatchInst* I = insts + blockIdx.x;
     if (I->stage >= 2 || I->st.error) return;
     const float* X = I->stage == 0 ? I->Xs : I->X;
     int* labels = I->stage == 0 ? I->lab_fast : I->lab_slow;
     recheck_warps(X, I->d, I->c, labels, I->list, &I->st, I->acc, threadIdx.x >> 5,
-                  blockDim.x >> 5);
+                  blockDim.x >> 5, cache[threadIdx.x >> 5], 256);
 }
 
 __global__ void __launch_bounds__(kThreads) batch_finalize_kernel(BatchInst* insts, int* active)

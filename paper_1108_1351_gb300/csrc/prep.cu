@@ -109,15 +109,19 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Accum acc, Centers c, St
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(handle, st->done ? 0u : 1u);
 }
 
+constexpr int kRecheckThreads = 256;
+constexpr int kRecheckCache = 1024;     // pass-1 values kept per warp (k <= 1024)
+
 // Warps of the grid share the listed points (see recheck_warps).
-__global__ void recheck_kernel(const float* __restrict__ X, int d, Centers c,
+__global__ void __launch_bounds__(kRecheckThreads) recheck_kernel(const float* __restrict__ X, int d, Centers c,
                                int* __restrict__ labels, const int* __restrict__ list,
                                StageState* st, Accum acc)
 {
+    __shared__ float cache[kRecheckThreads / 32][kRecheckCache];
     if (st->error) return;
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    recheck_warps(X, d, c, labels, list, st, acc, gw, nw);
+    recheck_warps(X, d, c, labels, list, st, acc, gw, nw, cache[threadIdx.x >> 5], kRecheckCache);
 }
 
 }  // namespace
@@ -138,6 +142,20 @@ int launch_maxabs(const float* X, long long n, int d, StageState* st, cudaStream
     int vec4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
     ++g_launches;
     maxabs_kernel<<<grid_for(count / 4 + 1, 256, sm_count, 8), 256, 0, s>>>(X, count, vec4, st);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+__global__ void recheck_reset_kernel(StageState* st)
+{
+    st->rechecked_total += st->recheck_count;
+    st->recheck_count = 0;
+}
+
+int launch_recheck_reset(StageState* st, cudaStream_t s)
+{
+    ++g_launches;
+    recheck_reset_kernel<<<1, 1, 0, s>>>(st);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
@@ -193,7 +211,7 @@ int launch_recheck(const float* X, int d, const Centers& c, int* labels, const i
                    StageState* st, const Accum& acc, cudaStream_t s, int sm_count)
 {
     ++g_launches;
-    recheck_kernel<<<sm_count * 4, 256, 0, s>>>(X, d, c, labels, list, st, acc);
+    recheck_kernel<<<sm_count * 4, kRecheckThreads, 0, s>>>(X, d, c, labels, list, st, acc);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }

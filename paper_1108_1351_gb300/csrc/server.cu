@@ -37,6 +37,9 @@ enum class JobState { Queued, Running, Done };
 
 struct Ticket {
     kmeans2_job job{};
+    kmeans2_materialize_fn materialize = nullptr;   // lazy input (NULL: job.X given)
+    kmeans2_consume_fn consume = nullptr;
+    void* user = nullptr;
     uint64_t footprint = 0;
     double work = 0.0;          // n k d: the cost of one iteration
     JobState state = JobState::Queued;
@@ -71,6 +74,7 @@ struct kmeans2_server {
     std::condition_variable cv_work;   // workers: a job arrived, memory was freed, or stop
     std::condition_variable cv_done;   // waiters: a job finished
     std::deque<uint64_t> queue;        // waiting tickets, arrival order
+    std::deque<uint64_t> finished;     // finished tickets not yet handed out by wait_any
     std::unordered_map<uint64_t, km2::Ticket> tickets;
     uint64_t next_ticket = 1;
     uint64_t in_use = 0, peak = 0;
@@ -137,6 +141,9 @@ struct kmeans2_server {
         for (;;) {
             uint64_t id = 0;
             kmeans2_job job{};
+            kmeans2_materialize_fn materialize = nullptr;
+            kmeans2_consume_fn consume = nullptr;
+            void* user = nullptr;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] {
@@ -151,6 +158,7 @@ struct kmeans2_server {
                         t.status = KMEANS2_ERR_ADMISSION;
                         t.times.t_done = now();
                         ++failed;
+                        finished.push_back(id);
                         cv_done.notify_all();
                     }
                     return;
@@ -163,15 +171,21 @@ struct kmeans2_server {
                 ++running;
                 ++admitted;
                 job = t.job;
+                materialize = t.materialize;
+                consume = t.consume;
+                user = t.user;
             }
             kmeans2_options o = opt;
             o.stream = streams[slot];
             kmeans2_result r;
             std::memset(&r, 0, sizeof(r));
             const long long l0 = km2::g_launches;
-            const int rc = kmeans2_fit(job.X, job.n, job.d, job.k, job.subset_fraction, job.seed,
-                                       job.tol, job.max_iter, job.centers_out, job.labels_out,
-                                       &r, &o);
+            int rc = KMEANS2_OK;
+            if (materialize)
+                rc = run_lazy(job, materialize, consume, user, o, &r);
+            else
+                rc = kmeans2_fit(job.X, job.n, job.d, job.k, job.subset_fraction, job.seed,
+                                 job.tol, job.max_iter, job.centers_out, job.labels_out, &r, &o);
             const long long dl = km2::g_launches - l0;
             {
                 std::lock_guard<std::mutex> lk(mu);
@@ -184,10 +198,45 @@ struct kmeans2_server {
                 --running;
                 if (rc == KMEANS2_OK) ++completed; else ++failed;
                 launches += dl;
+                finished.push_back(id);
             }
             cv_work.notify_all();
             cv_done.notify_all();
         }
+    }
+
+    // A lazy job: device buffers for X, centers and labels on the worker's
+    // stream, the caller's materialize, the fit, the caller's consume.
+    int run_lazy(const kmeans2_job& job, kmeans2_materialize_fn materialize,
+                 kmeans2_consume_fn consume, void* user, const kmeans2_options& o,
+                 kmeans2_result* r)
+    {
+        cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+        float* X = nullptr;
+        double* cen = nullptr;
+        int* lab = nullptr;
+        int rc = KMEANS2_OK;
+        const size_t xb = (size_t)job.n * (size_t)job.d * 4;
+        if (cudaMallocAsync((void**)&X, xb, s) != cudaSuccess ||
+            cudaMallocAsync((void**)&cen, (size_t)job.k * job.d * 8, s) != cudaSuccess ||
+            cudaMallocAsync((void**)&lab, (size_t)job.n * 4, s) != cudaSuccess) {
+            cudaGetLastError();
+            km2::set_last_error_text("server: no device memory for a lazy job");
+            rc = KMEANS2_ERR_NOMEM;
+        }
+        if (rc == KMEANS2_OK && materialize(user, X, o.stream) != 0) {
+            km2::set_last_error_text("server: the job's materialize callback failed");
+            rc = KMEANS2_ERR_INVALID;
+        }
+        if (rc == KMEANS2_OK)
+            rc = kmeans2_fit(X, job.n, job.d, job.k, job.subset_fraction, job.seed, job.tol,
+                             job.max_iter, cen, lab, r, &o);
+        if (rc == KMEANS2_OK && consume) consume(user, cen, lab, o.stream);
+        if (lab) cudaFreeAsync(lab, s);
+        if (cen) cudaFreeAsync(cen, s);
+        if (X) cudaFreeAsync(X, s);
+        cudaStreamSynchronize(s);
+        return rc;
     }
 
     // Under mu: the status of a finished ticket (and release it), or PENDING.
@@ -243,18 +292,22 @@ kmeans2_server* kmeans2_server_create(uint64_t hbm_budget, int32_t max_slots,
     return s;
 }
 
-int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t* ticket)
+namespace {
+
+int submit_common(kmeans2_server* srv, const kmeans2_job* job, kmeans2_materialize_fn materialize,
+                  kmeans2_consume_fn consume, void* user, uint64_t* ticket)
 {
     if (!srv || !job || !ticket) return KMEANS2_ERR_INVALID;
     const kmeans2_job& J = *job;
-    if (!J.X || !J.centers_out || !J.labels_out || J.reserved != 0 || J.n < 1 || J.d < 1 ||
-        J.k < 1 || J.k > J.n || !(J.subset_fraction > 0.0 && J.subset_fraction <= 1.0) ||
+    const bool lazy = materialize != nullptr;
+    if ((!lazy && (!J.X || !J.centers_out || !J.labels_out)) || J.reserved != 0 || J.n < 1 ||
+        J.d < 1 || J.k < 1 || J.k > J.n || !(J.subset_fraction > 0.0 && J.subset_fraction <= 1.0) ||
         !(J.tol >= 0.0) || J.max_iter < 1) {
         km2::set_last_error_text("kmeans2_server_submit: job out of range");
         return KMEANS2_ERR_INVALID;
     }
-    const bool x_dev = km2::on_device(J.X, 16);
-    const bool lab_dev = km2::on_device(J.labels_out, 4);
+    const bool x_dev = lazy || km2::on_device(J.X, 16);
+    const bool lab_dev = lazy || km2::on_device(J.labels_out, 4);
     uint64_t fp = kmeans2_fit_footprint(J.n, J.d, J.k, J.subset_fraction, J.max_iter,
                                         srv->opt.precision, x_dev ? 0 : 1, lab_dev ? 0 : 1);
     if (fp == 0) {
@@ -262,6 +315,7 @@ int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t*
         return KMEANS2_ERR_INVALID;
     }
     if (x_dev) fp += (uint64_t)J.n * (uint64_t)J.d * 4;   // resident data counts against the budget
+    if (lazy) fp += (uint64_t)J.k * (uint64_t)J.d * 8 + (uint64_t)J.n * 4;   // server-owned outputs
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return KMEANS2_ERR_ADMISSION;
     if (fp > srv->budget) {
@@ -272,6 +326,9 @@ int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t*
     const uint64_t id = srv->next_ticket++;
     km2::Ticket& t = srv->tickets[id];
     t.job = J;
+    t.materialize = materialize;
+    t.consume = consume;
+    t.user = user;
     t.footprint = fp;
     t.work = (double)J.n * (double)J.k * (double)J.d;
     t.times.t_submit = srv->now();
@@ -280,6 +337,21 @@ int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t*
     *ticket = id;
     srv->cv_work.notify_all();
     return KMEANS2_OK;
+}
+
+}  // namespace
+
+int kmeans2_server_submit(kmeans2_server* srv, const kmeans2_job* job, uint64_t* ticket)
+{
+    return submit_common(srv, job, nullptr, nullptr, nullptr, ticket);
+}
+
+int kmeans2_server_submit_lazy(kmeans2_server* srv, const kmeans2_job* job,
+                               kmeans2_materialize_fn materialize, kmeans2_consume_fn consume,
+                               void* user, uint64_t* ticket)
+{
+    if (!materialize) return KMEANS2_ERR_INVALID;
+    return submit_common(srv, job, materialize, consume, user, ticket);
 }
 
 int kmeans2_server_poll(kmeans2_server* srv, uint64_t ticket, kmeans2_result* res,
@@ -327,6 +399,26 @@ int kmeans2_server_stats_get(kmeans2_server* srv, kmeans2_server_stats* out)
 }
 
 double kmeans2_server_now(kmeans2_server* srv) { return srv ? srv->now() : 0.0; }
+
+int kmeans2_server_wait_any(kmeans2_server* srv, double timeout_s, uint64_t* ticket)
+{
+    if (!srv || !ticket) return KMEANS2_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto ready = [&] {
+        // skip tickets already collected by poll / wait
+        while (!srv->finished.empty() && srv->tickets.find(srv->finished.front()) == srv->tickets.end())
+            srv->finished.pop_front();
+        return !srv->finished.empty();
+    };
+    if (timeout_s < 0)
+        srv->cv_done.wait(lk, ready);
+    else
+        srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+    if (!ready()) return KMEANS2_PENDING;
+    *ticket = srv->finished.front();
+    srv->finished.pop_front();
+    return KMEANS2_OK;
+}
 
 int kmeans2_server_set_policy(kmeans2_server* srv, int32_t policy, double aging_s)
 {

@@ -125,7 +125,13 @@ static __device__ void finalize_block(Accum acc, Centers c, StageState* st, doub
         double diff2 = 0.0, cS = 0.0, cc = 0.0, nn = 0.0;
         for (int t = lane; t < d; t += 32) {
             long long e = (long long)j * d + t;
-            double S = split_value(acc.s_lo[e], acc.s_hi[e], inv);
+            const unsigned long long lo = acc.s_lo[e], hi = acc.s_hi[e];
+            double S = split_value(lo, hi, inv);
+            // carry the low word's upper half into the high word (same value):
+            // every pass adds at most 2 n < 2^32 low parts below 2^32 each, so
+            // the low word cannot wrap however many delta passes follow
+            acc.s_lo[e] = lo & 0xffffffffull;
+            acc.s_hi[e] = hi + (lo >> 32);
             double cv = c.c64[e];
             double cn = N > 0 ? S / (double)N : cv;
             double df = cn - cv;
@@ -193,16 +199,38 @@ static __device__ void finalize_block(Accum acc, Centers c, StageState* st, doub
     __syncthreads();
 }
 
-// One warp per listed point.  Pass 1: FP32 D_j = ||c_j||^2 - 2 x.c_j for every
-// center on the CUDA cores (the FMA chain whose error tie_kappa bounds) and
-// their minimum b1.  Pass 2: every center with D_j <= b1 + tie_kappa (2 C2 + X2)
-// -- a set that provably holds the FP64 argmin -- is evaluated exactly in the
-// oracle's form (sum_t fma(x_t - c_t, x_t - c_t, acc), t ascending) and the
-// smallest wins, lowest index on ties.
+// FP32 D_j = ||c_j||^2 - 2 x.c_j of one point against centers j0 + 32 i
+// (i < 4): the CUDA-core FMA chain whose error tie_kappa bounds, t ascending.
+// c32t (dims x kpad, coalesced across the warp's lanes) holds the same FP32
+// values as the row-major copy; fmaf(-2 x_t, c_t, a) equals fmaf(x_t, -2 c_t, a)
+// (scaling by -2 is exact).  Padding centers read zeros.
+static __device__ __forceinline__ void recheck_d4(const float* __restrict__ x, int d,
+                                                  const Centers& c, int j0, float a[4])
+{
+    const int kpad = c.kpad;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = c.cnorm[j0 + 32 * i];
+    const float* ct = c.c32t + j0;
+    for (int t = 0; t < d; ++t) {
+        const float xm2 = -2.0f * __ldg(x + t);
+        const float* row = ct + (long long)t * kpad;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = fmaf(xm2, row[32 * i], a[i]);
+    }
+}
+
+// One warp per listed point.  Pass 1: FP32 D_j for every center on the CUDA
+// cores (recheck_d4) and their minimum b1.  Pass 2: every center with
+// D_j <= b1 + tie_kappa (2 C2 + X2) -- a set that provably holds the FP64
+// argmin -- is evaluated exactly in the oracle's form (sum_t fma(x_t - c_t,
+// x_t - c_t, acc), t ascending) and the smallest wins, lowest index on ties.
+// cache: per-warp shared memory of cache_cap floats for the pass-1 values
+// (pass 2 recomputes them when kpad > cache_cap or cache is null).
 // Warps w0, w0 + wstride, ... of the caller each take the listed points.
 static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers c,
                                      int* __restrict__ labels, const int* __restrict__ list,
-                                     StageState* st, Accum acc, long long gw, long long nw)
+                                     StageState* st, Accum acc, long long gw, long long nw,
+                                     float* cache, int cache_cap)
 {
     const int count = st->recheck_count;
     const int mode = st->mode;
@@ -210,6 +238,7 @@ static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers
     const float c2x2 = 2.0f * st->cmax2;
     const float kap = tie_kappa(d);
     const int k = c.k;
+    const bool cached = cache != nullptr && c.kpad <= cache_cap;
     int lane = threadIdx.x & 31;
     for (long long w = gw; w < count; w += nw) {
         int i = list[w];
@@ -218,28 +247,39 @@ static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers
         for (int t = lane; t < d; t += 32) { float v = __ldg(x + t); x2 = fmaf(v, v, x2); }
         for (int o = 16; o; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
         float b1 = INFINITY;
-        for (int j = lane; j < k; j += 32) {
-            const float* cj = c.c32 + (long long)j * d;
-            float a = c.cnorm[j];
-            for (int t = 0; t < d; ++t) a = fmaf(__ldg(x + t), -2.0f * cj[t], a);
-            b1 = fminf(b1, a);
+        for (int j0 = lane; j0 < k; j0 += 128) {
+            float a[4];
+            recheck_d4(x, d, c, j0, a);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j0 + 32 * q < k) b1 = fminf(b1, a[q]);
+                if (cached) cache[j0 + 32 * q] = a[q];
+            }
         }
         for (int o = 16; o; o >>= 1) b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
         const float lim = b1 + kap * (c2x2 + x2) * 1.0009765625f;
         double best = DBL_MAX;
         int bj = INT_MAX;
-        for (int j = lane; j < k; j += 32) {
-            const float* cj = c.c32 + (long long)j * d;
-            float a = c.cnorm[j];
-            for (int t = 0; t < d; ++t) a = fmaf(__ldg(x + t), -2.0f * cj[t], a);
-            if (a <= lim) {
-                const double* cj64 = c.c64 + (long long)j * d;
-                double a2 = 0.0;
-                for (int t = 0; t < d; ++t) {
-                    double e = (double)__ldg(x + t) - cj64[t];
-                    a2 = fma(e, e, a2);
+        for (int j0 = lane; j0 < k; j0 += 128) {
+            float a[4];
+            if (cached) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a[q] = cache[j0 + 32 * q];
+            } else {
+                recheck_d4(x, d, c, j0, a);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + 32 * q;
+                if (j < k && a[q] <= lim) {
+                    const double* cj64 = c.c64 + (long long)j * d;
+                    double a2 = 0.0;
+                    for (int t = 0; t < d; ++t) {
+                        double e = (double)__ldg(x + t) - cj64[t];
+                        a2 = fma(e, e, a2);
+                    }
+                    if (a2 < best || (a2 == best && j < bj)) { best = a2; bj = j; }
                 }
-                if (a2 < best) { best = a2; bj = j; }
             }
         }
         for (int o = 16; o; o >>= 1) {
@@ -248,7 +288,7 @@ static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers
             if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
         }
         int old = (mode == kModeDelta) ? labels[i] : -1;
-        __syncwarp();   // every lane has read the old label before lane 0 rewrites it
+        __syncwarp();   // every lane has read the old label (and its cache) before reuse
         if (bj != old) {
             for (int t = lane; t < d; t += 32) {
                 long long v = to_fixed(__ldg(x + t), scaleF);

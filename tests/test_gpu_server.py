@@ -200,3 +200,56 @@ def test_server_shortest_policy_admission_order(aging, order):
     assert got == order
     for name, (n, d, k, s) in jobs.items():
         _same(res[name].result, km.fit(Xs[name], k, 0.1, s, 1e-6, 50))
+
+
+def test_server_lazy_jobs_equal_eager_fits():
+    # points produced at admission by a callback, outputs handed to a consumer:
+    # same results as eager fits of the same data; a failing producer fails
+    # only its own job
+    specs = {"a": (40_000, 16, 30, 0.1, 1e-6, 50, 81), "b": (25_000, 64, 50, 0.1, 1e-6, 40, 82),
+             "c": (60_000, 4, 12, 0.2, 1e-6, 60, 83)}
+    outs = {}
+
+    def make_for(n, d, k, s):
+        def make(X):
+            X.copy_(_data(n, d, k, s))
+        return make
+
+    def consume_for(name):
+        def consume(C, L):
+            outs[name] = (C.clone(), L.clone())
+        return consume
+
+    def broken(X):
+        raise RuntimeError("no data")
+
+    with km.Server(max_slots=3, policy="shortest", aging_s=5.0) as srv:
+        tickets = {name: srv.submit_lazy(n, d, k, f, s, tol, it, make_for(n, d, k, s),
+                                         consume_for(name))
+                   for name, (n, d, k, f, tol, it, s) in specs.items()}
+        tb = srv.submit_lazy(1000, 8, 4, 0.5, 1, 1e-6, 10, broken)
+        res = {name: srv.wait(t) for name, t in tickets.items()}
+        fb = srv.wait(tb)
+        st = srv.stats()
+    assert fb.status == -1 and st["failed"] == 1
+    for name, (n, d, k, f, tol, it, s) in specs.items():
+        assert res[name].status == 0
+        a = km.fit(_data(n, d, k, s), k, f, s, tol, it)
+        C, L = outs[name]
+        assert torch.equal(C, a.centers) and torch.equal(L, a.labels)
+        assert res[name].result.J == a.J
+        assert (res[name].result.iters_fast, res[name].result.iters_slow) == (a.iters_fast, a.iters_slow)
+
+
+def test_server_wait_any_returns_each_finished_job_once():
+    specs = [(20_000, 4, 8, 0.1, 1e-6, 40, 91 + j) for j in range(6)]
+    Xs = [_data(n, d, k, s) for (n, d, k, f, tol, it, s) in specs]
+    with km.Server(max_slots=3) as srv:
+        tickets = {srv.submit(X, k, f, s, tol, it) for X, (n, d, k, f, tol, it, s) in zip(Xs, specs)}
+        seen = set()
+        for _ in range(len(specs)):
+            sv = srv.wait_any(60.0)
+            assert sv is not None and sv.status == 0
+            seen.add(sv.ticket)
+        assert seen == tickets
+        assert srv.wait_any(0.01) is None
