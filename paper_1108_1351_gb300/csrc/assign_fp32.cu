@@ -19,10 +19,12 @@
 // Two forms:
 //  assign_small<D>     d <= 16.  Each thread owns P points in registers and
 //                      prefetches its next tile with cp.async; the k centers
-//                      (pre-scaled by -2, with ||c||^2) sit in shared memory
-//                      and are read as broadcast 128-bit loads, two at a time;
-//                      the top-2 runs on packed keys (index in the low mantissa
-//                      bits).  Per-CTA int64 partial sums in shared memory,
+//                      (pre-scaled by -2, with ||c||^2) sit in shared memory,
+//                      interleaved in pairs and read as broadcast 128-bit
+//                      loads; one packed FP32x2 FMA (fma.rn.f32x2, each half
+//                      rounded like its own fmaf) advances both centers of a
+//                      pair, halving the FMA instructions; the top-2 runs on
+//                      packed keys (index in the low mantissa bits).  Per-CTA int64 partial sums in shared memory,
 //                      flushed to the global split accumulators every 2^16 points.
 //  assign_large        any d.  128 points x 128 centers register-blocked tiles
 //                      (8 x 8 per thread) over 8-dimension slices staged in
@@ -149,7 +151,9 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
     const int tid = threadIdx.x;
 
     for (int e = tid; e < kc * DS; e += kThreads) {
-        int j = e / DS, t = e - j * DS;
+        // center pairs interleaved: (pair, t, member)
+        const int pr = e / (2 * DS), r = e - pr * 2 * DS;
+        const int t = r >> 1, j = 2 * pr + (r & 1);
         sc[e] = (j < k && t < D) ? -2.0f * c.c32[(long long)j * D + t] : 0.0f;
     }
     for (int j = tid; j < kc; j += kThreads)
@@ -221,27 +225,26 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
             for (int p = 0; p < P; ++p) { b1[p] = INFINITY; b2[p] = INFINITY; }
             const float* cbase = sc + (size_t)(ch << 5) * DS;
             const float* sbase = ss + (ch << 5);
+            // one packed FMA evaluates dimension t for both centers of a
+            // pair (each half rounds like its own fmaf)
 #pragma unroll 4
             for (unsigned jj = 0; jj < 32; jj += 2) {
-                float c0[DS], c1[DS];
-                const float4* q0 = reinterpret_cast<const float4*>(cbase + jj * DS);
-                const float4* q1 = reinterpret_cast<const float4*>(cbase + (jj + 1) * DS);
+                float2 cp[DS];
+                const float4* q = reinterpret_cast<const float4*>(cbase + jj * DS);
 #pragma unroll
-                for (int q = 0; q < DS / 4; ++q) {
-                    float4 v0 = q0[q], v1 = q1[q];
-                    c0[4 * q] = v0.x; c0[4 * q + 1] = v0.y; c0[4 * q + 2] = v0.z; c0[4 * q + 3] = v0.w;
-                    c1[4 * q] = v1.x; c1[4 * q + 1] = v1.y; c1[4 * q + 2] = v1.z; c1[4 * q + 3] = v1.w;
+                for (int h = 0; h < DS / 2; ++h) {
+                    const float4 v = q[h];
+                    cp[2 * h] = make_float2(v.x, v.y);
+                    cp[2 * h + 1] = make_float2(v.z, v.w);
                 }
                 const float2 st01 = *reinterpret_cast<const float2*>(sbase + jj);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    float d0 = st01.x, d1 = st01.y;
+                    float2 dd = st01;
 #pragma unroll
-                    for (int t = 0; t < D; ++t) {
-                        d0 = fmaf(x[p][t], c0[t], d0);
-                        d1 = fmaf(x[p][t], c1[t], d1);
-                    }
-                    const float k0 = pack_key(d0, jj), k1 = pack_key(d1, jj | 1u);
+                    for (int t = 0; t < D; ++t)
+                        dd = __ffma2_rn(make_float2(x[p][t], x[p][t]), cp[t], dd);
+                    const float k0 = pack_key(dd.x, jj), k1 = pack_key(dd.y, jj | 1u);
                     const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
                     b2[p] = fmin3(b2[p], hi, fmaxf(b1[p], lo));
                     b1[p] = fminf(b1[p], lo);
@@ -515,9 +518,10 @@ int launch_small(const float* X, long long n, const Centers& c, int* labels, Sta
     const bool with_acc = small_smem<D>(c.k, true) <= (size_t)kSmallSmemCap;
     const size_t sm = small_smem<D>(c.k, with_acc);
     if (sm > (size_t)kSmallSmemCap) return KMEANS2_ERR_UNSUPPORTED;
-    KM2_TRY(set_max_dynamic_smem((const void*)assign_small<D>, kSmallSmemCap));
+    const void* kfn = (const void*)assign_small<D>;
+    KM2_TRY(set_max_dynamic_smem(kfn, kSmallSmemCap));
     int per_sm = 0;
-    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assign_small<D>, kThreads, sm));
+    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, sm));
     if (per_sm < 1) return KMEANS2_ERR_UNSUPPORTED;
     const long long tiles = (n + SmallCfg<D>::TILE - 1) / SmallCfg<D>::TILE;
     long long grid = (long long)sm_count * per_sm;

@@ -646,14 +646,29 @@ int launch_tc_t(const float* X, long long n, const Centers& c, int* labels, Stag
     return KMEANS2_OK;
 }
 
-// Tiles per unit: four while a unit's accumulator stays within 128 columns.
+// True if some ring depth fits T tiles per unit into the shared-memory budget.
+bool tc_layout_fits(int D, int T, int npad, int k)
+{
+    for (int sacc = 1; sacc >= 0; --sacc)
+        for (int rs = kMaxRS; rs >= 3; --rs)
+            for (int sa = kMaxSA; sa >= 2; --sa)
+                if (sa <= rs - 1 && tc_layout(D, T, npad, k, rs, sa, sacc).total <=
+                                        (uint32_t)kSmemBudget)
+                    return true;
+    return false;
+}
+
+// Tiles per unit: four while a unit's accumulator stays within 128 columns,
+// fewer when that many tiles do not fit into shared memory (wide D).
 template <int D>
 int launch_tc(const float* X, long long n, const Centers& c, int* labels, StageState* st,
               const Accum& acc, int* list, cudaStream_t s, int sm_count)
 {
     const int npad = (c.k + 31) / 32 * 32;
-    if (npad <= 32) return launch_tc_t<D, 4>(X, n, c, labels, st, acc, list, s, sm_count, npad);
-    if (npad <= 64) return launch_tc_t<D, 2>(X, n, c, labels, st, acc, list, s, sm_count, npad);
+    int T = npad <= 32 ? 4 : (npad <= 64 ? 2 : 1);
+    while (T > 1 && !tc_layout_fits(D, T, npad, c.k)) T >>= 1;
+    if (T == 4) return launch_tc_t<D, 4>(X, n, c, labels, st, acc, list, s, sm_count, npad);
+    if (T == 2) return launch_tc_t<D, 2>(X, n, c, labels, st, acc, list, s, sm_count, npad);
     return launch_tc_t<D, 1>(X, n, c, labels, st, acc, list, s, sm_count, npad);
 }
 
@@ -663,7 +678,8 @@ int assign_tc32_supported(int d, int k, const float* X)
 {
     if (k < 1 || k > 256) return 0;
     if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return 0;
-    return d == 4 || d == 8 || d == 16 || d == 32;
+    if (!(d == 4 || d == 8 || d == 16 || d == 32)) return 0;
+    return tc_layout_fits(d, 1, (k + 31) / 32 * 32, k) ? 1 : 0;
 }
 
 int launch_assign_tc32(const float* X, long long n, int d, const Centers& c, int* labels,
