@@ -182,11 +182,15 @@ KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, dou
  * the copies asynchronous; pageable memory works, synchronously.
  *
  *  X             n*d FP32 points in host memory.
- *  chunk_points  rows per chunk, >= 1.
+ *  chunk_points  rows per chunk, >= 1; or 0 (automatic): if X is page-locked
+ *                and 16-byte aligned, the kernels read it in place over the
+ *                CPU-GPU link (NVLink-C2C on GB300) with no staging copies and
+ *                no chunk loop (the same results); otherwise chunks of 2^26
+ *                rows.
  *  opt           precision must be FP32 or AUTO (the CUDA-core form);
  *                use_graph is ignored (the slow stage is host-driven).
  * Errors as kmeans2_fit; KMEANS2_ERR_INVALID if X is device memory or
- * chunk_points < 1, KMEANS2_ERR_UNSUPPORTED for a tensor-core precision.
+ * chunk_points < 0, KMEANS2_ERR_UNSUPPORTED for a tensor-core precision.
  */
 KMEANS2_API int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k,
                                      double subset_fraction, uint64_t seed, double tol,
@@ -548,6 +552,13 @@ KMEANS2_API const char* kmeans2_last_error(void);
 
 /* Library version, (major << 16) | minor. */
 KMEANS2_API int32_t kmeans2_version(void);
+
+/* Device scratch of every call comes from a library-owned stream-ordered pool
+ * per GPU that keeps freed memory mapped, so repeated calls (a serving loop,
+ * the stage loops of many fits) reuse it without mapping it again.  This call
+ * waits for the current device and returns the pool's unused memory to the
+ * driver.  Returns KMEANS2_OK or KMEANS2_ERR_CUDA. */
+KMEANS2_API int kmeans2_release_memory(void);
 
 #ifdef __cplusplus
 }

@@ -7,10 +7,10 @@ binds it (``binding``) and provides seeded synthetic inputs (``synth``).
 """
 from .binding import (FitResult, KMeans2Error, LIB_PATH, Profile, Served, Server, Shard,
                       declared_symbols, fit, fit_batched, fit_data_parallel, fit_sharded,
-                      fit_streamed, footprint, load, sample, step, step_noalloc, strerror,
-                      subset_size, version)
+                      fit_streamed, footprint, load, release_memory, sample, step, step_noalloc,
+                      strerror, subset_size, version)
 
 __all__ = ["FitResult", "KMeans2Error", "LIB_PATH", "Profile", "Served", "Server", "Shard",
            "declared_symbols", "fit", "fit_batched", "fit_data_parallel", "fit_sharded",
-           "fit_streamed", "footprint", "load", "sample", "step", "step_noalloc", "strerror",
-           "subset_size", "version"]
+           "fit_streamed", "footprint", "load", "release_memory", "sample", "step",
+           "step_noalloc", "strerror", "subset_size", "version"]

@@ -213,6 +213,8 @@ def load():
         lib.kmeans2_strerror.argtypes = [ctypes.c_int]
         lib.kmeans2_last_error.restype = ctypes.c_char_p
         lib.kmeans2_last_error.argtypes = []
+        lib.kmeans2_release_memory.restype = ctypes.c_int
+        lib.kmeans2_release_memory.argtypes = []
         lib.kmeans2_version.restype = i32
         lib.kmeans2_version.argtypes = []
         _lib = lib
@@ -362,11 +364,13 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
 def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                  chunk_points: int, *, tol_fast: float = 0.0, init_centers=None,
                  start_stage: int = 0, stream=None, centers_out=None,
-                 labels_out=None) -> "FitResult":
-    """Two-stage k-means on host-resident X streamed through the GPU in chunks
-    of chunk_points rows (kmeans2_fit_streamed); same results as fit().
-    X: a numpy array or a CPU tensor (pinned for asynchronous copies).
-    Outputs are host arrays unless given."""
+                 labels_out=None, profile: "Profile | None" = None) -> "FitResult":
+    """Two-stage k-means on host-resident X (kmeans2_fit_streamed); same
+    results as fit().  chunk_points > 0: X is staged through the GPU in chunks
+    of that many rows; 0: page-locked X is read in place by the kernels over
+    the CPU-GPU link (pageable X falls back to 2^26-row chunks).
+    X: a numpy array or a CPU tensor (pinned for in-place reads and
+    asynchronous copies).  Outputs are host arrays unless given."""
     lib = load()
     if _is_torch(X) and X.is_cuda:
         raise TypeError("fit_streamed takes host-resident X")
@@ -381,6 +385,7 @@ def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_i
     opt.tol_fast = tol_fast
     opt.init_centers = _ptr(C0) if C0 is not None else None
     opt.start_stage = start_stage
+    opt.profile = ctypes.addressof(profile) if profile is not None else None
     dev = torch.device("cuda", torch.cuda.current_device())
     opt.stream = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
     res = Result()
@@ -520,6 +525,14 @@ def fit_data_parallel(X_local, row0: int, n_total: int, k: int, subset_fraction:
         return sh.result()
     finally:
         sh.close()
+
+
+def release_memory() -> None:
+    """Return the library's unused device scratch to the driver
+    (kmeans2_release_memory; waits for the current device)."""
+    rc = load().kmeans2_release_memory()
+    if rc != 0:
+        raise KMeans2Error(rc, "kmeans2_release_memory")
 
 
 def _fit_result(r, cen, lab, traj=None) -> FitResult:

@@ -67,6 +67,45 @@ cudaStream_t private_stream(int device)
     return streams[device];
 }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}
+
+// The library's stream-ordered pool on `device`: it keeps freed memory mapped
+// (no release threshold), so repeated calls reuse their scratch instead of
+// mapping it again each time (kmeans2_release_memory trims it).
+cudaMemPool_t library_pool(int device)
+{
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[device]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[device] = pool;
+    }
+    return g_pools[device];
+}
+
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = library_pool(dev);
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
 DeviceScratch::DeviceScratch(cudaStream_t s) : stream(s)
 {
     cudaGetDevice(&device);
@@ -100,9 +139,10 @@ int DeviceScratch::alloc(void** p, size_t bytes, cudaStream_t s)
         arena_used = off + bytes;
         return KMEANS2_OK;
     }
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = library_pool(device);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
-        set_last_error("cudaMallocAsync", e);
+        set_last_error("cudaMallocFromPoolAsync", e);
         cudaGetLastError();
         *p = nullptr;
         return KMEANS2_ERR_NOMEM;
@@ -551,6 +591,17 @@ uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fr
 
 int32_t kmeans2_version(void) { return (1 << 16) | 0; }
 
+int kmeans2_release_memory(void)
+{
+    int dev = 0;
+    KM2_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = library_pool(dev);
+    if (!pool) return KMEANS2_ERR_CUDA;
+    KM2_CUDA(cudaDeviceSynchronize());
+    KM2_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return KMEANS2_OK;
+}
+
 int kmeans2_sample(int64_t n, int32_t k, double f, uint64_t seed, int64_t* subset_out,
                    int64_t* init_pos_out, void* stream)
 {
@@ -664,27 +715,22 @@ int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
     return KMEANS2_OK;
 }
 
-int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_fraction,
-                uint64_t seed, double tol, int32_t max_iter, double* centers_out,
-                int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt)
+}  // extern "C"
+
+namespace {
+
+// The two-stage fit on Xd, n*d FP32 points the device can read (its own
+// memory or page-locked host memory), 16-byte aligned; arguments checked.
+int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fraction,
+           uint64_t seed, double tol, int32_t max_iter, double* centers_out, int32_t* labels_out,
+           kmeans2_result* res, const Resolved& r, DeviceScratch& ws,
+           std::chrono::steady_clock::time_point t0, long long launches0)
 {
-    auto t0 = std::chrono::steady_clock::now();
-    const long long launches0 = g_launches;
-    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) ||
-        !(subset_fraction > 0.0 && subset_fraction <= 1.0) || !(tol >= 0.0) || max_iter < 1)
-        return KMEANS2_ERR_INVALID;
-    Resolved r = resolve_options(opt);
     const kmeans2_options& o = r.opt;
-    if (o.start_stage != 0 && o.start_stage != 1) return KMEANS2_ERR_INVALID;
-    if (o.start_stage == 1 && !o.init_centers) return KMEANS2_ERR_INVALID;
     const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
     const bool use_graph = o.use_graph != 0;
     cudaStream_t s = r.stream;
-    DeviceScratch ws(s);
-
     const long long m = kmeans2_subset_size(n, k, subset_fraction);
-    const float* Xd = nullptr;
-    KM2_TRY(device_view(X, (long long)n * d, &Xd, ws, s));
     Workspace w;
     KM2_TRY(choose_form(o.precision, d, k, Xd, &w.form));
     KM2_TRY(alloc_workspace(w, ws, n, k, d, max_iter, s));
@@ -753,9 +799,34 @@ int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_f
     return KMEANS2_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, double subset_fraction,
+                uint64_t seed, double tol, int32_t max_iter, double* centers_out,
+                int32_t* labels_out, kmeans2_result* res, const kmeans2_options* opt)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = g_launches;
+    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) ||
+        !(subset_fraction > 0.0 && subset_fraction <= 1.0) || !(tol >= 0.0) || max_iter < 1)
+        return KMEANS2_ERR_INVALID;
+    Resolved r = resolve_options(opt);
+    if (r.opt.start_stage != 0 && r.opt.start_stage != 1) return KMEANS2_ERR_INVALID;
+    if (r.opt.start_stage == 1 && !r.opt.init_centers) return KMEANS2_ERR_INVALID;
+    DeviceScratch ws(r.stream);
+    const float* Xd = nullptr;
+    KM2_TRY(device_view(X, (long long)n * d, &Xd, ws, r.stream));
+    return fit_on(Xd, n, d, k, subset_fraction, seed, tol, max_iter, centers_out, labels_out, res,
+                  r, ws, t0, launches0);
+}
+
 }  // extern "C"
 
 namespace {
+
+constexpr long long kDefaultChunkPoints = 1ll << 26;
 
 // Host-resident X streamed through two device chunk buffers: copies run on a
 // stream of their own and overlap the kernels of the previous chunk.
@@ -835,7 +906,7 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
 {
     auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = g_launches;
-    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) || chunk_points < 1 ||
+    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) || chunk_points < 0 ||
         !(subset_fraction > 0.0 && subset_fraction <= 1.0) || !(tol >= 0.0) || max_iter < 1)
         return KMEANS2_ERR_INVALID;
     if (is_device_ptr(X)) {
@@ -849,6 +920,23 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
     if (o.precision != KMEANS2_PRECISION_FP32 && o.precision != KMEANS2_PRECISION_AUTO) {
         set_last_error_text("kmeans2_fit_streamed runs the CUDA-core FP32 form only");
         return KMEANS2_ERR_UNSUPPORTED;
+    }
+    if (chunk_points == 0) {
+        // page-locked X: the kernels read it where it is, over the CPU-GPU
+        // link, at the link's rate and with no staging copies
+        cudaPointerAttributes pa;
+        const void* dp = nullptr;
+        if (cudaPointerGetAttributes(&pa, X) == cudaSuccess && pa.type == cudaMemoryTypeHost)
+            dp = pa.devicePointer;
+        cudaGetLastError();
+        if (dp && (reinterpret_cast<uintptr_t>(dp) & 15) == 0) {
+            Resolved rd = r;
+            rd.opt.precision = KMEANS2_PRECISION_FP32;
+            DeviceScratch ws(rd.stream);
+            return fit_on(static_cast<const float*>(dp), n, d, k, subset_fraction, seed, tol,
+                          max_iter, centers_out, labels_out, res, rd, ws, t0, launches0);
+        }
+        chunk_points = kDefaultChunkPoints;   // pageable memory: staged chunks
     }
     const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
     cudaStream_t s = r.stream;

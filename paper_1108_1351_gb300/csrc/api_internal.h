@@ -39,6 +39,12 @@ void set_last_error_text(const char* text);
 // unlike the legacy default stream).
 cudaStream_t private_stream(int device);
 
+// The library's stream-ordered memory pool on `device` (freed memory stays
+// mapped for reuse; kmeans2_release_memory trims it); null if it cannot be made.
+cudaMemPool_t library_pool(int device);
+// cudaMallocAsync from the library pool of the current device.
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s);
+
 // Stream-ordered scratch: every allocation is released (cudaFreeAsync on the
 // same stream) when the object goes out of scope.
 struct DeviceScratch {

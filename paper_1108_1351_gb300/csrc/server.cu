@@ -217,9 +217,9 @@ struct kmeans2_server {
         int* lab = nullptr;
         int rc = KMEANS2_OK;
         const size_t xb = (size_t)job.n * (size_t)job.d * 4;
-        if (cudaMallocAsync((void**)&X, xb, s) != cudaSuccess ||
-            cudaMallocAsync((void**)&cen, (size_t)job.k * job.d * 8, s) != cudaSuccess ||
-            cudaMallocAsync((void**)&lab, (size_t)job.n * 4, s) != cudaSuccess) {
+        if (km2::pool_malloc_async((void**)&X, xb, s) != cudaSuccess ||
+            km2::pool_malloc_async((void**)&cen, (size_t)job.k * job.d * 8, s) != cudaSuccess ||
+            km2::pool_malloc_async((void**)&lab, (size_t)job.n * 4, s) != cudaSuccess) {
             cudaGetLastError();
             km2::set_last_error_text("server: no device memory for a lazy job");
             rc = KMEANS2_ERR_NOMEM;
