@@ -182,15 +182,15 @@ KMEANS2_API int kmeans2_fit(const float* X, int64_t n, int32_t d, int32_t k, dou
  * the copies asynchronous; pageable memory works, synchronously.
  *
  *  X             n*d FP32 points in host memory.
- *  chunk_points  rows per chunk, >= 1; or 0 (automatic): if X is page-locked
- *                and 16-byte aligned, the kernels read it in place over the
- *                CPU-GPU link (NVLink-C2C on GB300) with no staging copies and
- *                no chunk loop (the same results); otherwise chunks of 2^26
- *                rows.
+ *  chunk_points  rows per chunk; 0 = 2^26 rows; < 0 = in place: if X is
+ *                page-locked and 16-byte aligned the kernels read it where it
+ *                is, over the CPU-GPU link (NVLink-C2C on GB300), with no
+ *                staging copies and no chunk loop (same results; on GB300 the
+ *                staged chunks measured faster), otherwise 2^26-row chunks.
  *  opt           precision must be FP32 or AUTO (the CUDA-core form);
  *                use_graph is ignored (the slow stage is host-driven).
- * Errors as kmeans2_fit; KMEANS2_ERR_INVALID if X is device memory or
- * chunk_points < 0, KMEANS2_ERR_UNSUPPORTED for a tensor-core precision.
+ * Errors as kmeans2_fit; KMEANS2_ERR_INVALID if X is device memory,
+ * KMEANS2_ERR_UNSUPPORTED for a tensor-core precision.
  */
 KMEANS2_API int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k,
                                      double subset_fraction, uint64_t seed, double tol,

@@ -367,8 +367,8 @@ def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_i
                  labels_out=None, profile: "Profile | None" = None) -> "FitResult":
     """Two-stage k-means on host-resident X (kmeans2_fit_streamed); same
     results as fit().  chunk_points > 0: X is staged through the GPU in chunks
-    of that many rows; 0: page-locked X is read in place by the kernels over
-    the CPU-GPU link (pageable X falls back to 2^26-row chunks).
+    of that many rows (0: 2^26 rows); < 0: page-locked X is read in place by
+    the kernels over the CPU-GPU link (pageable X falls back to chunks).
     X: a numpy array or a CPU tensor (pinned for in-place reads and
     asynchronous copies).  Outputs are host arrays unless given."""
     lib = load()

@@ -906,7 +906,7 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
 {
     auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = g_launches;
-    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) || chunk_points < 0 ||
+    if (!X || !centers_out || !labels_out || !valid_shape(n, d, k) ||
         !(subset_fraction > 0.0 && subset_fraction <= 1.0) || !(tol >= 0.0) || max_iter < 1)
         return KMEANS2_ERR_INVALID;
     if (is_device_ptr(X)) {
@@ -921,9 +921,9 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
         set_last_error_text("kmeans2_fit_streamed runs the CUDA-core FP32 form only");
         return KMEANS2_ERR_UNSUPPORTED;
     }
-    if (chunk_points == 0) {
+    if (chunk_points < 0) {
         // page-locked X: the kernels read it where it is, over the CPU-GPU
-        // link, at the link's rate and with no staging copies
+        // link, with no staging copies
         cudaPointerAttributes pa;
         const void* dp = nullptr;
         if (cudaPointerGetAttributes(&pa, X) == cudaSuccess && pa.type == cudaMemoryTypeHost)
@@ -936,8 +936,9 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
             return fit_on(static_cast<const float*>(dp), n, d, k, subset_fraction, seed, tol,
                           max_iter, centers_out, labels_out, res, rd, ws, t0, launches0);
         }
-        chunk_points = kDefaultChunkPoints;   // pageable memory: staged chunks
+        chunk_points = 0;                     // pageable memory: staged chunks
     }
+    if (chunk_points == 0) chunk_points = kDefaultChunkPoints;
     const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
     cudaStream_t s = r.stream;
     DeviceScratch ws(s);

@@ -54,23 +54,25 @@ def test_streamed_pinned_host_memory_and_oracle():
     assert_J_close(b.J, o["J"], Xh)
 
 
-def test_streamed_rejects_device_x_and_tensor_core_forms():
+def test_streamed_rejects_device_x_and_invalid_shapes():
     X = torch.zeros((100, 8), device=DEV)
     with pytest.raises(TypeError):
         km.fit_streamed(X, 4, 0.5, 1, 1e-6, 5, 10)
     with pytest.raises(km.KMeans2Error):
-        km.fit_streamed(np.zeros((100, 8), np.float32), 4, 0.5, 1, 1e-6, 5, -1)
+        km.fit_streamed(np.zeros((100, 8), np.float32), 200, 0.5, 1, 1e-6, 5, 10)   # k > n
 
 
 @pytest.mark.parametrize("pinned", [True, False])
 def test_streamed_in_place_equals_resident(pinned):
-    # chunk_points = 0: page-locked X is read by the kernels where it is;
-    # pageable X falls back to staged chunks.  Both equal the resident fit.
+    # chunk_points < 0: page-locked X is read by the kernels where it is;
+    # pageable X falls back to staged chunks (as for 0).  All equal the
+    # resident fit.
     n, d, k = 1_000_003, 8, 32
     Xt = synth.aniso_gaussian_noise(n, d, k, 12, device="cpu", chunk=1 << 20)
     if pinned:
         Xt = Xt.pin_memory()
     a = km.fit(Xt.numpy(), k, 0.02, 4, 1e-6, 40, precision="fp32")
-    b = km.fit_streamed(Xt, k, 0.02, 4, 1e-6, 40, 0)
+    b = km.fit_streamed(Xt, k, 0.02, 4, 1e-6, 40, -1)
     _same(a, b)
     assert b.precision_used == "fp32"
+    _same(a, km.fit_streamed(Xt, k, 0.02, 4, 1e-6, 40, 0))
