@@ -80,7 +80,8 @@ extern "C" {
                                          split in two BF16 parts, three products, FP32
                                          accumulation); d a multiple of 16 in [16, 128] */
 #define KMEANS2_PRECISION_AUTO 2      /* fastest form measured for the shape (default):
-                                         BF16 for d in {64, 80, ..., 128}, else FP32 */
+                                         BF16 for d in {64, 80, ..., 128} and k >= 512,
+                                         else FP32 */
 #define KMEANS2_PRECISION_TF32X3 3    /* cross term on the tensor cores as three TF32
                                          products of the exact hi/lo split of the FP32
                                          operands; d in {4, 8, 16, 32}, k <= 256 */

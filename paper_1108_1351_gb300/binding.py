@@ -17,7 +17,10 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libkmeans2.so")
+# KMEANS2_DEBUG=1 loads the debug build (device-side index checks that report
+# an error status instead of trapping; build it with build.build(debug=True))
+LIB_PATH = os.path.join(_HERE, "libkmeans2_debug.so" if os.environ.get("KMEANS2_DEBUG") == "1"
+                        else "libkmeans2.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "kmeans2.h")
 
 PRECISION = {"fp32": 0, "bf16": 1, "auto": 2, "tf32x3": 3}

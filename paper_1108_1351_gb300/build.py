@@ -17,6 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(CSRC, "_build")
 LIB = os.path.join(HERE, "libkmeans2.so")
+# debug build: device-side index checks (KM2_DEBUG_CHECKS) that report an
+# error status instead of trapping; loaded when KMEANS2_DEBUG=1
+OBJ_DEBUG = os.path.join(CSRC, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libkmeans2_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -42,9 +46,14 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link the library; returns the path of the shared object."""
+def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False,
+          debug: bool = False) -> str:
+    """Compile and link the library; returns the path of the shared object.
+    debug=True builds libkmeans2_debug.so with the device-side index checks."""
     nvcc = _nvcc()
+    OBJ = OBJ_DEBUG if debug else globals()["OBJ"]
+    LIB = LIB_DEBUG if debug else globals()["LIB"]
+    flags = NVCC_FLAGS + (["-DKM2_DEBUG_CHECKS"] if debug else [])
     os.makedirs(OBJ, exist_ok=True)
     # objects built on another host architecture (x86 here, aarch64 on the GPU
     # hosts) must not be linked: rebuild everything when the stamp differs
@@ -62,7 +71,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
     for src in srcs:
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *flags, "-I", INCLUDE, "-c", src, "-o", obj]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append((src, cmd))

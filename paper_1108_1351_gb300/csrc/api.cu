@@ -17,9 +17,20 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "api_internal.h"
 
 namespace km2 {
+
+// NVTX range for the lifetime of the object (header-only NVTX v3: a no-op
+// unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 thread_local long long g_launches = 0;
 
@@ -262,9 +273,12 @@ int choose_form(int requested, int d, int k, const float* X, int* form)
             return KMEANS2_OK;
         case KMEANS2_PRECISION_AUTO:
             // For d <= 32 the CUDA-core form is as fast per launch as the tensor-core
-            // forms and flags far fewer near ties (measured); from d = 64 on the
-            // d FFMAs per distance dominate and the BF16 tensor-core form wins.
-            *form = (bf && d >= 64) ? KMEANS2_PRECISION_BF16 : KMEANS2_PRECISION_FP32;
+            // forms and flags far fewer near ties (measured).  From d = 64 on the
+            // BF16 tensor-core form wins once k is large (k >= 512: 1.1-2.5x
+            // faster fits); with fewer centers the CUDA-core kernel is fast
+            // enough that the BF16 form's 5-10x more near-tie rechecks lose
+            // (measured on Gaussian mixtures of 4 to 1024 components).
+            *form = (bf && d >= 64 && k >= 512) ? KMEANS2_PRECISION_BF16 : KMEANS2_PRECISION_FP32;
             return KMEANS2_OK;
         default:
             set_last_error_text("precision form not available in this build");
@@ -345,6 +359,7 @@ int run_loop_host(const float* X, long long n, int d, Workspace& w, int* labels,
     }
     int rc = KMEANS2_OK;
     for (int it = 0; it < max_iter && rc == KMEANS2_OK; ++it) {
+        NvtxRange iteration_range("kmeans2 iteration");
         if (prof) {
             cudaEventRecord(ev0, s);
             rc = launch_assign(X, n, d, w, labels, s, sm_count);
@@ -386,6 +401,10 @@ int map_stage_error(int err)
         set_last_error_text("a device-side wait on the tensor-core pipeline timed out");
         return KMEANS2_ERR_TIMEOUT;
     }
+    if (err == kErrBounds) {
+        set_last_error_text("a device-side index check failed (debug build)");
+        return KMEANS2_ERR_CUDA;
+    }
     set_last_error_text("max|x| >= 2^50 is outside the supported range");
     return KMEANS2_ERR_UNSUPPORTED;
 }
@@ -394,8 +413,10 @@ int map_stage_error(int err)
 // master already set).  The caller has zeroed w.st and recorded max|x| in it.
 int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, double tol,
               int max_iter, bool use_graph, cudaStream_t s, int sm_count, StageState& out,
-              double* traj_J_host, double* traj_shift_host, kmeans2_profile* prof)
+              double* traj_J_host, double* traj_shift_host, kmeans2_profile* prof,
+              const char* name = "kmeans2 stage")
 {
+    NvtxRange stage_range(name);
     size_t kd = (size_t)w.c.k * d;
     KM2_CUDA(cudaMemsetAsync(w.acc.s_lo, 0, kd * 8, s));
     KM2_CUDA(cudaMemsetAsync(w.acc.s_hi, 0, kd * 8, s));
@@ -726,6 +747,7 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
            kmeans2_result* res, const Resolved& r, DeviceScratch& ws,
            std::chrono::steady_clock::time_point t0, long long launches0)
 {
+    NvtxRange fit_range("kmeans2 fit");
     const kmeans2_options& o = r.opt;
     const double tol_fast = (o.tol_fast > 0.0) ? o.tol_fast : tol;
     const bool use_graph = o.use_graph != 0;
@@ -765,7 +787,7 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
         KM2_TRY(launch_gather(Xd, d, subset, m, Xs, w.st, s, ws.sm_count));
         if (!o.init_centers) KM2_TRY(launch_init_centers(Xs, d, pos, k, w.c.c64, s));
         KM2_TRY(run_stage(Xs, m, d, w, labels_s, tol_fast, max_iter, use_graph, s, ws.sm_count,
-                          fs, o.traj_J_fast, o.traj_shift_fast, o.profile));
+                          fs, o.traj_J_fast, o.traj_shift_fast, o.profile, "kmeans2 fast stage"));
         rr.iters_fast = fs.iter;
         rr.converged_fast = fs.converged;
         rr.shift_fast = fs.shift;
@@ -776,7 +798,7 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
     KM2_TRY(launch_maxabs(Xd, n, d, w.st, s, ws.sm_count));
     StageState ss;
     KM2_TRY(run_stage(Xd, n, d, w, labels, tol, max_iter, use_graph, s, ws.sm_count, ss,
-                      o.traj_J_slow, o.traj_shift_slow, o.profile));
+                      o.traj_J_slow, o.traj_shift_slow, o.profile, "kmeans2 slow stage"));
     rr.iters_slow = ss.iter;
     rr.converged_slow = ss.converged;
     rr.shift_slow = ss.shift;
@@ -1011,6 +1033,7 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
     StageState ss;
     std::memset(&ss, 0, sizeof(ss));
     for (int it = 0; it < max_iter; ++it) {
+        NvtxRange iteration_range("kmeans2 streamed iteration");
         KM2_TRY(stream_pass(cs, s, [&](long long c, const float* Xc, long long rows) {
             int* lab = labels + c * chunk;
             KM2_TRY(launch_assign(Xc, rows, d, w, lab, s, ws.sm_count));

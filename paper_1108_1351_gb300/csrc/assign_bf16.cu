@@ -460,7 +460,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 old = (lab_bulk && in_ring) ? side.lab[r][row] : labels[p];
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.side_empty[r]);
-            if (valid && !flag) {
+            if (valid && !flag && label_ok(BI, a.k, st) && old_label_ok(old, a.k, st)) {
                 if (BI != old) {
                     for (int t = 0; t < d; ++t) {
                         const long long val = to_fixed(__ldg(xr + t), scaleF);

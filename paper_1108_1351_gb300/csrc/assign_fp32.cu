@@ -272,7 +272,7 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
                 for (int t = 0; t < D; ++t) qloc += sq_fixed(x[p][t], scaleG);
             }
             recheck_append(flag, (int)i, list, &st->recheck_count);
-            if (valid && !flag) {
+            if (valid && !flag && label_ok(BI[p], k, st) && old_label_ok(oldl[p], k, st)) {
                 const int lab = BI[p];
                 const int old = oldl[p];
                 if (lab != old) {
@@ -478,8 +478,9 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
                 for (int t = tx; t < d; t += 16) qloc += sq_fixed(__ldg(xr + t), scaleG);
             if (flag) continue;
             const int lab = bi[r];
+            if (!label_ok(lab, c.k, st)) continue;
             const int old = olds[r];
-            if (lab == old) continue;
+            if (!old_label_ok(old, c.k, st) || lab == old) continue;
             for (int t = tx; t < d; t += 16) {
                 long long v = to_fixed(__ldg(xr + t), scaleF);
                 split_add(acc.s_lo + (long long)lab * d + t, acc.s_hi + (long long)lab * d + t, v);

@@ -528,7 +528,7 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                                                      : labels[p])
                                         : -1;
                     const int lab = BI[t];
-                    if (lab != old) {
+                    if (lab != old && label_ok(lab, c.k, st) && old_label_ok(old, c.k, st)) {
 #pragma unroll
                         for (int e = 0; e < D; ++e) {
                             const long long val = to_fixed(x[e], scaleF);

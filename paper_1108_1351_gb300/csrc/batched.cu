@@ -373,7 +373,8 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
                     if (valid && !flag) {
                         const int lab = BI[p];
                         const int old = (mode == kModeDelta) ? labels[i] : -1;
-                        if (lab != old) {
+                        if (lab != old && label_ok(lab, I->c.k, st) &&
+                            old_label_ok(old, I->c.k, st)) {
 #pragma unroll
                             for (int t = 0; t < DC; ++t) {
                                 if (t >= d) break;

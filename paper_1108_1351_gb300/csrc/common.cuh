@@ -51,6 +51,28 @@ struct StageState {
 constexpr int kErrNonFinite = 1;
 constexpr int kErrRange = 2;       // max|x| >= 2^50
 constexpr int kErrTimeout = 3;     // a bounded device-side wait gave up
+constexpr int kErrBounds = 4;      // a debug-build index check failed (KM2_DEBUG_CHECKS)
+
+// Debug builds (-DKM2_DEBUG_CHECKS) check every decided label, and every old
+// label read back in delta mode (-1 = none), against [0, k) before it
+// addresses the cluster sums; a failure records kErrBounds and the point is
+// skipped (no trap).  Release builds compile the checks away.
+__device__ __forceinline__ bool label_ok(int lab, int k, StageState* st)
+{
+#ifdef KM2_DEBUG_CHECKS
+    if ((unsigned)lab >= (unsigned)k) {
+        atomicExch(&st->error, kErrBounds);
+        return false;
+    }
+#else
+    (void)lab; (void)k; (void)st;
+#endif
+    return true;
+}
+__device__ __forceinline__ bool old_label_ok(int old, int k, StageState* st)
+{
+    return old == -1 || label_ok(old, k, st);
+}
 
 // Accumulator arrays of one stage (device, zeroed by the host before a full pass).
 struct Accum {

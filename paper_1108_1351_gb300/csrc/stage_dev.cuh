@@ -288,8 +288,8 @@ static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers
             if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
         }
         int old = (mode == kModeDelta) ? labels[i] : -1;
-        __syncwarp();   // every lane has read the old label (and its cache) before reuse
-        if (bj != old) {
+        __syncwarp();   // every lane has read the old label before lane 0 rewrites it
+        if (bj != old && label_ok(bj, k, st) && old_label_ok(old, k, st)) {
             for (int t = lane; t < d; t += 32) {
                 long long v = to_fixed(__ldg(x + t), scaleF);
                 split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, v);
