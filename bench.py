@@ -15,8 +15,9 @@ fraction 1%, tol 1e-5, max_iter 50 per stage, seed 0.  X is 16 GB, far larger
 than L2, so no flush is needed between steps.
 
 Under torchrun (N > 1) every rank fits its own replica of the workload (seed +
-rank): the fit has no cross-rank exchange in this build ("replicas only"), the
-value is the total over ranks divided by the slowest rank's time ("weak").
+rank) with no cross-rank exchange ("replicas"; the row-sharded fit is the
+separate shard-session API), and the value is the total over ranks divided by
+the slowest rank's time ("weak").
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the only other place this file runs the oracle;
@@ -611,6 +612,57 @@ def run_sweep(args):
     return 0
 
 
+def run_sharded(args, cfg):
+    """The data-parallel form on one GPU: the default workload split into
+    --shards row blocks, each run as a rank (own sums, labels and near-tie
+    list, replicated centers) with the integer partials all-reduced in rank
+    order every iteration (kmeans2_fit_sharded); the unsharded fit beside it."""
+    import torch
+    import paper_1108_1351_gb300 as km
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    km.load()
+    X = _gen(cfg, dev, cfg["seed"] + rank)
+    stream = torch.cuda.current_stream(dev)
+    fargs = (cfg["k"], cfg["f"], cfg["seed"] + rank, cfg["tol"], cfg["max_iter"])
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = fn()
+        torch.cuda.synchronize()
+        return r, (time.perf_counter() - t0) / args.steps
+
+    clk = ClockSampler(None)
+    clk.start()
+    r, t = timed(lambda: km.fit_sharded(X, *fargs, args.shards, stream=stream))
+    r1, t1 = timed(lambda: km.fit(X, *fargs, stream=stream))
+    clocks = clk.stop()
+    same = (r.J == r1.J and (r.iters_fast, r.iters_slow) == (r1.iters_fast, r1.iters_slow)
+            and bool(torch.equal(r.labels, r1.labels)) and bool(torch.equal(r.centers, r1.centers)))
+    t_ms, evals = reduce_over_ranks(1e3 * t, r.distance_evals, ws, dev)
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": evals / (t_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sharded", "n": cfg["n"], "d": cfg["d"], "k": cfg["k"],
+                       "ranks_on_one_gpu": args.shards,
+                       "exchange": "int64 partials summed in rank order per iteration"},
+            "time_to_converge_s": t_ms / 1e3, "unsharded_time_to_converge_s": t1,
+            "identical_to_unsharded": same,
+            "fit": {"J": r.J, "iters_fast": r.iters_fast, "iters_slow": r.iters_slow},
+            "roofline": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_streamed(args, cfg):
     """Host-resident X streamed through the GPU each slow-stage iteration
     (kmeans2_fit_streamed), on the default workload held in pinned host
@@ -774,7 +826,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="aniso8",
-                    choices=sorted(CONFIGS) + ["serve", "batched", "sweep", "streamed"])
+                    choices=sorted(CONFIGS) + ["serve", "batched", "sweep", "streamed", "sharded"])
+    ap.add_argument("--shards", type=int, default=4,
+                    help="sharded: ranks simulated on this GPU")
     ap.add_argument("--chunk-points", type=int, default=1 << 26,
                     help="streamed: rows per streamed chunk")
     ap.add_argument("--sweep-n", type=int, default=10_000_000, help="sweep: points")
@@ -798,6 +852,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
+    if args.config == "sharded":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the sharded workload compares "
+                              "with the unsharded GPU fit in the same line"}))
+            return 0
+        return run_sharded(args, CONFIGS["aniso8"])
     if args.config == "streamed":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the streamed workload compares "

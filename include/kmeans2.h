@@ -69,7 +69,7 @@ extern "C" {
 #define KMEANS2_ERR_NONFINITE (-4)    /* X holds a NaN or an infinity */
 #define KMEANS2_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
 #define KMEANS2_ERR_ADMISSION (-6)    /* a server refused a job (HBM budget) */
-#define KMEANS2_ERR_UNSUPPORTED (-7)  /* shape or mode not available on this build */
+#define KMEANS2_ERR_UNSUPPORTED (-7)  /* shape or mode not supported */
 
 /* ---------------------------------------------------------------- options */
 /* Forms of the distance kernel.  Every form returns the same labels (near

@@ -281,7 +281,7 @@ int choose_form(int requested, int d, int k, const float* X, int* form)
             *form = (bf && d >= 64 && k >= 512) ? KMEANS2_PRECISION_BF16 : KMEANS2_PRECISION_FP32;
             return KMEANS2_OK;
         default:
-            set_last_error_text("precision form not available in this build");
+            set_last_error_text("unknown precision form");
             return KMEANS2_ERR_UNSUPPORTED;
     }
 }
