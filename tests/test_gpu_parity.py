@@ -276,3 +276,13 @@ def test_nonfinite_input_is_rejected():
     with pytest.raises(km.KMeans2Error) as e:
         km.fit(torch.as_tensor(X, device=DEV), 3, 0.5, 0, 1e-6, 10)
     assert e.value.status == -4
+
+
+def test_release_memory_between_fits_keeps_results():
+    # the library's scratch pool keeps freed memory mapped; trimming it between
+    # calls changes nothing in the results
+    X = torch.as_tensor(synth.aniso_gaussian_noise(200_000, 8, 16, seed=5), device=DEV)
+    a = km.fit(X, 16, 0.05, 2, 1e-6, 30)
+    km.release_memory()
+    b = km.fit(X, 16, 0.05, 2, 1e-6, 30)
+    assert torch.equal(a.labels, b.labels) and torch.equal(a.centers, b.centers) and a.J == b.J
