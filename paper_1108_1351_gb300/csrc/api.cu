@@ -325,7 +325,9 @@ int run_loop_graph(const float* X, long long n, int d, Workspace& w, int* labels
         e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { set_last_error("cudaStreamBeginCaptureToGraph", e); rc = KMEANS2_ERR_CUDA; break; }
+        const long long body0 = g_launches;
         rc = launch_iteration(X, n, d, w, labels, (unsigned long long)handle, 1, s, sm_count);
+        const long long body_launches = g_launches - body0;
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(s, &captured);
         if (rc != KMEANS2_OK) break;
@@ -341,7 +343,8 @@ int run_loop_graph(const float* X, long long n, int d, Workspace& w, int* labels
         e = cudaMemcpyAsync(&iters, &w.st->iter, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { set_last_error("cudaMemcpyAsync", e); rc = KMEANS2_ERR_CUDA; break; }
-        g_launches += 3ll * (iters > 1 ? iters - 1 : 0);   // body kernels per executed iteration
+        // the capture counted the body's kernels once; each further iteration reruns them
+        g_launches += body_launches * (iters > 1 ? iters - 1 : 0);
     } while (0);
     if (exec) cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);

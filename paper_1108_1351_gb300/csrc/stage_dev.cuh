@@ -95,6 +95,49 @@ static __device__ void stage_init_dev(StageState* st, int d, double tol, int max
     st->inv_scaleG = ldexp(1.0, -G);
 }
 
+// One warp: the new center j (its cluster mean; an empty cluster keeps its
+// center) with its FP32 copies and ||c_j||^2, and center j's terms of the
+// movement, of J and of the empty count in clus (4 k doubles).
+static __device__ __forceinline__ void finalize_center_warp(const Accum& acc, const Centers& c,
+                                                            double inv, int j, double* clus)
+{
+    const int k = c.k, d = c.d;
+    const int lane = threadIdx.x & 31;
+    long long N = (long long)acc.cnt[j];
+    double diff2 = 0.0, cS = 0.0, cc = 0.0, nn = 0.0;
+    for (int t = lane; t < d; t += 32) {
+        long long e = (long long)j * d + t;
+        const unsigned long long lo = acc.s_lo[e], hi = acc.s_hi[e];
+        double S = split_value(lo, hi, inv);
+        // carry the low word's upper half into the high word (same value):
+        // every pass adds at most 2 n < 2^32 low parts below 2^32 each, so
+        // the low word cannot wrap however many delta passes follow
+        acc.s_lo[e] = lo & 0xffffffffull;
+        acc.s_hi[e] = hi + (lo >> 32);
+        double cv = c.c64[e];
+        double cn = N > 0 ? S / (double)N : cv;
+        double df = cn - cv;
+        diff2 = fma(df, df, diff2);
+        cS = fma(cv, S, cS);
+        cc = fma(cv, cv, cc);
+        nn = fma(cn, cn, nn);
+        c.c64[e] = cn;
+        c.c32[e] = (float)cn;
+        c.c32t[(long long)t * c.kpad + j] = (float)cn;
+    }
+    diff2 = warp_sum_f64(diff2);
+    cS = warp_sum_f64(cS);
+    cc = warp_sum_f64(cc);
+    nn = warp_sum_f64(nn);
+    if (lane == 0) {
+        clus[j] = diff2;
+        clus[k + j] = 2.0 * cS - (double)N * cc;
+        clus[2 * k + j] = nn;
+        clus[3 * k + j] = (N == 0) ? 1.0 : 0.0;
+        c.cnorm[j] = (float)nn;
+    }
+}
+
 struct FinalizeSmem {
     double r_shift[1024];
     double r_J[1024];
@@ -103,13 +146,13 @@ struct FinalizeSmem {
     double Qtot;
 };
 
-// Whole block (blockDim.x <= 1024, a power of two).  New centers, movement,
-// J; loop control for the next iteration (thread 0 updates st).  clus: 4 k
-// doubles of scratch.  Ends with the block synchronised.
-static __device__ void finalize_block(Accum acc, Centers c, StageState* st, double* traj_J,
-                                      double* traj_shift, double* clus, FinalizeSmem& sm)
+// Whole block (blockDim.x <= 1024, a power of two), after every center's
+// finalize_center_warp: movement, J and loop control from clus, in a fixed
+// order (thread 0 updates st).  Ends with the block synchronised.
+static __device__ void finalize_reduce_block(int k, StageState* st, double* traj_J,
+                                             double* traj_shift, const double* clus,
+                                             FinalizeSmem& sm)
 {
-    const int k = c.k, d = c.d;
     if (threadIdx.x == 0) {
         double Q = st->Qtot;
         if (st->mode == kModeFull) {
@@ -118,44 +161,6 @@ static __device__ void finalize_block(Accum acc, Centers c, StageState* st, doub
         }
         sm.Qtot = Q;
     }
-    const double inv = st->inv_scaleF;
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < k; j += nw) {
-        long long N = (long long)acc.cnt[j];
-        double diff2 = 0.0, cS = 0.0, cc = 0.0, nn = 0.0;
-        for (int t = lane; t < d; t += 32) {
-            long long e = (long long)j * d + t;
-            const unsigned long long lo = acc.s_lo[e], hi = acc.s_hi[e];
-            double S = split_value(lo, hi, inv);
-            // carry the low word's upper half into the high word (same value):
-            // every pass adds at most 2 n < 2^32 low parts below 2^32 each, so
-            // the low word cannot wrap however many delta passes follow
-            acc.s_lo[e] = lo & 0xffffffffull;
-            acc.s_hi[e] = hi + (lo >> 32);
-            double cv = c.c64[e];
-            double cn = N > 0 ? S / (double)N : cv;
-            double df = cn - cv;
-            diff2 = fma(df, df, diff2);
-            cS = fma(cv, S, cS);
-            cc = fma(cv, cv, cc);
-            nn = fma(cn, cn, nn);
-            c.c64[e] = cn;
-            c.c32[e] = (float)cn;
-            c.c32t[(long long)t * c.kpad + j] = (float)cn;
-        }
-        diff2 = warp_sum_f64(diff2);
-        cS = warp_sum_f64(cS);
-        cc = warp_sum_f64(cc);
-        nn = warp_sum_f64(nn);
-        if (lane == 0) {
-            clus[j] = diff2;
-            clus[k + j] = 2.0 * cS - (double)N * cc;
-            clus[2 * k + j] = nn;
-            clus[3 * k + j] = (N == 0) ? 1.0 : 0.0;
-            c.cnorm[j] = (float)nn;
-        }
-    }
-    __syncthreads();
     double sh = 0.0, jj = 0.0, mx = 0.0;
     int em = 0;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
@@ -197,6 +202,19 @@ static __device__ void finalize_block(Accum acc, Centers c, StageState* st, doub
         st->recheck_count = 0;
     }
     __syncthreads();
+}
+
+// Whole block (blockDim.x <= 1024, a power of two).  New centers, movement,
+// J; loop control for the next iteration (thread 0 updates st).  clus: 4 k
+// doubles of scratch.  Ends with the block synchronised.
+static __device__ void finalize_block(Accum acc, Centers c, StageState* st, double* traj_J,
+                                      double* traj_shift, double* clus, FinalizeSmem& sm)
+{
+    const double inv = st->inv_scaleF;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < c.k; j += nw) finalize_center_warp(acc, c, inv, j, clus);
+    __syncthreads();
+    finalize_reduce_block(c.k, st, traj_J, traj_shift, clus, sm);
 }
 
 // FP32 D_j = ||c_j||^2 - 2 x.c_j of one point against centers j0 + 32 i
