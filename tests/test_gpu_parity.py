@@ -286,3 +286,20 @@ def test_release_memory_between_fits_keeps_results():
     km.release_memory()
     b = km.fit(X, 16, 0.05, 2, 1e-6, 30)
     assert torch.equal(a.labels, b.labels) and torch.equal(a.centers, b.centers) and a.J == b.J
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16"])
+def test_step_many_near_ties_with_many_centers(form):
+    # far from the origin with k * d >= 32768: thousands of flagged points go
+    # through the recheck that takes eight points per warp; labels stay exact
+    rng = np.random.default_rng(21)
+    n, d, k = 30000, 64, 600
+    X = (200.0 + rng.normal(size=(n, d)) * 0.05).astype(np.float32)
+    C = 200.0 + rng.normal(size=(k, d)) * 0.05
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision=form)
+    ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
+    assert np.array_equal(to_np(lab), olab)
+    assert_centers_close(to_np(cn), ocn, X)
+    assert_J_close(J, oJ, X)
+    assert em == oem
