@@ -102,6 +102,12 @@ struct Bf16Args {
     float kappa, kpack;
 };
 
+// Accumulators per epilogue group: two (MMAs of the next chunk overlap the
+// epilogue of this one) while 2 groups x 2 x NC columns fit in TMEM's 512;
+// one for NC = 256 (the wider MMAs then alternate with the epilogue).
+template <int NC>
+constexpr int kAccBufs = NC >= 256 ? 1 : 2;
+
 constexpr int kSR = 4;                 // side ring depth (tiles): ||x||^2 and old labels
 constexpr int kRecheckQ = 256;         // flagged points staged per epilogue warp
 
@@ -320,7 +326,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 if (two && !(ok = wait_bar(&bars.a_full[1], par, abort_v, st))) break;
                 tc::fence_after_sync();
                 for (int ch = 0; ch < nch && ok; ++ch) {
-                    const int b0 = ch & 1, b1 = 2 + (ch & 1);
+                    const int b0 = ch % kAccBufs<NC>, b1 = kAccBufs<NC> + ch % kAccBufs<NC>;
                     if (!(ok = wait_bar(&bars.acc_empty[b0], ((phase >> b0) & 1u) ^ 1u, abort_v, st))) break;
                     if (two && !(ok = wait_bar(&bars.acc_empty[b1], ((phase >> b1) & 1u) ^ 1u, abort_v, st)))
                         break;
@@ -397,8 +403,9 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             float B1 = INFINITY, B2 = INFINITY;
             int BI = 0;
             for (int ch = 0; ch < nch; ++ch) {
-                const int b = 2 * g + (ch & 1);
-                bool w = wait_bar(&bars.acc_full[b], (phase >> (ch & 1)) & 1u, abort_v, st);
+                const int b = g * kAccBufs<NC> + ch % kAccBufs<NC>;
+                bool w = wait_bar(&bars.acc_full[b], (phase >> (ch % kAccBufs<NC>)) & 1u, abort_v,
+                                  st);
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 tc::fence_after_sync();
                 // 32 columns at a time; the next load overlaps the current compare
@@ -420,7 +427,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
-                phase ^= 1u << (ch & 1);
+                phase ^= 1u << (ch % kAccBufs<NC>);
             }
             if (!ok) break;
             // ---- decide row `row` of tile i
@@ -611,14 +618,15 @@ int assign_bf16_supported(int d, int k, const float* X)
     return d >= 16 && d % 16 == 0 && bf16_fits(d);
 }
 
-// Chunk width NC: 128, or 64 when k fits in 64 (NC * chunks then never exceeds
-// k rounded up to 128, the least length of the padded ||c||^2 array).  Two
-// epilogue groups x two accumulators x NC columns fill at most the 512 TMEM
-// columns of the SM.
+// Chunk width NC: 64 when k fits in 64, 256 from k = 512 on (one M128 x N256
+// MMA per part and K-step: half the instructions and a wider B operand per
+// A read), else 128.  Two epilogue groups x kAccBufs accumulators x NC
+// columns fill at most the 512 TMEM columns of the SM.  Columns past k hold
+// zero centers with the padding norm, so they never win.
 int bf16_chunk(int d, int k)
 {
     (void)d;
-    return k <= 64 ? 64 : 128;
+    return k <= 64 ? 64 : (k >= 512 ? 256 : 128);
 }
 
 size_t bf16_xt_bytes(long long n, int d)
@@ -664,7 +672,7 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
         KM2_CUDA(cudaGetLastError());
     }
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * kEpiGroups * NC)) cols <<= 1;
+    while (cols < (uint32_t)(kEpiGroups * (NC >= 256 ? 1 : 2) * NC)) cols <<= 1;
     const size_t abytes = (size_t)4 * kRows * d, sbytes = (size_t)NC * 64;
     int sb = (int)((kSmemBudget - kStaticSmem - kSA * abytes - 4096) / sbytes);
     if (sb > kMaxSB) sb = kMaxSB;
@@ -677,6 +685,7 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     // barriers, the side ring and the recheck queues)
     KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<64>, kSmemBudget - kStaticSmem));
     KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<128>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<256>, kSmemBudget - kStaticSmem));
     const long long tiles = (n + kRows - 1) / kRows;
     long long grid = sm_count;
     if (grid > tiles) grid = tiles;
@@ -699,8 +708,10 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     ++g_launches;
     if (NC == 64)
         assign_bf16<64><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
-    else
+    else if (NC == 128)
         assign_bf16<128><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+    else
+        assign_bf16<256><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
