@@ -119,6 +119,15 @@ typedef struct kmeans2_options {
     double* traj_J_slow;
     double* traj_shift_slow;
     kmeans2_profile* profile;   /* optional HOST struct, see kmeans2_profile */
+    /* kmeans2_fit only: optional HOST arrays receiving, per iteration, the
+       updated centers (capacity max_iter*k*d FP64, iteration-major) and the
+       cluster sizes of that iteration's assignment (max_iter*k int64): the
+       center movements of Figs. 4-9 and the point / center distribution of
+       Table 1. */
+    double* traj_centers_fast;
+    double* traj_centers_slow;
+    int64_t* traj_counts_fast;
+    int64_t* traj_counts_slow;
 } kmeans2_options;
 
 /* Fill *opt with the defaults (AUTO form, tol_fast = tol, random init, graph loop). */

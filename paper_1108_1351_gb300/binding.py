@@ -61,6 +61,10 @@ class Options(ctypes.Structure):
         ("traj_J_slow", ctypes.c_void_p),
         ("traj_shift_slow", ctypes.c_void_p),
         ("profile", ctypes.c_void_p),
+        ("traj_centers_fast", ctypes.c_void_p),
+        ("traj_centers_slow", ctypes.c_void_p),
+        ("traj_counts_fast", ctypes.c_void_p),
+        ("traj_counts_slow", ctypes.c_void_p),
     ]
 
 
@@ -321,10 +325,14 @@ class FitResult:
 
 def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int, *,
         tol_fast: float = 0.0, precision: str = "auto", init_centers=None, start_stage: int = 0,
-        use_graph: bool = True, stream=None, trajectories: bool = False, centers_out=None,
-        labels_out=None, profile: "Profile | None" = None) -> FitResult:
+        use_graph: bool = True, stream=None, trajectories: bool = False,
+        center_trajectories: bool = False, centers_out=None, labels_out=None,
+        profile: "Profile | None" = None) -> FitResult:
     """Two-stage k-means (kmeans2_fit).  Outputs live where X lives (device
-    tensors for a CUDA tensor, host arrays otherwise) unless given."""
+    tensors for a CUDA tensor, host arrays otherwise) unless given.
+    trajectories: per-iteration J and max center movement of both stages;
+    center_trajectories: also the updated centers (iterations x k x d) and the
+    cluster sizes (iterations x k) of every iteration."""
     lib = load()
     X = _as_points(X)
     n, d = X.shape
@@ -345,15 +353,21 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
         for key in ("J_fast", "shift_fast", "J_slow", "shift_slow"):
             traj[key] = np.zeros(max_iter, dtype=np.float64)
             setattr(opt, "traj_" + key, traj[key].ctypes.data)
+    if center_trajectories:
+        for st in ("fast", "slow"):
+            traj["centers_" + st] = np.zeros((max_iter, k, d), dtype=np.float64)
+            traj["counts_" + st] = np.zeros((max_iter, k), dtype=np.int64)
+            setattr(opt, "traj_centers_" + st, traj["centers_" + st].ctypes.data)
+            setattr(opt, "traj_counts_" + st, traj["counts_" + st].ctypes.data)
     res = Result()
     with _device_of(X):
         rc = lib.kmeans2_fit(_ptr(X), n, d, k, subset_fraction, seed & (2**64 - 1), tol, max_iter,
                              _ptr(cen), _ptr(lab), ctypes.byref(res), ctypes.byref(opt))
     if rc != 0:
         raise KMeans2Error(rc, "kmeans2_fit")
-    if trajectories:
-        traj = {"J_fast": traj["J_fast"][:res.iters_fast], "shift_fast": traj["shift_fast"][:res.iters_fast],
-                "J_slow": traj["J_slow"][:res.iters_slow], "shift_slow": traj["shift_slow"][:res.iters_slow]}
+    if traj:
+        lim = {"fast": res.iters_fast, "slow": res.iters_slow}
+        traj = {key: v[:lim[key.rsplit("_", 1)[1]]] for key, v in traj.items()}
     return FitResult(centers=cen, labels=lab, J=res.J, iters_fast=res.iters_fast,
                      iters_slow=res.iters_slow, converged_fast=bool(res.converged_fast),
                      converged_slow=bool(res.converged_slow), empty_clusters=res.empty_clusters,

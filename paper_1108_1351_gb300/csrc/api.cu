@@ -292,7 +292,7 @@ int launch_iteration(const float* X, long long n, int d, Workspace& w, int* labe
 {
     KM2_TRY(launch_assign(X, n, d, w, labels, s, sm_count));
     KM2_TRY(launch_recheck(X, d, w.c, labels, w.list, w.st, w.acc, s, sm_count));
-    KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, handle, use_cond,
+    KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj(), w.clus, handle, use_cond,
                             s));
     return KMEANS2_OK;
 }
@@ -370,7 +370,7 @@ int run_loop_host(const float* X, long long n, int d, Workspace& w, int* labels,
             if (rc == KMEANS2_OK)
                 rc = launch_recheck(X, d, w.c, labels, w.list, w.st, w.acc, s, sm_count);
             if (rc == KMEANS2_OK)
-                rc = launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, 0ull, 0, s);
+                rc = launch_finalize(w.acc, w.c, w.st, w.traj(), w.clus, 0ull, 0, s);
         } else {
             rc = launch_iteration(X, n, d, w, labels, 0ull, 0, s, sm_count);
         }
@@ -417,7 +417,8 @@ int map_stage_error(int err)
 int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, double tol,
               int max_iter, bool use_graph, cudaStream_t s, int sm_count, StageState& out,
               double* traj_J_host, double* traj_shift_host, kmeans2_profile* prof,
-              const char* name = "kmeans2 stage")
+              const char* name = "kmeans2 stage", double* traj_c_host = nullptr,
+              int64_t* traj_n_host = nullptr)
 {
     NvtxRange stage_range(name);
     size_t kd = (size_t)w.c.k * d;
@@ -439,6 +440,13 @@ int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, dou
                                  cudaMemcpyDeviceToHost, s));
     if (traj_shift_host && out.iter > 0)
         KM2_CUDA(cudaMemcpyAsync(traj_shift_host, w.traj_shift, sizeof(double) * out.iter,
+                                 cudaMemcpyDeviceToHost, s));
+    if (traj_c_host && w.traj_c && out.iter > 0)
+        KM2_CUDA(cudaMemcpyAsync(traj_c_host, w.traj_c,
+                                 sizeof(double) * (size_t)out.iter * w.c.k * d,
+                                 cudaMemcpyDeviceToHost, s));
+    if (traj_n_host && w.traj_n && out.iter > 0)
+        KM2_CUDA(cudaMemcpyAsync(traj_n_host, w.traj_n, sizeof(int64_t) * (size_t)out.iter * w.c.k,
                                  cudaMemcpyDeviceToHost, s));
     KM2_CUDA(cudaStreamSynchronize(s));
     return KMEANS2_OK;
@@ -759,6 +767,10 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
     Workspace w;
     KM2_TRY(choose_form(o.precision, d, k, Xd, &w.form));
     KM2_TRY(alloc_workspace(w, ws, n, k, d, max_iter, s));
+    if (o.traj_centers_fast || o.traj_centers_slow)
+        KM2_TRY(ws.alloc((void**)&w.traj_c, sizeof(double) * (size_t)max_iter * k * d, s));
+    if (o.traj_counts_fast || o.traj_counts_slow)
+        KM2_TRY(ws.alloc((void**)&w.traj_n, sizeof(long long) * (size_t)max_iter * k, s));
     bool lab_dev = is_device_ptr(labels_out) && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
     int* labels = lab_dev ? labels_out : nullptr;
     if (!labels) KM2_TRY(ws.alloc((void**)&labels, sizeof(int) * (size_t)n, s));
@@ -790,7 +802,8 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
         KM2_TRY(launch_gather(Xd, d, subset, m, Xs, w.st, s, ws.sm_count));
         if (!o.init_centers) KM2_TRY(launch_init_centers(Xs, d, pos, k, w.c.c64, s));
         KM2_TRY(run_stage(Xs, m, d, w, labels_s, tol_fast, max_iter, use_graph, s, ws.sm_count,
-                          fs, o.traj_J_fast, o.traj_shift_fast, o.profile, "kmeans2 fast stage"));
+                          fs, o.traj_J_fast, o.traj_shift_fast, o.profile, "kmeans2 fast stage",
+                          o.traj_centers_fast, o.traj_counts_fast));
         rr.iters_fast = fs.iter;
         rr.converged_fast = fs.converged;
         rr.shift_fast = fs.shift;
@@ -801,7 +814,8 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
     KM2_TRY(launch_maxabs(Xd, n, d, w.st, s, ws.sm_count));
     StageState ss;
     KM2_TRY(run_stage(Xd, n, d, w, labels, tol, max_iter, use_graph, s, ws.sm_count, ss,
-                      o.traj_J_slow, o.traj_shift_slow, o.profile, "kmeans2 slow stage"));
+                      o.traj_J_slow, o.traj_shift_slow, o.profile, "kmeans2 slow stage",
+                      o.traj_centers_slow, o.traj_counts_slow));
     rr.iters_slow = ss.iter;
     rr.converged_slow = ss.converged;
     rr.shift_slow = ss.shift;
@@ -1043,7 +1057,7 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
             KM2_TRY(launch_recheck(Xc, d, w.c, lab, w.list, w.st, w.acc, s, ws.sm_count));
             return launch_recheck_reset(w.st, s);
         }));
-        KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj_J, w.traj_shift, w.clus, 0ull, 0, s));
+        KM2_TRY(launch_finalize(w.acc, w.c, w.st, w.traj(), w.clus, 0ull, 0, s));
         KM2_CUDA(cudaMemcpyAsync(&ss, w.st, sizeof(StageState), cudaMemcpyDeviceToHost, s));
         KM2_CUDA(cudaStreamSynchronize(s));
         if (ss.error) return map_stage_error(ss.error);

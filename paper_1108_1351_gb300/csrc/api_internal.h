@@ -87,10 +87,9 @@ int launch_init_centers(const float* Xs, int d, const long long* pos, int k, dou
                         cudaStream_t s);
 int launch_center_prep(const Centers& c, StageState* st, cudaStream_t s);
 int launch_stage_init(StageState* st, int d, double tol, int max_iter, cudaStream_t s);
-// clus: 4*k doubles of scratch.
-int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* traj_J,
-                    double* traj_shift, double* clus, unsigned long long cond_handle,
-                    int use_cond, cudaStream_t s);
+// clus: 4*k doubles of scratch; tr: the stage's optional per-iteration records.
+int launch_finalize(const Accum& acc, const Centers& c, StageState* st, const TrajDev& tr,
+                    double* clus, unsigned long long cond_handle, int use_cond, cudaStream_t s);
 int launch_recheck(const float* X, int d, const Centers& c, int* labels, const int* list,
                    StageState* st, const Accum& acc, cudaStream_t s, int sm_count);
 // Folds this pass's recheck count into the stage total and empties the list
@@ -131,6 +130,9 @@ struct Workspace {
     double* clus = nullptr;
     double* traj_J = nullptr;      // max_iter
     double* traj_shift = nullptr;  // max_iter
+    double* traj_c = nullptr;      // max_iter * k * d (only when requested)
+    long long* traj_n = nullptr;   // max_iter * k (only when requested)
+    TrajDev traj() const { return TrajDev{traj_J, traj_shift, traj_c, traj_n}; }
     int max_iter = 0;
     DeviceScratch* ws = nullptr;   // the call's scratch (per-stage buffers)
     // BF16 form: the stage's points as BF16 tiles, their ||x||^2, the centers' chunks

@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kThreads) batch_finalize_kernel(BatchInst* ins
         if (threadIdx.x == 0) { I->stage = 2; I->error = I->st.error; }
         return;
     }
-    finalize_block(I->acc, I->c, &I->st, nullptr, nullptr, I->clus, sm);
+    finalize_block(I->acc, I->c, &I->st, TrajDev{nullptr, nullptr, nullptr, nullptr}, I->clus, sm);
     if (threadIdx.x == 0) {
         switched = 0;
         if (I->st.done) {

@@ -81,6 +81,14 @@ struct Accum {
     unsigned long long* cnt;      // k (two's complement int64)
 };
 
+// Optional per-iteration records of a stage (device arrays, null = off).
+struct TrajDev {
+    double* J;                 // max_iter
+    double* shift;             // max_iter
+    double* centers;           // max_iter * k * d: the updated centers
+    long long* counts;         // max_iter * k: the cluster sizes of the assignment
+};
+
 // Center copies derived from the FP64 master by center_prep / finalize.
 struct Centers {
     double* c64;                  // k*d   FP64 master (row-major)

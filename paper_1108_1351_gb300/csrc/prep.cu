@@ -93,9 +93,8 @@ __global__ void stage_init_kernel(StageState* st, int d, double tol, int max_ite
 
 // One CTA.  New centers, movement, J; loop control for the next iteration.
 __global__ void __launch_bounds__(1024) finalize_kernel(Accum acc, Centers c, StageState* st,
-                                                        double* traj_J, double* traj_shift,
-                                                        double* clus, unsigned long long handle,
-                                                        int use_cond)
+                                                        TrajDev tr, double* clus,
+                                                        unsigned long long handle, int use_cond)
 {
     __shared__ FinalizeSmem sm;
     if (st->error) {
@@ -105,25 +104,26 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Accum acc, Centers c, St
         }
         return;
     }
-    finalize_block(acc, c, st, traj_J, traj_shift, clus, sm);
+    finalize_block(acc, c, st, tr, clus, sm);
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(handle, st->done ? 0u : 1u);
 }
 
 // Many CTAs: the new centers, one warp per center (large k * d).
 __global__ void __launch_bounds__(256) finalize_centers_kernel(Accum acc, Centers c,
-                                                               StageState* st, double* clus)
+                                                               StageState* st, TrajDev tr,
+                                                               double* clus)
 {
     if (st->error) return;
     const double inv = st->inv_scaleF;
+    const int it = st->iter;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int j = gw; j < c.k; j += nw) finalize_center_warp(acc, c, inv, j, clus);
+    for (int j = gw; j < c.k; j += nw) finalize_center_warp(acc, c, inv, j, clus, tr, it);
 }
 
 // One CTA after finalize_centers_kernel: movement, J, loop control.
 __global__ void __launch_bounds__(1024) finalize_reduce_kernel(int k, StageState* st,
-                                                               double* traj_J, double* traj_shift,
-                                                               const double* clus,
+                                                               TrajDev tr, const double* clus,
                                                                unsigned long long handle,
                                                                int use_cond)
 {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(1024) finalize_reduce_kernel(int k, StageState
         }
         return;
     }
-    finalize_reduce_block(k, st, traj_J, traj_shift, clus, sm);
+    finalize_reduce_block(k, st, tr, clus, sm);
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(handle, st->done ? 0u : 1u);
 }
 
@@ -230,9 +230,8 @@ int launch_stage_init(StageState* st, int d, double tol, int max_iter, cudaStrea
 // k * d from which the center updates run on many CTAs instead of one.
 constexpr long long kSplitFinalizeWork = 16384;
 
-int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* traj_J,
-                    double* traj_shift, double* clus, unsigned long long cond_handle,
-                    int use_cond, cudaStream_t s)
+int launch_finalize(const Accum& acc, const Centers& c, StageState* st, const TrajDev& tr,
+                    double* clus, unsigned long long cond_handle, int use_cond, cudaStream_t s)
 {
     if ((long long)c.k * c.d >= kSplitFinalizeWork) {
         // spread the k center updates over the GPU, then reduce in one CTA
@@ -240,15 +239,14 @@ int launch_finalize(const Accum& acc, const Centers& c, StageState* st, double* 
         int blocks = (c.k + 7) / 8;
         if (blocks > 1024) blocks = 1024;
         g_launches += 2;
-        finalize_centers_kernel<<<blocks, 256, 0, s>>>(acc, c, st, clus);
+        finalize_centers_kernel<<<blocks, 256, 0, s>>>(acc, c, st, tr, clus);
         KM2_CUDA(cudaGetLastError());
-        finalize_reduce_kernel<<<1, 1024, 0, s>>>(c.k, st, traj_J, traj_shift, clus, cond_handle,
-                                                   use_cond);
+        finalize_reduce_kernel<<<1, 1024, 0, s>>>(c.k, st, tr, clus, cond_handle, use_cond);
         KM2_CUDA(cudaGetLastError());
         return KMEANS2_OK;
     }
     ++g_launches;
-    finalize_kernel<<<1, 1024, 0, s>>>(acc, c, st, traj_J, traj_shift, clus, cond_handle, use_cond);
+    finalize_kernel<<<1, 1024, 0, s>>>(acc, c, st, tr, clus, cond_handle, use_cond);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }

@@ -287,7 +287,7 @@ int resume_iter(kmeans2_shard* sh, kmeans2_exchange* next)
     unpack_partials_kernel<<<grid_for(kd + sh->k), 256, 0, s>>>(sh->x, sh->tot, sh->k, sh->d,
                                                                  sh->w.st);
     KM2_CUDA(cudaGetLastError());
-    KM2_TRY(launch_finalize(sh->tot, sh->w.c, sh->w.st, sh->w.traj_J, sh->w.traj_shift,
+    KM2_TRY(launch_finalize(sh->tot, sh->w.c, sh->w.st, sh->w.traj(),
                             sh->w.clus, 0ull, 0, s));
     StageState st;
     KM2_CUDA(cudaMemcpyAsync(&st, sh->w.st, sizeof(st), cudaMemcpyDeviceToHost, s));

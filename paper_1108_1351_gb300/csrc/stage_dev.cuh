@@ -97,9 +97,11 @@ static __device__ void stage_init_dev(StageState* st, int d, double tol, int max
 
 // One warp: the new center j (its cluster mean; an empty cluster keeps its
 // center) with its FP32 copies and ||c_j||^2, and center j's terms of the
-// movement, of J and of the empty count in clus (4 k doubles).
+// movement, of J and of the empty count in clus (4 k doubles).  Iteration it's
+// records of center j go to tr.centers / tr.counts when those are set.
 static __device__ __forceinline__ void finalize_center_warp(const Accum& acc, const Centers& c,
-                                                            double inv, int j, double* clus)
+                                                            double inv, int j, double* clus,
+                                                            const TrajDev& tr, int it)
 {
     const int k = c.k, d = c.d;
     const int lane = threadIdx.x & 31;
@@ -124,6 +126,7 @@ static __device__ __forceinline__ void finalize_center_warp(const Accum& acc, co
         c.c64[e] = cn;
         c.c32[e] = (float)cn;
         c.c32t[(long long)t * c.kpad + j] = (float)cn;
+        if (tr.centers) tr.centers[(long long)it * k * d + e] = cn;
     }
     diff2 = warp_sum_f64(diff2);
     cS = warp_sum_f64(cS);
@@ -135,6 +138,7 @@ static __device__ __forceinline__ void finalize_center_warp(const Accum& acc, co
         clus[2 * k + j] = nn;
         clus[3 * k + j] = (N == 0) ? 1.0 : 0.0;
         c.cnorm[j] = (float)nn;
+        if (tr.counts) tr.counts[(long long)it * k + j] = N;
     }
 }
 
@@ -149,10 +153,11 @@ struct FinalizeSmem {
 // Whole block (blockDim.x <= 1024, a power of two), after every center's
 // finalize_center_warp: movement, J and loop control from clus, in a fixed
 // order (thread 0 updates st).  Ends with the block synchronised.
-static __device__ void finalize_reduce_block(int k, StageState* st, double* traj_J,
-                                             double* traj_shift, const double* clus,
-                                             FinalizeSmem& sm)
+static __device__ void finalize_reduce_block(int k, StageState* st, const TrajDev& tr,
+                                             const double* clus, FinalizeSmem& sm)
 {
+    double* traj_J = tr.J;
+    double* traj_shift = tr.shift;
     if (threadIdx.x == 0) {
         double Q = st->Qtot;
         if (st->mode == kModeFull) {
@@ -207,14 +212,15 @@ static __device__ void finalize_reduce_block(int k, StageState* st, double* traj
 // Whole block (blockDim.x <= 1024, a power of two).  New centers, movement,
 // J; loop control for the next iteration (thread 0 updates st).  clus: 4 k
 // doubles of scratch.  Ends with the block synchronised.
-static __device__ void finalize_block(Accum acc, Centers c, StageState* st, double* traj_J,
-                                      double* traj_shift, double* clus, FinalizeSmem& sm)
+static __device__ void finalize_block(Accum acc, Centers c, StageState* st, TrajDev tr,
+                                      double* clus, FinalizeSmem& sm)
 {
     const double inv = st->inv_scaleF;
+    const int it = st->iter;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < c.k; j += nw) finalize_center_warp(acc, c, inv, j, clus);
+    for (int j = warp; j < c.k; j += nw) finalize_center_warp(acc, c, inv, j, clus, tr, it);
     __syncthreads();
-    finalize_reduce_block(c.k, st, traj_J, traj_shift, clus, sm);
+    finalize_reduce_block(c.k, st, tr, clus, sm);
 }
 
 // FP32 D_j = ||c_j||^2 - 2 x.c_j of one point against centers j0 + 32 i

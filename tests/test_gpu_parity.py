@@ -303,3 +303,28 @@ def test_step_many_near_ties_with_many_centers(form):
     assert_centers_close(to_np(cn), ocn, X)
     assert_J_close(J, oJ, X)
     assert em == oem
+
+
+def test_center_and_count_trajectories_match_oracle_steps():
+    # per iteration, the recorded centers and cluster sizes equal one oracle
+    # Lloyd step from the previous recorded centers (the first from the drawn
+    # initial centers, the slow stage's first from the fast stage's last)
+    n, d, k, f, seed = 20_000, 3, 5, 0.1, 4
+    X = _mixture(n, d, k, seed=31)
+    Xd = torch.as_tensor(X, device=DEV)
+    r = km.fit(Xd, k, f, seed, 1e-6, 40, trajectories=True, center_trajectories=True)
+    tr = r.traj
+    assert tr["centers_fast"].shape == (r.iters_fast, k, d)
+    assert tr["counts_slow"].shape == (r.iters_slow, k)
+    sub, pos = oracle.sample(n, k, f, seed)
+    Xs = X[sub]
+    C = Xs[pos].astype(np.float64)
+    for stage, Xst, iters in (("fast", Xs, r.iters_fast), ("slow", X, r.iters_slow)):
+        for i in range(iters):
+            Cn, lab, J, shift, em = oracle.lloyd_step(Xst, C, nthreads=NT)
+            assert np.array_equal(tr["counts_" + stage][i], np.bincount(lab, minlength=k))
+            assert_centers_close(tr["centers_" + stage][i], Cn, Xst)
+            assert_J_close(tr["J_" + stage][i], J, Xst)
+            C = tr["centers_" + stage][i]
+    assert np.array_equal(tr["centers_slow"][-1], r.centers.cpu().numpy())
+    assert tr["counts_slow"][-1].sum() == n and tr["counts_fast"][-1].sum() == len(sub)
