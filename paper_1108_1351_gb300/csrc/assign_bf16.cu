@@ -459,26 +459,40 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                     rq_n += __popc(m);
                 }
             }
-            const float* xr = a.X + p * d;
-            if (mode == kModeFull && valid)
-                for (int t = 0; t < d; ++t) qloc += sq_fixed(__ldg(xr + t), scaleG);
             int old = -1;
             if (mode == kModeDelta && valid)
                 old = (lab_bulk && in_ring) ? side.lab[r][row] : labels[p];
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.side_empty[r]);
-            if (valid && !flag && label_ok(BI, a.k, st) && old_label_ok(old, a.k, st)) {
-                if (BI != old) {
-                    for (int t = 0; t < d; ++t) {
-                        const long long val = to_fixed(__ldg(xr + t), scaleF);
-                        split_add(acc.s_lo + (long long)BI * d + t, acc.s_hi + (long long)BI * d + t, val);
-                        if (old >= 0)
-                            split_add(acc.s_lo + (long long)old * d + t,
-                                      acc.s_hi + (long long)old * d + t, -val);
+            const bool moved = valid && !flag && label_ok(BI, a.k, st) && old_label_ok(old, a.k, st) &&
+                               BI != old;
+            if (moved) {
+                atomicAdd(acc.cnt + BI, 1ull);
+                if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+                labels[p] = BI;
+            }
+            // Sums (and ||x||^2 in full mode): one row at a time, the warp's lanes
+            // over its coordinates, so each atomic instruction touches a few
+            // contiguous lines of s_lo / s_hi and each row is read coalesced.
+            const unsigned mmov = __ballot_sync(0xffffffffu, moved);
+            const unsigned msq = mode == kModeFull ? __ballot_sync(0xffffffffu, valid) : 0u;
+            for (unsigned m = mmov | msq; m; m &= m - 1) {
+                const int src = __ffs(m) - 1;
+                const long long pj = __shfl_sync(0xffffffffu, p, src);
+                const int bj = __shfl_sync(0xffffffffu, BI, src);
+                const int oj = __shfl_sync(0xffffffffu, old, src);
+                const bool mv = (mmov >> src) & 1u, sq = (msq >> src) & 1u;
+                const float* xr = a.X + pj * d;
+                for (int t = lane; t < d; t += 32) {
+                    const float xv = __ldg(xr + t);
+                    if (sq) qloc += sq_fixed(xv, scaleG);
+                    if (mv) {
+                        const long long val = to_fixed(xv, scaleF);
+                        split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, val);
+                        if (oj >= 0)
+                            split_add(acc.s_lo + (long long)oj * d + t,
+                                      acc.s_hi + (long long)oj * d + t, -val);
                     }
-                    atomicAdd(acc.cnt + BI, 1ull);
-                    if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
-                    labels[p] = BI;
                 }
             }
         }
