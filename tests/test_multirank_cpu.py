@@ -79,6 +79,17 @@ def test_reference_arm_rank0_prints_one_line():
     assert rec["e2e"]["h2d_bytes_per_step"] == 0
 
 
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    X = np.random.default_rng(0).standard_normal((20_000, 4)).astype(np.float32)
+    rec = bench.cpu_baseline(X, dict(k=8, d=4), budget_s=0.2, budget_1core_s=0.1)
+    assert rec["kind"] == "oracle" and rec["value"] > 0 and rec["cores"] >= 1
+    one = rec["one_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == rec["unit"]
+
+
 # ---------------------------------------------------------------- data-parallel driver
 # fit_data_parallel drives one shard per rank and turns each exchange the
 # shard asks for into one all_reduce over the group.  On CPU the CUDA shard is
