@@ -39,9 +39,10 @@
  *    distances are farther apart than a rigorous rounding-error bound; the
  *    other points are re-evaluated in exactly that FP64 form.
  *  - Cluster sums are exact integer (fixed-point) sums of the FP32 inputs at a
- *    per-stage scale 2^F, F = 46 - ceil(log2 max|x|) (so a center is off the
- *    exact mean by at most 2^-(F+1) per coordinate), which makes every mode
- *    deterministic: results do not depend on thread scheduling.
+ *    per-stage scale 2^F, F = 46 - E with E the smallest integer such that
+ *    max|x| < 2^E (so a center is off the exact mean by at most 2^-(F+1) per
+ *    coordinate, plus the FP64 rounding of the division), which makes every
+ *    mode deterministic: results do not depend on thread scheduling.
  *  - J is evaluated as sum_i ||x_i||^2 - sum_j (2 c_j . S_j - N_j ||c_j||^2)
  *    from exact sums, in FP64.
  */
