@@ -33,6 +33,9 @@ MUTATIONS = [
      "for (int32_t j = 0; j < k; ++j)\n        for (int32_t t = 0; t < d; ++t)\n"
      "            centers_out[(size_t)j * d + t] = (double)Xs[(size_t)pos[j] * d + t];\n"
      "    if (fast_centers_out)\n        memcpy(fast_centers_out,"),
+    ("shift_without_root", "        mv = sqrt(mv);\n", "\n"),
+    ("subset_unsorted", "    qsort(subset_out, (size_t)m, sizeof(int64_t), cmp_i64);\n", "\n"),
+    ("empty_not_counted", "            ++empty;\n", "\n"),
     ("labels_after_update", "memcpy(C, nxt, (size_t)k * (size_t)d * sizeof(double));\n        if (shift <= tol)",
      "memcpy(C, nxt, (size_t)k * (size_t)d * sizeof(double));\n"
      "        oracle_assign(X, n, d, k, C, labels, NULL, nthreads);\n        if (shift <= tol)"),
