@@ -408,25 +408,31 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                                   st);
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 tc::fence_after_sync();
-                // 32 columns at a time; the next load overlaps the current compare
-                uint32_t ra[32], rb[32];
+                // 32 columns at a time through three register buffers: block i + 2
+                // loads while block i is compared, and the accumulator is handed
+                // back to the MMA issuer as soon as its last block is in registers
+                // (the last two blocks are compared after that).
+                constexpr int NB = NC / 32;
+                uint32_t rr[3][32];
                 const uint32_t cb = tmem + lane_addr + (uint32_t)(b * NC);
-                tc::tmem_ld32_async(cb, ra);
+                auto release = [&]() {
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
+                };
+                tc::tmem_ld32_async(cb, rr[0]);
+                if (NB > 1) tc::tmem_ld32_async(cb + 32u, rr[1]);
                 tc::tmem_wait_ld();
+                if (NB <= 2) release();
 #pragma unroll
-                for (int c0 = 0; c0 < NC; c0 += 64) {
-                    if (c0 + 32 < NC) tc::tmem_ld32_async(cb + (uint32_t)(c0 + 32), rb);
-                    top2_cols(ra, ch * NC + c0, B1, B2, BI);
-                    tc::tmem_wait_ld();
-                    if (c0 + 32 < NC) {
-                        if (c0 + 64 < NC) tc::tmem_ld32_async(cb + (uint32_t)(c0 + 64), ra);
-                        top2_cols(rb, ch * NC + c0 + 32, B1, B2, BI);
+                for (int i = 0; i < NB; ++i) {
+                    if (i + 2 < NB) tc::tmem_ld32_async(cb + (uint32_t)(32 * (i + 2)), rr[(i + 2) % 3]);
+                    top2_cols(rr[i % 3], ch * NC + 32 * i, B1, B2, BI);
+                    if (i + 2 < NB) {
                         tc::tmem_wait_ld();
+                        if (i + 3 == NB) release();
                     }
                 }
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bars.acc_empty[b]);
                 phase ^= 1u << (ch % kAccBufs<NC>);
             }
             if (!ok) break;
