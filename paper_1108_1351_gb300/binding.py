@@ -260,23 +260,47 @@ def _as_points(X):
     return X
 
 
-def _as_centers(C, like):
+def _as_centers(C, like, k=None, d=None):
+    """FP64 contiguous centers (k x d; k taken from C when not given)."""
     if C is None:
         return None
     if _is_torch(C):
-        return C.to(dtype=torch.float64).contiguous()
-    C = np.ascontiguousarray(C, dtype=np.float64)
-    if _is_torch(like) and like.is_cuda:
-        return torch.as_tensor(C, device=like.device)
+        C = C.to(dtype=torch.float64).contiguous()
+    else:
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        if _is_torch(like) and like.is_cuda:
+            C = torch.as_tensor(C, device=like.device)
+    kk = C.shape[0] if (k is None and C.ndim == 2) else k
+    if C.ndim != 2 or (d is not None and C.shape[1] != d) or C.shape[0] != kk:
+        raise ValueError(f"centers must have shape ({kk}, {d}), got {tuple(C.shape)}")
     return C
+
+
+_TORCH_KIND = {"f64": torch.float64, "i32": torch.int32, "i64": torch.int64}
+_NP_KIND = {"f64": np.float64, "i32": np.int32, "i64": np.int64}
 
 
 def _empty(like, shape, kind):
     if _is_torch(like):
-        dt = {"f64": torch.float64, "i32": torch.int32, "i64": torch.int64}[kind]
-        return torch.empty(shape, dtype=dt, device=like.device)
-    dt = {"f64": np.float64, "i32": np.int32, "i64": np.int64}[kind]
-    return np.empty(shape, dtype=dt)
+        return torch.empty(shape, dtype=_TORCH_KIND[kind], device=like.device)
+    return np.empty(shape, dtype=_NP_KIND[kind])
+
+
+def _out(buf, like, shape, kind, name):
+    """A caller-given output buffer after checking its type, size and layout
+    (the library writes exactly prod(shape) elements), else a new one where
+    `like` lives."""
+    if buf is None:
+        return _empty(like, shape, kind)
+    count = int(np.prod(shape))
+    if _is_torch(buf):
+        ok = buf.dtype == _TORCH_KIND[kind] and buf.is_contiguous() and buf.numel() == count
+    else:
+        ok = (isinstance(buf, np.ndarray) and buf.dtype == _NP_KIND[kind]
+              and buf.flags.c_contiguous and buf.flags.writeable and buf.size == count)
+    if not ok:
+        raise ValueError(f"{name} must be a contiguous, writable {kind} buffer of {count} elements")
+    return buf
 
 
 def _stream_of(X, stream):
@@ -336,9 +360,9 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
     lib = load()
     X = _as_points(X)
     n, d = X.shape
-    C0 = _as_centers(init_centers, X)
-    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
-    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    C0 = _as_centers(init_centers, X, k, d)
+    cen = _out(centers_out, X, (k, d), "f64", "centers_out")
+    lab = _out(labels_out, X, (n,), "i32", "labels_out")
     opt = Options()
     lib.kmeans2_default_options(ctypes.byref(opt))
     opt.precision = PRECISION[precision]
@@ -393,9 +417,9 @@ def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_i
         raise TypeError("fit_streamed takes host-resident X")
     X = _as_points(X)
     n, d = X.shape
-    C0 = _as_centers(init_centers, X) if init_centers is not None else None
-    cen = centers_out if centers_out is not None else np.empty((k, d), dtype=np.float64)
-    lab = labels_out if labels_out is not None else np.empty((n,), dtype=np.int32)
+    C0 = _as_centers(init_centers, X, k, d)
+    cen = _out(centers_out, None, (k, d), "f64", "centers_out")
+    lab = _out(labels_out, None, (n,), "i32", "labels_out")
     opt = Options()
     lib.kmeans2_default_options(ctypes.byref(opt))
     opt.precision = PRECISION["fp32"]
@@ -425,9 +449,9 @@ def fit_sharded(X, k: int, subset_fraction: float, seed: int, tol: float, max_it
     lib = load()
     X = _as_points(X)
     n, d = X.shape
-    C0 = _as_centers(init_centers, X)
-    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
-    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    C0 = _as_centers(init_centers, X, k, d)
+    cen = _out(centers_out, X, (k, d), "f64", "centers_out")
+    lab = _out(labels_out, X, (n,), "i32", "labels_out")
     opt = Options()
     lib.kmeans2_default_options(ctypes.byref(opt))
     opt.precision = PRECISION[precision]
@@ -465,7 +489,7 @@ class Shard:
         self.device = self.X.device
         E = int(lib.kmeans2_shard_exchange_elems(self.d, self.k))
         self.xbuf = torch.zeros(E, dtype=torch.int64, device=self.device)
-        self._C0 = _as_centers(init_centers, self.X)
+        self._C0 = _as_centers(init_centers, self.X, self.k, self.d)
         opt = Options()
         lib.kmeans2_default_options(ctypes.byref(opt))
         opt.precision = PRECISION[precision]
@@ -621,8 +645,8 @@ class Server:
         lib = load()
         X = _as_points(X)
         n, d = X.shape
-        cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
-        lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+        cen = _out(centers_out, X, (k, d), "f64", "centers_out")
+        lab = _out(labels_out, X, (n,), "i32", "labels_out")
         job = Job(X=_ptr(X), n=n, d=d, k=int(k), subset_fraction=float(subset_fraction),
                   seed=int(seed) & (2**64 - 1), tol=float(tol), max_iter=int(max_iter), reserved=0,
                   centers_out=_ptr(cen), labels_out=_ptr(lab))
@@ -799,10 +823,10 @@ def step(X, centers, *, precision: str = "auto", stream=None, centers_out=None, 
     lib = load()
     X = _as_points(X)
     n, d = X.shape
-    C = _as_centers(centers, X)
+    C = _as_centers(centers, X, None, d)
     k = C.shape[0]
-    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
-    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    cen = _out(centers_out, X, (k, d), "f64", "centers_out")
+    lab = _out(labels_out, X, (n,), "i32", "labels_out")
     J = ctypes.c_double()
     sh = ctypes.c_double()
     em = ctypes.c_int32()
@@ -828,10 +852,10 @@ def step_noalloc(X, centers, *, stream=None, centers_out=None, labels_out=None):
         raise TypeError("step_noalloc needs X on a CUDA device")
     X = _as_points(X)
     n, d = X.shape
-    C = _as_centers(centers, X)
+    C = _as_centers(centers, X, None, d)
     k = C.shape[0]
-    cen = centers_out if centers_out is not None else _empty(X, (k, d), "f64")
-    lab = labels_out if labels_out is not None else _empty(X, (n,), "i32")
+    cen = _out(centers_out, X, (k, d), "f64", "centers_out")
+    lab = _out(labels_out, X, (n,), "i32", "labels_out")
     J = ctypes.c_double()
     sh = ctypes.c_double()
     em = ctypes.c_int32()

@@ -115,3 +115,28 @@ def test_server_create_without_device_or_bad_args(lib):
     assert lib.kmeans2_server_now(None) == 0.0
     lib.kmeans2_server_destroy(None)
     assert km.strerror(1) == "pending"
+
+
+def test_binding_rejects_mismatched_buffers_before_any_device_work(lib):
+    """The library writes exactly k*d FP64 centers and n int32 labels and reads
+    k*d FP64 initial centers: the binding refuses buffers of another type, size
+    or layout instead of passing them on."""
+    X = np.random.default_rng(0).standard_normal((100, 4)).astype(np.float32)
+    bad_out = [
+        dict(centers_out=np.empty((5, 4), dtype=np.float32)),       # wrong type
+        dict(centers_out=np.empty((4, 4), dtype=np.float64)),       # too small
+        dict(centers_out=np.empty((4, 10), dtype=np.float64)[:, :5].T),  # not contiguous
+        dict(labels_out=np.empty(99, dtype=np.int32)),              # too small
+        dict(labels_out=np.empty(100, dtype=np.int64)),             # wrong type
+        dict(init_centers=np.zeros((5, 3))),                        # wrong d
+        dict(init_centers=np.zeros((4, 4))),                        # wrong k
+    ]
+    for kw in bad_out:
+        with pytest.raises(ValueError):
+            km.fit(X, 5, 0.5, 0, 1e-6, 10, **kw)
+    ro = np.empty((5, 4), dtype=np.float64)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        km.fit(X, 5, 0.5, 0, 1e-6, 10, centers_out=ro)
+    with pytest.raises(ValueError):
+        km.step(X, np.zeros((5, 3)))                                # centers of another d
