@@ -18,7 +18,9 @@
  *  - Every pointer may be a device pointer (cudaMalloc, torch tensors) or a
  *    host pointer (pageable or pinned); the library checks each with
  *    cudaPointerGetAttributes and stages host buffers through device memory.
- *    Host staging copies are part of the call.
+ *    Host staging copies are part of the call.  Device pointers must belong to
+ *    the current device (the one the call runs on): the kernels address them
+ *    directly, and another GPU's memory is not supported.
  *  - The caller owns every buffer it passes.  The library allocates only
  *    scratch (stream-ordered, from the device's default memory pool) and
  *    frees it before returning.

@@ -311,6 +311,18 @@ def _stream_of(X, stream):
     return None
 
 
+def _check_devices(X, *bufs):
+    """Every CUDA tensor of a call must live on the device the call runs on
+    (X's device, else the current one): the kernels read and write them
+    directly, and another GPU's memory is not addressable without peer access."""
+    dev = X.device if (_is_torch(X) and X.is_cuda) else None
+    if dev is None and torch.cuda.is_available():
+        dev = torch.device("cuda", torch.cuda.current_device())
+    for b in bufs:
+        if _is_torch(b) and b.is_cuda and b.device != dev:
+            raise ValueError(f"a CUDA tensor on {b.device} was passed to a call running on {dev}")
+
+
 class _device_of:
     """Make X's device current for the call (the library uses the current device)."""
 
@@ -363,6 +375,7 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
     C0 = _as_centers(init_centers, X, k, d)
     cen = _out(centers_out, X, (k, d), "f64", "centers_out")
     lab = _out(labels_out, X, (n,), "i32", "labels_out")
+    _check_devices(X, C0, cen, lab)
     opt = Options()
     lib.kmeans2_default_options(ctypes.byref(opt))
     opt.precision = PRECISION[precision]
@@ -420,6 +433,7 @@ def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_i
     C0 = _as_centers(init_centers, X, k, d)
     cen = _out(centers_out, None, (k, d), "f64", "centers_out")
     lab = _out(labels_out, None, (n,), "i32", "labels_out")
+    _check_devices(X, C0, cen, lab)
     opt = Options()
     lib.kmeans2_default_options(ctypes.byref(opt))
     opt.precision = PRECISION["fp32"]
@@ -452,6 +466,7 @@ def fit_sharded(X, k: int, subset_fraction: float, seed: int, tol: float, max_it
     C0 = _as_centers(init_centers, X, k, d)
     cen = _out(centers_out, X, (k, d), "f64", "centers_out")
     lab = _out(labels_out, X, (n,), "i32", "labels_out")
+    _check_devices(X, C0, cen, lab)
     opt = Options()
     lib.kmeans2_default_options(ctypes.byref(opt))
     opt.precision = PRECISION[precision]
@@ -490,6 +505,7 @@ class Shard:
         E = int(lib.kmeans2_shard_exchange_elems(self.d, self.k))
         self.xbuf = torch.zeros(E, dtype=torch.int64, device=self.device)
         self._C0 = _as_centers(init_centers, self.X, self.k, self.d)
+        _check_devices(self.X, self._C0)
         opt = Options()
         lib.kmeans2_default_options(ctypes.byref(opt))
         opt.precision = PRECISION[precision]
@@ -647,6 +663,7 @@ class Server:
         n, d = X.shape
         cen = _out(centers_out, X, (k, d), "f64", "centers_out")
         lab = _out(labels_out, X, (n,), "i32", "labels_out")
+        _check_devices(X, cen, lab)
         job = Job(X=_ptr(X), n=n, d=d, k=int(k), subset_fraction=float(subset_fraction),
                   seed=int(seed) & (2**64 - 1), tol=float(tol), max_iter=int(max_iter), reserved=0,
                   centers_out=_ptr(cen), labels_out=_ptr(lab))
@@ -775,6 +792,8 @@ def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: floa
     device centers and labels) and the status code."""
     lib = load()
     cnt = len(Xs)
+    if cnt == 0:
+        return [], 0
 
     def per_job(v):
         return list(v) if isinstance(v, (list, tuple)) else [v] * cnt
@@ -785,6 +804,8 @@ def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: floa
     for j, X in enumerate(Xs):
         if not (_is_torch(X) and X.is_cuda):
             raise TypeError("fit_batched needs CUDA tensors")
+        if X.device != Xs[0].device:
+            raise ValueError("fit_batched needs every job's X on the same device")
         X = _as_points(X)
         n, d = X.shape
         cen = _empty(X, (ks[j], d), "f64")
@@ -827,6 +848,7 @@ def step(X, centers, *, precision: str = "auto", stream=None, centers_out=None, 
     k = C.shape[0]
     cen = _out(centers_out, X, (k, d), "f64", "centers_out")
     lab = _out(labels_out, X, (n,), "i32", "labels_out")
+    _check_devices(X, C, cen, lab)
     J = ctypes.c_double()
     sh = ctypes.c_double()
     em = ctypes.c_int32()
@@ -856,6 +878,7 @@ def step_noalloc(X, centers, *, stream=None, centers_out=None, labels_out=None):
     k = C.shape[0]
     cen = _out(centers_out, X, (k, d), "f64", "centers_out")
     lab = _out(labels_out, X, (n,), "i32", "labels_out")
+    _check_devices(X, C, cen, lab)
     J = ctypes.c_double()
     sh = ctypes.c_double()
     em = ctypes.c_int32()

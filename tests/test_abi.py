@@ -140,3 +140,7 @@ def test_binding_rejects_mismatched_buffers_before_any_device_work(lib):
         km.fit(X, 5, 0.5, 0, 1e-6, 10, centers_out=ro)
     with pytest.raises(ValueError):
         km.step(X, np.zeros((5, 3)))                                # centers of another d
+
+
+def test_batched_binding_accepts_an_empty_job_list(lib):
+    assert km.fit_batched([], [], 0.1, [], 1e-6, 10) == ([], 0)
