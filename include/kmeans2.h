@@ -541,8 +541,9 @@ KMEANS2_API int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_
 KMEANS2_API int64_t kmeans2_subset_size(int64_t n, int32_t k, double subset_fraction);
 
 /*
- * kmeans2_sample -- the random draws of the Algorithm ("S_n = per% of S_n",
- * "Select X_c from S_n randomly"), computed on the GPU.
+ * kmeans2_sample -- the Algorithm's two random draws (the fast-stage subset
+ * S_s, a per% share of S_n, and the initial centers picked at random from
+ * it), computed on the GPU.
  *
  * SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) is used as a counter-based
  * generator: key_i = mix64(seed + (i+1) * 0x9E3779B97F4A7C15).  S_s is the set

@@ -9,13 +9,13 @@ compiles it with gcc and marshals numpy arrays through ctypes.  Each function
 cites the passage of the paper (arXiv 1108.1351) it follows:
 
 * :func:`sample` -- the fast-stage subset S_s and the initial centers
-  (Algorithm: "per% of S_n", "select X_c from S_n randomly"; Section 2).
+  (the Algorithm's per% subset and its random initial centers; Section 2).
 * :func:`assign` -- squared distance (Eq. 1 without the root, Algorithm) and
   nearest-center label.
 * :func:`lloyd_step` -- one Lloyd iteration (Section 4.1): assignment, J
   (Eq. 3), means, largest center movement.
 * :func:`lloyd_stage` / :func:`fit` -- the stage loop and the two-stage fit
-  (Algorithm; Section 2 "the centers of the slow stage start with c_i").
+  (Algorithm; Section 2: the slow stage starts from the fast stage's centers).
 """
 from __future__ import annotations
 

@@ -8,8 +8,8 @@
  *
  * What it computes, and where the paper says so:
  *   - sampling of the fast-stage subset S_s and of the initial centers
- *     (Section 2, Algorithm: "per% of S_n", "select X_c randomly"; Section 2:
- *     centers drawn at random from the data);
+ *     (Section 2 and the Algorithm: a per% share of S_n, centers drawn at
+ *     random from the data);
  *   - the "modified distance" (Eq. 1 without the square root, Algorithm),
  *     the nearest-center assignment with the lowest index winning ties;
  *   - the objective J (Eq. 3; WCSS of Eqs. 6-7 read with squared norms);
@@ -26,9 +26,10 @@
  *   - The Algorithm prints the mean step only after the fast loop; Lloyd's
  *     method (Section 4.1) updates the centers in every iteration, so each
  *     iteration here is: assign, J, update, stop test.
- *   - "While J_f <= mu" is read as "until max_j ||c_j' - c_j||_2 <= tol"; the
- *     iteration that detects convergence is counted (Table 1 shows old = new
- *     centers in the last counted iteration of each stage).
+ *   - The loop condition on J and mu is read as: stop once
+ *     max_j ||c_j' - c_j||_2 <= tol; the iteration that detects convergence
+ *     is counted (Table 1 shows old = new centers in the last counted
+ *     iteration of each stage).
  *   - Subset size m = min(n, max(k, ceil(f*n))), ceil taken of the double
  *     product f*n.
  *   - Random choice: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a

@@ -788,7 +788,7 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
                                                                : cudaMemcpyHostToDevice, s));
     }
     if (o.start_stage == 0) {
-        // fast stage on S_s (Algorithm: "S_n = per% of S_n", "Select X_c from S_n randomly")
+        // fast stage on S_s (Algorithm: a per% subset, initial centers drawn from it)
         long long* subset = nullptr;
         long long* pos = nullptr;
         float* Xs = nullptr;

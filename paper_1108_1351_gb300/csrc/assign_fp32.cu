@@ -1,7 +1,7 @@
 // assign_fp32.cu -- fused distance + nearest-center + cluster-sum kernels, FP32 on
-// the CUDA cores (the hot loop of the Algorithm: "Calculate the modified
-// distance", "Find minimum of d", "Assign the cluster number"; the sums feed the
-// mean step of Lloyd's method, Section 4.1).
+// the CUDA cores (the hot loop of the Algorithm: the squared distance of each
+// point to each center, the smallest one, and the point's new cluster; the sums
+// feed the mean step of Lloyd's method, Section 4.1).
 //
 // The argmin needs only D_j = ||c_j||^2 - 2 x.c_j (||x||^2 is common to all
 // centers).  Each kernel keeps the best and second-best D per point; when the

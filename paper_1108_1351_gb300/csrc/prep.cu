@@ -1,7 +1,7 @@
 // prep.cu -- the small kernels around the distance kernels:
 //   maxabs      max |x| over a stage's data (fixed-point scale, finiteness check)
-//   gather      X_s = rows of X at the subset indices (Algorithm, "per% of S_n")
-//   init        initial centers = chosen points of X_s (Algorithm, "Select X_c")
+//   gather      X_s = rows of X at the subset indices (Algorithm: the per% subset)
+//   init        initial centers = chosen points of X_s (Algorithm: random initial centers)
 //   center_prep FP32 / transposed copies of the FP64 centers and ||c||^2
 //   stage_init  fixed-point scales and loop state of one stage
 //   finalize    new centers = cluster means (Lloyd's method, Section 4.1), the

@@ -1,5 +1,5 @@
-// sample.cu -- the random draws of the Algorithm ("S_n = per% of S_n",
-// "Select X_c from S_n randomly"), done on the GPU.
+// sample.cu -- the Algorithm's two random draws (the per% subset S_s and the
+// initial centers picked at random from it), done on the GPU.
 //
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) serves as a counter-based
 // generator: key_i = mix64(seed + (i + 1) * GAMMA).  mix64 is a bijection, so

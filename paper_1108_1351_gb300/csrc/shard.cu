@@ -4,7 +4,7 @@
 // centers.  The ranks exchange data at three kinds of points, each an
 // all-reduce of one small buffer that the caller performs (NCCL, gloo, or the
 // in-process reduction of kmeans2_fit_sharded):
-//   * the initial centers (Algorithm, "Select X_c from S_n randomly"): every
+//   * the initial centers (the Algorithm's random draw from S_s): every
 //     rank writes the chosen rows of X_s that it owns and -0.0 elsewhere; the
 //     FP64 sum is exact in any order (x + -0.0 = x for every x);
 //   * max |x| of a stage's points, which fixes the stage's fixed-point scales;

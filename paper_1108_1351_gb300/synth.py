@@ -7,7 +7,7 @@ tensors from here, so neither side regenerates the other's inputs.
 The paper's datasets (a 150-point 3-D set, UCI "Synthetic Control Chart",
 its unnamed "Synthetic" 100,000 x 10 and 1M-10M x 12 sets) are not available;
 these generators stand in for them with the shapes the paper uses
-(Section 4: "random and uniform clusters"; Section 6: 100,000 x 10;
+(Section 4: randomly placed clusters of uniform size; Section 6: 100,000 x 10;
 Section 6.1: up to 10M points in 12-D; Abstract: 500M+ points).
 
 Mixture parameters (means, rotations, weights, concentrations) are drawn on
