@@ -16,10 +16,9 @@
  *   - the center update as the mean of each cluster (Lloyd's method,
  *     Section 4.1), an empty cluster keeping its center;
  *   - the stopping test on the largest center movement (Section 5, Section 6:
- *     mu is the required accuracy, measured as center movement);
+ *     mu is the accuracy asked for, measured as center movement);
  *   - the fast stage on S_s, then the slow stage on S_n started from the fast
- *     stage's final centers (Algorithm; Section 2, "the centers of the slow
- *     stage start with c_i"; Section 5).
+ *     stage's final centers (Algorithm; Section 2; Section 5).
  *
  * Readings where the paper is silent or garbled (each also listed in the
  * design notes):
