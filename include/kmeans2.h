@@ -535,7 +535,7 @@ KMEANS2_API int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_
 
 /*
  * kmeans2_subset_size -- m = min(n, max(k, ceil(per*n))), the size of S_s
- * (Algorithm: "S_n = per% of S_n"; at least k points so that k distinct
+ * (the Algorithm's per% share of the data; at least k points so that k distinct
  * initial centers exist).  Host only; returns -1 on invalid arguments.
  */
 KMEANS2_API int64_t kmeans2_subset_size(int64_t n, int32_t k, double subset_fraction);
