@@ -116,9 +116,16 @@ class ClockSampler:
             self.proc.kill()
         if self.th:
             self.th.join(timeout=2)
+        return self.summarize(self.lines)
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, max clock and the throttle reasons seen Active in
+        nvidia-smi CSV rows of FIELDS (malformed rows skipped); None if no row
+        parses."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue

@@ -234,3 +234,20 @@ def test_data_parallel_driver_gloo_world2():
         assert iters == (o["iters_fast"], o["iters_slow"])
         sub, _ = oracle.sample(len(X), k, 0.2, 7)
         assert maxabs == [int(np.abs(X[sub]).max() * 8), int(np.abs(X).max() * 8)]
+
+
+def test_clock_summary_of_nvidia_smi_rows():
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+        "garbage line",                                                               # skipped
+    ]
+    s = bench.ClockSampler.summarize(rows)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+    assert bench.ClockSampler.summarize(["x"]) is None
+    hot = rows[:1] + ["0, 1500, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active"]
+    assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
