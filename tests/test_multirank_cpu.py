@@ -251,3 +251,25 @@ def test_clock_summary_of_nvidia_smi_rows():
     assert bench.ClockSampler.summarize(["x"]) is None
     hot = rows[:1] + ["0, 1500, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active"]
     assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_traffic_line_is_used_only_for_the_source_it_was_measured_on(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import hashlib
+    import bench
+    (tmp_path / "paper_1108_1351_gb300" / "csrc").mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "paper_1108_1351_gb300" / "csrc" / "assign_bf16.cu"
+    src.write_text("// kernel v1\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    (tmp_path / "profiles" / "x.md").write_text(f"`traffic-per-point: assign_bf16 520.0 {sha}`\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+
+    class Prof:
+        assign_launches = 4
+        assign_bytes = 4 * (4.0 * 128 * 1000)      # four launches of 1000 points, d = 128
+
+    assert bench.traffic_of("assign_bf16", Prof, 128) == 520.0 * 1000
+    assert bench.traffic_of("assign_small<8>", Prof, 8) is None       # no line for it
+    src.write_text("// kernel v2\n")                                   # source changed since
+    assert bench.traffic_of("assign_bf16", Prof, 128) is None
