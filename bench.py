@@ -400,6 +400,8 @@ def run_ours(args, cfg):
                    "l2": "inputs larger than L2 (X is %.1f GB)" % (n * d * 4 / 1e9)
                    if n * d * 4 > 2e8 else "inputs smaller than L2"},
         "time_to_converge_s": (ms_max / args.steps) / 1e3,
+        # each timed call's own wall time (host clock inside the library; rank 0)
+        "time_to_converge_median_s": statistics.median(r.seconds for r in results) if results else None,
         "fit": {"J": r0.J, "iters_fast": r0.iters_fast, "iters_slow": r0.iters_slow,
                 "converged_fast": r0.converged_fast, "converged_slow": r0.converged_slow,
                 "rechecked_points": r0.rechecked_points, "distance_evals": r0.distance_evals,
