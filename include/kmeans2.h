@@ -45,8 +45,14 @@
  *    max|x| < 2^E (so a center is off the exact mean by at most 2^-(F+1) per
  *    coordinate, plus the FP64 rounding of the division), which makes every
  *    mode deterministic: results do not depend on thread scheduling.
- *  - J is evaluated as sum_i ||x_i||^2 - sum_j (2 c_j . S_j - N_j ||c_j||^2)
- *    from exact sums, in FP64.
+ *  - J (Eq. 3) is formed on the same fixed-point values, without cancellation:
+ *    J = W + M with W = (sum_i ||s_i||^2 - sum_j ||s_j||^2 / N_j) 2^-2F, where s
+ *    are the integer coordinates and s_j their exact cluster sums (exact
+ *    256-bit integer arithmetic, one final rounding), and M = sum_j N_j
+ *    ||c_j - mu_j||^2 with each displacement from the exact mean mu_j formed in
+ *    double-word arithmetic.  J therefore equals sum_i ||x_i - c_label(i)||^2
+ *    to a few FP64 ulps relative; only coordinates with |x| < 2^(E-23), which
+ *    lie off the 2^-F grid, can add more (at most 2^(2E-46) each).
  */
 #ifndef KMEANS2_H
 #define KMEANS2_H
@@ -218,7 +224,8 @@ KMEANS2_API int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32
  * cluster sums and near-tie list, and a replicated copy of the centers.  Per
  * Lloyd iteration (Section 4.1) the ranks all-reduce the integer partials of
  * the centroid update -- sum_i x_i split into two int64 words, N_j and, in a
- * stage's first iteration, sum ||x||^2 -- and every rank runs the same
+ * stage's first iteration, the exact sum of the squared fixed-point
+ * coordinates (four int64 words) -- and every rank runs the same
  * finalize on the totals.  Integer sums do not depend on the order of the
  * reduction, so labels, centers, J and iteration counts equal those of
  * kmeans2_fit on the whole of X, bit for bit, for any number of ranks and any
@@ -242,7 +249,7 @@ typedef struct kmeans2_exchange {
     int64_t count;       /* 8-byte elements of the exchange buffer to reduce, from element 0 */
 } kmeans2_exchange;
 
-/* 8-byte elements the exchange buffer must hold for (d, k): 2 k d + k + 5;
+/* 8-byte elements the exchange buffer must hold for (d, k): 2 k d + k + 7;
  * -1 for d < 1 or k < 1. */
 KMEANS2_API int64_t kmeans2_shard_exchange_elems(int32_t d, int32_t k);
 
@@ -510,10 +517,12 @@ KMEANS2_API int kmeans_step(const float* X, int64_t n, int32_t d, int32_t k, con
  * device memory is entirely owned by its own caching allocator or memory pool,
  * where a stray allocation could fail or fragment that pool, or a latency-
  * critical loop that must not wait on the allocator.  This entry point runs
- * the same kernels as kmeans_step but takes its scratch from one fixed device
- * array of 24 MiB compiled into the library, which every GPU that loads the
- * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
- * other allocating routine.
+ * kmeans_step's CUDA-core FP32 form (the form whose scratch fits the array for
+ * every shape within the limits below; the tensor-core forms would need a copy
+ * of X) and takes its scratch from one fixed device array of 24 MiB compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its labels, centers and J equal kmeans_step's in any form.
  *
  *  X, centers_in, centers_out, labels_out: DEVICE memory on the current device
  *                (X 16-byte aligned); the caller still owns and passes them.

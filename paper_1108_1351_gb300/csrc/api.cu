@@ -214,7 +214,7 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     KM2_TRY(ws.alloc((void**)&w.acc.cnt, (size_t)k * 8, s));
     KM2_TRY(ws.alloc((void**)&w.st, sizeof(StageState), s));
     KM2_TRY(ws.alloc((void**)&w.list, (size_t)(list_cap > 0 ? list_cap : 1) * sizeof(int), s));
-    KM2_TRY(ws.alloc((void**)&w.clus, (size_t)4 * k * sizeof(double), s));
+    KM2_TRY(ws.alloc((void**)&w.clus, (size_t)kClusSlots * k * sizeof(double), s));
     KM2_TRY(ws.alloc((void**)&w.traj_J, (size_t)max_iter * sizeof(double), s));
     KM2_TRY(ws.alloc((void**)&w.traj_shift, (size_t)max_iter * sizeof(double), s));
     KM2_CUDA(cudaMemsetAsync(w.c.c32t, 0, (size_t)w.c.dpad * w.c.kpad * sizeof(float), s));
@@ -427,6 +427,7 @@ int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, dou
     KM2_CUDA(cudaMemsetAsync(w.acc.cnt, 0, (size_t)w.c.k * 8, s));
     KM2_TRY(launch_center_prep(w.c, w.st, s));
     KM2_TRY(launch_stage_init(w.st, d, tol, max_iter, s));
+    KM2_TRY(launch_qsum(X, n, d, w.st, s, sm_count));
     KM2_TRY(prepare_stage_points(X, n, d, w, *w.ws, s));
     if (use_graph && !prof)
         KM2_TRY(run_loop_graph(X, n, d, w, labels, s, sm_count));
@@ -595,7 +596,7 @@ uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fr
     add(K * 8);
     add(sizeof(StageState));
     add(N * 4);
-    add(4 * K * 8);
+    add((unsigned long long)kClusSlots * K * 8);
     add(2 * (unsigned long long)max_iter * 8);
     if (form == KMEANS2_PRECISION_BF16) add(bf16_cb_bytes(d, k));
     if (labels_on_host) add(N * 4);
@@ -728,8 +729,13 @@ int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
     KM2_TRY(noalloc_scratch(&arena));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceScratch ws(s, arena, kNoAllocBytes);
+    // The CUDA-core form: its scratch (the near-tie list, n ints, plus O(k d)
+    // center copies and sums) fits the array over the whole stated range; the
+    // tensor-core forms would also need a per-call copy of X (about 4 n d
+    // bytes for BF16), which it cannot hold.  Every form returns the same
+    // labels, centers and J.
     Workspace w;
-    KM2_TRY(choose_form(KMEANS2_PRECISION_AUTO, d, k, X, &w.form));
+    w.form = KMEANS2_PRECISION_FP32;
     KM2_TRY(alloc_workspace(w, ws, n, k, d, 1, s));
     KM2_CUDA(cudaMemcpyAsync(w.c.c64, centers_in, sizeof(double) * (size_t)k * d,
                              cudaMemcpyDeviceToDevice, s));
@@ -1053,6 +1059,7 @@ int kmeans2_fit_streamed(const float* X, int64_t n, int32_t d, int32_t k, double
         NvtxRange iteration_range("kmeans2 streamed iteration");
         KM2_TRY(stream_pass(cs, s, [&](long long c, const float* Xc, long long rows) {
             int* lab = labels + c * chunk;
+            if (it == 0) KM2_TRY(launch_qsum(Xc, rows, d, w.st, s, ws.sm_count));
             KM2_TRY(launch_assign(Xc, rows, d, w, lab, s, ws.sm_count));
             KM2_TRY(launch_recheck(Xc, d, w.c, lab, w.list, w.st, w.acc, s, ws.sm_count));
             return launch_recheck_reset(w.st, s);

@@ -81,13 +81,15 @@ int sample_device(long long n, int k, long long m, unsigned long long seed, long
 // max |x| of n rows of d values, into st->maxabs_bits.
 int launch_maxabs(const float* X, long long n, int d, StageState* st, cudaStream_t s,
                   int sm_count);
+// Exact sum of s^2 over n rows of d values into st->q (after stage_init: needs F).
+int launch_qsum(const float* X, long long n, int d, StageState* st, cudaStream_t s, int sm_count);
 int launch_gather(const float* X, int d, const long long* subset, long long m, float* Xs,
                   StageState* st, cudaStream_t s, int sm_count);
 int launch_init_centers(const float* Xs, int d, const long long* pos, int k, double* c64,
                         cudaStream_t s);
 int launch_center_prep(const Centers& c, StageState* st, cudaStream_t s);
 int launch_stage_init(StageState* st, int d, double tol, int max_iter, cudaStream_t s);
-// clus: 4*k doubles of scratch; tr: the stage's optional per-iteration records.
+// clus: kClusSlots*k doubles of scratch; tr: the stage's optional per-iteration records.
 int launch_finalize(const Accum& acc, const Centers& c, StageState* st, const TrajDev& tr,
                     double* clus, unsigned long long cond_handle, int use_cond, cudaStream_t s);
 int launch_recheck(const float* X, int d, const Centers& c, int* labels, const int* list,

@@ -380,7 +380,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
         const int quarter = warp & 3;                     // TMEM lanes 32 * (warp % 4) ...
         const int row = 32 * quarter + lane;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
-        const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float scaleF = st->scaleF;
         const float thr_base = 2.0f * st->cmax2;
         int* rq = rqs[ew];
         int rq_n = 0;                                      // warp-uniform queue length
@@ -396,8 +396,6 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             rq_n = 0;
         };
         uint32_t phase = 0u;                 // bit s: parity of accumulator 2 g + s's next use
-        long long qloc = 0;
-        long long done = 0;
         bool ok = true;
         for (long long i = g; i < cnt && ok; i += kEpiGroups) {
             float B1 = INFINITY, B2 = INFINITY;
@@ -446,14 +444,6 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 if (!__all_sync(0xffffffffu, w)) break;
             }
             const bool in_ring = (long long)row < ((a.n - tile * kRows) & ~3ll);
-            if ((done & 255) == 255) {
-                // keep each ||x||^2 partial below 2^62: fold it every 256 tiles
-                long long qs = qloc;
-                for (int o = 16; o; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
-                if (lane == 0 && qs) split_add(&st->q_lo, &st->q_hi, qs);
-                qloc = 0;
-            }
-            ++done;
             const float xx = valid ? (in_ring ? side.xn2[r][row] : __ldg(a.xn2 + p)) : 0.0f;
             const float thr = a.kappa * (thr_base + xx) + a.kpack * (fabsf(B1) + fabsf(B2));
             const bool flag = valid && (B2 - B1 <= thr);
@@ -477,35 +467,26 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
                 labels[p] = BI;
             }
-            // Sums (and ||x||^2 in full mode): one row at a time, the warp's lanes
-            // over its coordinates, so each atomic instruction touches a few
-            // contiguous lines of s_lo / s_hi and each row is read coalesced.
+            // Sums: one moved row at a time, the warp's lanes over its
+            // coordinates, so each atomic instruction touches a few contiguous
+            // lines of s_lo / s_hi and each row is read coalesced.
             const unsigned mmov = __ballot_sync(0xffffffffu, moved);
-            const unsigned msq = mode == kModeFull ? __ballot_sync(0xffffffffu, valid) : 0u;
-            for (unsigned m = mmov | msq; m; m &= m - 1) {
+            for (unsigned m = mmov; m; m &= m - 1) {
                 const int src = __ffs(m) - 1;
                 const long long pj = __shfl_sync(0xffffffffu, p, src);
                 const int bj = __shfl_sync(0xffffffffu, BI, src);
                 const int oj = __shfl_sync(0xffffffffu, old, src);
-                const bool mv = (mmov >> src) & 1u, sq = (msq >> src) & 1u;
                 const float* xr = a.X + pj * d;
                 for (int t = lane; t < d; t += 32) {
-                    const float xv = __ldg(xr + t);
-                    if (sq) qloc += sq_fixed(xv, scaleG);
-                    if (mv) {
-                        const long long val = to_fixed(xv, scaleF);
-                        split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, val);
-                        if (oj >= 0)
-                            split_add(acc.s_lo + (long long)oj * d + t,
-                                      acc.s_hi + (long long)oj * d + t, -val);
-                    }
+                    const long long val = to_fixed(__ldg(xr + t), scaleF);
+                    split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, val);
+                    if (oj >= 0)
+                        split_add(acc.s_lo + (long long)oj * d + t,
+                                  acc.s_hi + (long long)oj * d + t, -val);
                 }
             }
         }
         rq_flush();
-        // one partial of ||x||^2 per warp (each below 2^62)
-        for (int o = 16; o; o >>= 1) qloc += __shfl_xor_sync(0xffffffffu, qloc, o);
-        if (lane == 0 && qloc) split_add(&st->q_lo, &st->q_hi, qloc);
     }
     tc::fence_before_sync();
     __syncthreads();

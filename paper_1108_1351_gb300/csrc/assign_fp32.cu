@@ -141,12 +141,10 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
     int* sl = reinterpret_cast<int*>(sx + (size_t)C::TILE * D);  // TILE old labels
     long long* sacc = reinterpret_cast<long long*>(sl + C::TILE);  // k * D (if use_sacc)
     int* scnt = reinterpret_cast<int*>(sacc + (size_t)k * D);       // k (if use_sacc)
-    __shared__ unsigned long long sq;
 
     if (st->error) return;
     const int mode = st->mode;
     const float scaleF = st->scaleF;
-    const float scaleG = st->scaleG;
     const float thr_base = 2.0f * st->cmax2;
     const int tid = threadIdx.x;
 
@@ -162,7 +160,6 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
         for (int e = tid; e < k * D; e += kThreads) sacc[e] = 0;
         for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
     }
-    if (tid == 0) sq = 0;
     __syncthreads();
 
     const long long ntiles = (n + C::TILE - 1) / C::TILE;
@@ -183,7 +180,6 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
     };
     if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0u);
 
-    long long qloc = 0;
     int it = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const long long base = tile * C::TILE;
@@ -267,10 +263,6 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
             const bool valid = i < n;
             const float thr = kappa * (thr_base + xn2[p]) + kpack * (fabsf(B1[p]) + fabsf(B2[p]));
             const bool flag = valid && (B2[p] - B1[p] <= thr);
-            if (mode == kModeFull && valid) {
-#pragma unroll
-                for (int t = 0; t < D; ++t) qloc += sq_fixed(x[p][t], scaleG);
-            }
             recheck_append(flag, (int)i, list, &st->recheck_count);
             if (valid && !flag && label_ok(BI[p], k, st) && old_label_ok(oldl[p], k, st)) {
                 const int lab = BI[p];
@@ -307,8 +299,6 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
         // Static flush schedule: at most FLUSH_TILES tiles (2^16 points) per partial.
         const bool last = tile + gridDim.x >= ntiles;
         if ((it + 1) % C::FLUSH_TILES == 0 || last) {
-            if (qloc) atomicAdd(&sq, (unsigned long long)qloc);
-            qloc = 0;
             __syncthreads();
             if (use_sacc) {
                 for (int e = tid; e < k * D; e += kThreads) {
@@ -325,10 +315,6 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
                         scnt[e] = 0;
                     }
                 }
-            }
-            if (tid == 0) {
-                if (sq) split_add(&st->q_lo, &st->q_hi, (long long)sq);
-                sq = 0;
             }
             __syncthreads();
         }
@@ -349,11 +335,9 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
     if (st->error) return;
     const int mode = st->mode;
     const float scaleF = st->scaleF;
-    const float scaleG = st->scaleG;
     const float c2x2 = 2.0f * st->cmax2;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int lane = tid & 31;
     const int kpad = c.kpad;
     const int nct = kpad / BN;
     const int nks = c.dpad / BK;
@@ -458,7 +442,6 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
                 top2_merge(b1[r], b2[r], bi[r], o1, o2, oi);
             }
         }
-        long long qloc = 0;
         int olds[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -474,8 +457,6 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
             recheck_append(flag && tx == 0, (int)i, list, &st->recheck_count);
             if (!valid) continue;
             const float* xr = X + i * d;
-            if (mode == kModeFull)
-                for (int t = tx; t < d; t += 16) qloc += sq_fixed(__ldg(xr + t), scaleG);
             if (flag) continue;
             const int lab = bi[r];
             if (!label_ok(lab, c.k, st)) continue;
@@ -493,10 +474,6 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
                 if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
                 labels[i] = lab;
             }
-        }
-        if (mode == kModeFull) {
-            for (int o = 16; o; o >>= 1) qloc += __shfl_xor_sync(0xffffffffu, qloc, o);
-            if (lane == 0 && qloc) split_add(&st->q_lo, &st->q_hi, qloc);
         }
     }
 }

@@ -422,7 +422,7 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
         const int quarter = warp & 3;                      // TMEM lanes 32 * (warp % 4) ...
         const int row = 32 * quarter + lane;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
-        const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float scaleF = st->scaleF;
         const float thr_base = 2.0f * st->cmax2;
         int* rq = reinterpret_cast<int*>(smem + L.rq_off) + ew * kRecheckQ;
         int rq_n = 0;                                      // warp-uniform queue length
@@ -442,7 +442,6 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
         // per-warp partials hold at most 2^16 points: fold them every 2^16 / (32 T) units
         const long long flush_units = kFlushPoints / (32 * T);
         uint32_t phase = 0u;                 // bit s: parity of accumulator g NB + s's next use
-        long long qloc = 0;
         long long done = 0;
         for (long long u = g; u < units; u += 2) {
             const int slot = (int)((u >> 1) % NB);
@@ -509,10 +508,6 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                 for (int e = 0; e < D; ++e) xn2 = fmaf(x[e], x[e], xn2);
                 const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1[t]) + fabsf(B2[t]));
                 const bool flag = valid && (B2[t] - B1[t] <= thr);
-                if (mode == kModeFull && valid) {
-#pragma unroll
-                    for (int e = 0; e < D; ++e) qloc += sq_fixed(x[e], scaleG);
-                }
                 {
                     const unsigned m = __ballot_sync(0xffffffffu, flag);
                     if (m) {
@@ -562,10 +557,6 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
             // static flush schedule: at most 2^16 points per partial
             ++done;
             if (done % flush_units == 0 || u + 2 >= units) {
-                long long qs = qloc;
-                for (int o = 16; o; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
-                if (lane == 0 && qs) split_add(&st->q_lo, &st->q_hi, qs);
-                qloc = 0;
                 if (L.sacc) {
                     __syncwarp();
                     for (int e = lane; e < k * D; e += 32) {

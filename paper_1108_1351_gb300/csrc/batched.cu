@@ -51,7 +51,7 @@ struct BatchInst {
     long long* subset;       // m
     long long* pos;          // k
     long long* seltmp;       // k
-    double* clus;            // 4 k
+    double* clus;            // kClusSlots k
     Centers c;
     Accum acc;
     StageState st;
@@ -210,8 +210,7 @@ __global__ void __launch_bounds__(kThreads) batch_reset_kernel(BatchInst* insts)
     for (long long e = threadIdx.x; e < kd; e += blockDim.x) { I->acc.s_lo[e] = 0; I->acc.s_hi[e] = 0; }
     for (int j = threadIdx.x; j < I->k; j += blockDim.x) I->acc.cnt[j] = 0;
     if (threadIdx.x == 0) {
-        I->st.q_lo = 0;
-        I->st.q_hi = 0;
+        for (int w = 0; w < 4; ++w) I->st.q[w] = 0ull;
         I->st.recheck_count = 0;
     }
 }
@@ -249,7 +248,7 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
     float* ss = sc + kMaxK * DC;                              // kMaxK: ||c||^2
     long long* sacc = reinterpret_cast<long long*>(ss + kMaxK);
     int* scnt = reinterpret_cast<int*>(sacc + kMaxK * DC);
-    __shared__ unsigned long long sq;
+    __shared__ unsigned long long sq[4];     // this item's sum of s^2 (wide_add4 words)
     __shared__ int s_item;
     const int tid = threadIdx.x;
 
@@ -274,7 +273,7 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
         const int d = I->d, k = I->k;
         const int kc = (k + 31) & ~31;
         const int mode = st->mode;
-        const float scaleF = st->scaleF, scaleG = st->scaleG;
+        const float scaleF = st->scaleF;
         const float thr_base = 2.0f * st->cmax2;
         const float kappa = tie_kappa(d);
 
@@ -288,10 +287,10 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
             for (int e = tid; e < k * DC; e += kThreads) sacc[e] = 0;
             for (int e = tid; e < k; e += kThreads) scnt[e] = 0;
         }
-        if (tid == 0) sq = 0;
+        if (tid < 4) sq[tid] = 0;
         __syncthreads();
 
-        long long qloc = 0;
+        unsigned __int128 qloc = 0;     // full mode: exact sum of s^2 (J, Eq. 3)
         const long long t_end = min(tiles, (long long)w.tile0 + w.ntile);
         for (long long tile = w.tile0; tile < t_end; ++tile) {
             for (int sub = 0; sub < C::NSUB; ++sub) {
@@ -367,7 +366,7 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
                     if (mode == kModeFull && valid) {
 #pragma unroll
                         for (int t = 0; t < DC; ++t)
-                            if (t < d) qloc += sq_fixed(x[p][t], scaleG);
+                            if (t < d) qloc += sq_fixed(x[p][t], scaleF);
                     }
                     recheck_append(flag, (int)i, I->list, &st->recheck_count);
                     if (valid && !flag) {
@@ -406,7 +405,10 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
                 }
             }
         }
-        if (qloc) atomicAdd(&sq, (unsigned long long)qloc);
+        if (mode == kModeFull) {
+            qloc = warp_sum_u128(qloc);
+            if ((tid & 31) == 0 && qloc) wide_add4(sq, qloc);
+        }
         __syncthreads();
         if (C::SACC) {
             for (int e = tid; e < k * DC; e += kThreads) {
@@ -418,7 +420,7 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
             for (int j = tid; j < k; j += kThreads)
                 if (scnt[j]) atomicAdd(I->acc.cnt + j, (unsigned long long)(long long)scnt[j]);
         }
-        if (tid == 0 && sq) split_add(&st->q_lo, &st->q_hi, (long long)sq);
+        if (tid < 4 && sq[tid]) atomicAdd(&st->q[tid], sq[tid]);
     }
 }
 
@@ -630,7 +632,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             const size_t kd = (size_t)J.k * J.d;
             offs[j] = total;
             total += up(m * J.d * 4) + up(m * 4) + up(J.n * 4) + up(J.n * 4) + up(m * 8) +
-                     3 * up((size_t)J.k * 8) + up(4 * (size_t)J.k * 8) + up(kd * 8) + up(kd * 4) +
+                     3 * up((size_t)J.k * 8) + up((size_t)kClusSlots * J.k * 8) + up(kd * 8) + up(kd * 4) +
                      up((size_t)dpad * kpad * 4) + up((size_t)kpad * 4) + 2 * up(kd * 8) +
                      up((size_t)J.k * 8);
             nvec[j] = J.n;
@@ -661,7 +663,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             I.pos = (long long*)take((size_t)J.k * 8);
             I.seltmp = (long long*)take((size_t)J.k * 8);
             take((size_t)J.k * 8);
-            I.clus = (double*)take(4 * (size_t)J.k * 8);
+            I.clus = (double*)take((size_t)kClusSlots * J.k * 8);
             I.c.c64 = (double*)take(kd * 8);
             I.c.c32 = (float*)take(kd * 4);
             I.c.c32t = (float*)take((size_t)dpad * kpad * 4);

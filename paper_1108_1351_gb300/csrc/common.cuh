@@ -1,7 +1,7 @@
 // common.cuh -- definitions shared by the kernels of libkmeans2 (not by the oracle).
 //
 // Exact cluster sums.  Each FP32 coordinate x enters the sums as the integer
-// round(x * 2^F).  The per-stage exponent F = 46 - E, with max|x| < 2^E, keeps
+// s = round(x * 2^F).  The per-stage exponent F = 46 - E, with max|x| < 2^E, keeps
 // one value below 2^46 in magnitude, so an int64 partial over at most
 // kFlushPoints = 2^16 points cannot overflow.  Global sums are kept as two
 // 64-bit words: `lo` accumulates the low 32 bits of every contribution
@@ -9,6 +9,12 @@
 // (int128)hi * 2^32 + lo for any number of contributions below 2^31.  Integer
 // addition is associative, so the sums, the centers and J do not depend on the
 // order in which threads add: every mode is deterministic.
+//
+// The objective J (Eq. 3) is formed from the same integers: sum_i s_i^2 over a
+// stage's coordinates (st->q, exact), the sums S_j and the counts N_j, so that
+// J = W + M with W = sum ||x||^2 - sum_j ||S_j||^2 / N_j (exact integer
+// arithmetic) and M = sum_j N_j ||c_j - S_j / N_j||^2 (each difference formed
+// without cancellation): no term is a difference of large nearly equal sums.
 #pragma once
 
 #include <cstdint>
@@ -24,10 +30,10 @@ constexpr int kModeDelta = 1;           // later iterations: only points whose l
 // the loop.  Written only by the single-thread / single-CTA kernels
 // (stage_init, finalize) except for the atomically updated counters.
 struct StageState {
-    // fixed-point scales (stage_init)
-    int F, G;                     // exponents of the x and ||x||^2 fixed points
-    float scaleF, scaleG;         // 2^F, 2^G
-    double inv_scaleF, inv_scaleG;
+    // fixed-point scale (stage_init)
+    int F;                        // exponent of the coordinate fixed point
+    float scaleF;                 // 2^F
+    double inv_scaleF;            // 2^-F
     unsigned int maxabs_bits;     // max |x| as float bits (atomicMax; NaN/inf sort above)
     int error;                    // nonzero: stage aborted (see kErr*)
     // loop control
@@ -44,9 +50,13 @@ struct StageState {
     long long rechecked_total;
     double J;                     // objective of the last assignment
     double shift;                 // last max center movement
-    double Qtot;                  // sum_i ||x_i||^2 of the stage's points
-    unsigned long long q_lo, q_hi;  // exact fixed-point sum of ||x||^2 (scale 2^G)
+    // sum of s^2 over every coordinate of the stage's points (s = round(x 2^F)),
+    // exact: the value is sum_w q[w] 2^(32 w) (qsum pass, wide_add4)
+    unsigned long long q[4];
 };
+
+// Per-center scratch of finalize, in doubles per center (finalize_center_warp).
+constexpr int kClusSlots = 7;
 
 constexpr int kErrNonFinite = 1;
 constexpr int kErrRange = 2;       // max|x| >= 2^50
@@ -132,13 +142,35 @@ __device__ __forceinline__ double split_value(unsigned long long lo, unsigned lo
     return (double)v * inv_scale;
 }
 
-// ||x||^2 contribution of one coordinate as exact fixed point: x*x = p + e
-// exactly (p = fl(x*x), e = fma(x, x, -p)), each part rounded to the 2^-G grid.
-__device__ __forceinline__ long long sq_fixed(float x, float scaleG)
+// s^2 of one coordinate's fixed-point integer s = to_fixed(x, scale), exactly
+// (|s| < 2^46, so s^2 < 2^92).
+__device__ __forceinline__ unsigned __int128 sq_fixed(float x, float scale)
 {
-    float p = x * x;
-    float e = fmaf(x, x, -p);
-    return __float2ll_rn(p * scaleG) + __float2ll_rn(e * scaleG);
+    const long long v = to_fixed(x, scale);
+    const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+    return (unsigned __int128)a * a;
+}
+
+// Adds v (< 2^128) to a wide accumulator w[0..3] whose value is
+// sum_i w[i] 2^(32 i): piece i of v (32 bits) goes to w[i].  Each word gains
+// less than 2^32 per call, so fewer than 2^31 calls cannot wrap it.
+__device__ __forceinline__ void wide_add4(unsigned long long* w, unsigned __int128 v)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const unsigned long long piece = (unsigned long long)(v >> (32 * i)) & 0xffffffffull;
+        if (piece) atomicAdd(w + i, piece);
+    }
+}
+
+__device__ __forceinline__ unsigned __int128 warp_sum_u128(unsigned __int128 v)
+{
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+        v += ((unsigned __int128)hi << 64) | lo;
+    }
+    return v;
 }
 
 // 3-input minimum (sm_100+ PTX form).

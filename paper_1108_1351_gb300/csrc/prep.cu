@@ -1,5 +1,7 @@
 // prep.cu -- the small kernels around the distance kernels:
 //   maxabs      max |x| over a stage's data (fixed-point scale, finiteness check)
+//   qsum        exact sum of s^2 over a stage's coordinates, s = round(x 2^F)
+//               (the integer that J is formed from, Eq. 3)
 //   gather      X_s = rows of X at the subset indices (Algorithm: the per% subset)
 //   init        initial centers = chosen points of X_s (Algorithm: random initial centers)
 //   center_prep FP32 / transposed copies of the FP64 centers and ||c||^2
@@ -46,6 +48,33 @@ __global__ void maxabs_kernel(const float* __restrict__ X, long long count, int 
     for (long long i = done + tid; i < count; i += stride) m = max(m, abs_bits(__ldg(X + i)));
     m = warp_max_u32(m);
     if ((threadIdx.x & 31) == 0 && m) atomicMax(&st->maxabs_bits, m);
+}
+
+// Exact sum of s^2 over count coordinates, s = to_fixed(x, 2^F) (the same
+// integers the cluster sums add), into st->q.  Each thread sums < 2^26
+// squares below 2^92 in 128 bits; one wide_add4 per warp.
+__global__ void qsum_kernel(const float* __restrict__ X, long long count, int vec4,
+                            StageState* st)
+{
+    if (st->error) return;
+    const float scale = st->scaleF;
+    unsigned __int128 a = 0;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long done = 0;
+    if (vec4) {
+        const float4* X4 = reinterpret_cast<const float4*>(X);
+        long long n4 = count >> 2;
+        for (long long i = tid; i < n4; i += stride) {
+            float4 v = __ldg(X4 + i);
+            a += sq_fixed(v.x, scale) + sq_fixed(v.y, scale) + sq_fixed(v.z, scale) +
+                 sq_fixed(v.w, scale);
+        }
+        done = n4 << 2;
+    }
+    for (long long i = done + tid; i < count; i += stride) a += sq_fixed(__ldg(X + i), scale);
+    a = warp_sum_u128(a);
+    if ((threadIdx.x & 31) == 0 && a) wide_add4(st->q, a);
 }
 
 __global__ void gather_kernel(const float* __restrict__ X, int d,
@@ -172,6 +201,17 @@ int launch_maxabs(const float* X, long long n, int d, StageState* st, cudaStream
     int vec4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
     ++g_launches;
     maxabs_kernel<<<grid_for(count / 4 + 1, 256, sm_count, 8), 256, 0, s>>>(X, count, vec4, st);
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+int launch_qsum(const float* X, long long n, int d, StageState* st, cudaStream_t s, int sm_count)
+{
+    const long long count = n * d;
+    if (count <= 0) return KMEANS2_OK;
+    int vec4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
+    ++g_launches;
+    qsum_kernel<<<grid_for(count / 4 + 1, 256, sm_count, 8), 256, 0, s>>>(X, count, vec4, st);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }

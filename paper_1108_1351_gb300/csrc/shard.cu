@@ -10,7 +10,7 @@
 //   * max |x| of a stage's points, which fixes the stage's fixed-point scales;
 //   * per Lloyd iteration (Section 4.1), the integer partials of the update:
 //     the split sums S_j, the counts N_j and, in the first iteration of a
-//     stage, sum ||x||^2.  Integer sums are order-independent, so every rank
+//     stage, the exact sum of the squared fixed-point coordinates (for J).  Integer sums are order-independent, so every rank
 //     runs the same finalize on the same totals and all replicas, labels and
 //     iteration counts equal those of one unsharded fit bit for bit.
 // Sampling needs no exchange: the keys that choose S_s depend only on the
@@ -65,10 +65,11 @@ __global__ void init_contrib_kernel(const float* Xs, long long a, long long rows
 
 // Exchange layout of the per-iteration partials (int64 entries):
 //   [0, kd) low words of S | [kd, 2kd) high words of S | [2kd, 2kd + k) N |
-//   q_lo, q_hi | one flag per device error kind (1..3)
+//   q[0..3] (sum of s^2, first iteration of a stage) | one flag per device
+//   error kind (1..3)
 __host__ __device__ inline long long partials_count(int k, int d)
 {
-    return 2ll * k * d + k + 2 + 3;
+    return 2ll * k * d + k + 4 + 3;
 }
 
 // Carries each local low word into its high word (value unchanged) and copies
@@ -91,11 +92,17 @@ __global__ void pack_partials_kernel(Accum acc, int k, int d, const StageState* 
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const bool full = st->mode == kModeFull;
-        const unsigned long long qlo = full ? st->q_lo : 0ull, qhi = full ? st->q_hi : 0ull;
-        x[2 * kd + k] = qlo & 0xffffffffull;
-        x[2 * kd + k + 1] = qhi + (qlo >> 32);
-        for (int e = 1; e <= 3; ++e) x[2 * kd + k + 1 + e] = (st->error == e) ? 1ull : 0ull;
+        // the sum of s^2 with its words carried (q[0..2] < 2^32, value
+        // unchanged), so the sum over ranks cannot wrap either
+        unsigned long long q[4] = {0ull, 0ull, 0ull, 0ull};
+        if (st->mode == kModeFull)
+            for (int w = 0; w < 4; ++w) q[w] = st->q[w];
+        for (int w = 0; w < 3; ++w) {
+            q[w + 1] += q[w] >> 32;
+            q[w] &= 0xffffffffull;
+        }
+        for (int w = 0; w < 4; ++w) x[2 * kd + k + w] = q[w];
+        for (int e = 1; e <= 3; ++e) x[2 * kd + k + 3 + e] = (st->error == e) ? 1ull : 0ull;
     }
 }
 
@@ -114,12 +121,10 @@ __global__ void unpack_partials_kernel(const unsigned long long* x, Accum tot, i
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (st->mode == kModeFull) {
-            st->q_lo = x[2 * kd + k];
-            st->q_hi = x[2 * kd + k + 1];
-        }
+        if (st->mode == kModeFull)
+            for (int w = 0; w < 4; ++w) st->q[w] = x[2 * kd + k + w];
         for (int e = 1; e <= 3; ++e)
-            if (x[2 * kd + k + 1 + e] != 0ull && st->error == 0) st->error = e;
+            if (x[2 * kd + k + 3 + e] != 0ull && st->error == 0) st->error = e;
     }
 }
 
@@ -274,8 +279,11 @@ int resume_maxabs(kmeans2_shard* sh, kmeans2_exchange* next)
     KM2_CUDA(cudaMemcpyAsync(&st, sh->w.st, sizeof(st), cudaMemcpyDeviceToHost, s));
     KM2_CUDA(cudaStreamSynchronize(s));
     if (st.error) return map_stage_error(st.error);   // the same on every rank
-    if (sh->stage_rows() > 0)
+    if (sh->stage_rows() > 0) {
+        KM2_TRY(launch_qsum(sh->stage_X(), sh->stage_rows(), sh->d, sh->w.st, s,
+                            sh->ws->sm_count));
         KM2_TRY(prepare_stage_points(sh->stage_X(), sh->stage_rows(), sh->d, sh->w, *sh->ws, s));
+    }
     return run_local_pass(sh, next);
 }
 

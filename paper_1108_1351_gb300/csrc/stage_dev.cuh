@@ -63,11 +63,9 @@ static __device__ void stage_init_dev(StageState* st, int d, double tol, int max
     st->tol = tol;
     st->recheck_count = 0;
     st->rechecked_total = 0;
-    st->q_lo = 0;
-    st->q_hi = 0;
+    for (int w = 0; w < 4; ++w) st->q[w] = 0ull;
     st->J = 0.0;
     st->shift = 0.0;
-    st->Qtot = 0.0;
     st->empty = 0;
     st->error = 0;
     if (b >= 0x7f800000u) {
@@ -83,58 +81,182 @@ static __device__ void stage_init_dev(StageState* st, int d, double tol, int max
         st->done = 1;
         return;
     }
-    int lg = 0;
-    while ((1 << lg) < d) ++lg;
+    (void)d;
     int F = min(120, max(-100, 46 - E));
-    int G = min(120, max(-100, 62 - 2 * E - 16 - lg));
     st->F = F;
-    st->G = G;
     st->scaleF = ldexpf(1.0f, F);
-    st->scaleG = ldexpf(1.0f, G);
     st->inv_scaleF = ldexp(1.0, -F);
-    st->inv_scaleG = ldexp(1.0, -G);
+}
+
+// ---------------------------------------------------------------- exact J
+// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, and the
+// FMA two-product) for the center-displacement term of J.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(double a, double b, double& s, double& e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+// N c - s 2^-F for a center coordinate c (FP64), a cluster size N and the
+// exact integer sum s of the cluster's fixed-point coordinates: N times the
+// center's displacement from the cluster mean.  c N is split exactly into the
+// double-word p + e (FMA two-product) and s 2^-F exactly into a1 + a2 (the
+// 32-bit halves of s, scaled by powers of two), renormalised by TwoSum into
+// the double-word b1 + b2; the two double-words are then added with the
+// accurate double-word sum (two TwoSums, two renormalisations), whose relative
+// error is below 3 * 2^-106 of the result however close c is to the mean.
+__device__ __forceinline__ double displacement(double c, double N, __int128 s, double inv)
+{
+    const __int128 sh = s >> 32;                       // |sh| < 2^50: exact in FP64
+    const double a1 = (double)(long long)sh * (inv * 4294967296.0);
+    const double a2 = (double)(unsigned long long)(s - (sh << 32)) * inv;
+    double b1, b2;
+    two_sum(a1, a2, b1, b2);
+    const double p = c * N;
+    const double e = fma(c, N, -p);
+    double s1, s2, t1, t2;
+    two_sum(p, -b1, s1, s2);
+    two_sum(e, -b2, t1, t2);
+    s2 += t1;
+    fast_two_sum(s1, s2, s1, s2);
+    s2 += t2;
+    fast_two_sum(s1, s2, s1, s2);
+    return s1;
+}
+
+// 256-bit two's complement integers for the integer part of J.
+struct U256 {
+    unsigned long long w[4];
+};
+
+// a += v * 2^(64 limb), carries propagated to the top limb.
+__device__ __forceinline__ void u256_add_at(U256& a, unsigned __int128 v, int limb)
+{
+    unsigned long long carry = 0;
+    for (int i = limb; i < 4; ++i) {
+        const unsigned long long add = (i == limb) ? (unsigned long long)v
+                                     : (i == limb + 1) ? (unsigned long long)(v >> 64) : 0ull;
+        const unsigned __int128 t = (unsigned __int128)a.w[i] + add + carry;
+        a.w[i] = (unsigned long long)t;
+        carry = (unsigned long long)(t >> 64);
+    }
+}
+
+__device__ __forceinline__ void u256_neg(U256& a)
+{
+    unsigned long long carry = 1;
+    for (int i = 0; i < 4; ++i) {
+        const unsigned __int128 t = (unsigned __int128)(~a.w[i]) + carry;
+        a.w[i] = (unsigned long long)t;
+        carry = (unsigned long long)(t >> 64);
+    }
+}
+
+// The signed value of a, rounded to FP64 (the top 128 significant bits are
+// converted in one rounding; the rest is below 2^-64 of it).
+__device__ __forceinline__ double u256_to_double(U256 a)
+{
+    const bool neg = (long long)a.w[3] < 0;
+    if (neg) u256_neg(a);
+    int top = 3;
+    while (top > 0 && a.w[top] == 0) --top;
+    double r;
+    if (top == 0) {
+        r = (double)a.w[0];
+    } else {
+        const unsigned __int128 hi = ((unsigned __int128)a.w[top] << 64) | a.w[top - 1];
+        r = ldexp((double)hi, 64 * (top - 1));
+        if (top >= 2) r += ldexp((double)a.w[top - 2], 64 * (top - 2));
+    }
+    return neg ? -r : r;
 }
 
 // One warp: the new center j (its cluster mean; an empty cluster keeps its
 // center) with its FP32 copies and ||c_j||^2, and center j's terms of the
-// movement, of J and of the empty count in clus (4 k doubles).  Iteration it's
-// records of center j go to tr.centers / tr.counts when those are set.
+// movement, of J and of the empty count in clus (kClusSlots k doubles):
+//   clus[j]          ||c_j' - c_j||^2
+//   clus[k + j]      N_j ||c_j - mu_j||^2 - frac(T_j / N_j) 2^-2F
+//   clus[2k + j]     ||c_j'||^2
+//   clus[3k + j]     1 if the cluster is empty
+//   clus[4k + 3j..]  floor(T_j / N_j) as three 64-bit limbs
+// where s_jt = the exact integer sum of the cluster's fixed-point coordinates,
+// mu_j = s_j 2^-F / N_j its mean and T_j = ||s_j||^2, so that over all clusters
+// J = (sum s^2 - sum_j T_j / N_j) 2^-2F + sum_j N_j ||c_j - mu_j||^2
+//   = sum_j sum_{i in j} ||x_i - c_j||^2   (Eq. 3, on the fixed-point values).
+// Iteration it's records of center j go to tr.centers / tr.counts when those are set.
 static __device__ __forceinline__ void finalize_center_warp(const Accum& acc, const Centers& c,
                                                             double inv, int j, double* clus,
                                                             const TrajDev& tr, int it)
 {
     const int k = c.k, d = c.d;
     const int lane = threadIdx.x & 31;
-    long long N = (long long)acc.cnt[j];
-    double diff2 = 0.0, cS = 0.0, cc = 0.0, nn = 0.0;
+    const long long N = (long long)acc.cnt[j];
+    const double Nd = (double)N;
+    double diff2 = 0.0, dev2 = 0.0, nn = 0.0;
+    // T_j = t_hi 2^64 + t_lo, partial per lane (no carries needed: t_lo gains
+    // < 2^65 per coordinate, t_hi < 2^101)
+    unsigned __int128 t_lo = 0, t_hi = 0;
     for (int t = lane; t < d; t += 32) {
         long long e = (long long)j * d + t;
         const unsigned long long lo = acc.s_lo[e], hi = acc.s_hi[e];
-        double S = split_value(lo, hi, inv);
+        const __int128 v = (__int128)(long long)hi * (__int128)4294967296LL + (__int128)lo;
+        double S = (double)v * inv;
         // carry the low word's upper half into the high word (same value):
         // every pass adds at most 2 n < 2^32 low parts below 2^32 each, so
         // the low word cannot wrap however many delta passes follow
         acc.s_lo[e] = lo & 0xffffffffull;
         acc.s_hi[e] = hi + (lo >> 32);
         double cv = c.c64[e];
-        double cn = N > 0 ? S / (double)N : cv;
+        double cn = N > 0 ? S / Nd : cv;
         double df = cn - cv;
         diff2 = fma(df, df, diff2);
-        cS = fma(cv, S, cS);
-        cc = fma(cv, cv, cc);
         nn = fma(cn, cn, nn);
+        if (N > 0) {
+            const unsigned __int128 a = (unsigned __int128)(v < 0 ? -v : v);   // < 2^82
+            const unsigned long long al = (unsigned long long)a & 0xffffffffull;
+            const unsigned __int128 ah = a >> 32;
+            const unsigned __int128 m = 2 * ah * al;
+            t_hi += ah * ah + (m >> 32);
+            t_lo += ((m & 0xffffffffull) << 32) + (unsigned __int128)al * al;
+            const double r = displacement(cv, Nd, v, inv);
+            dev2 = fma(r, r, dev2);
+        }
         c.c64[e] = cn;
         c.c32[e] = (float)cn;
         c.c32t[(long long)t * c.kpad + j] = (float)cn;
         if (tr.centers) tr.centers[(long long)it * k * d + e] = cn;
     }
     diff2 = warp_sum_f64(diff2);
-    cS = warp_sum_f64(cS);
-    cc = warp_sum_f64(cc);
+    dev2 = warp_sum_f64(dev2);
     nn = warp_sum_f64(nn);
+    t_lo = warp_sum_u128(t_lo);
+    t_hi = warp_sum_u128(t_hi);
     if (lane == 0) {
+        unsigned long long* qw = reinterpret_cast<unsigned long long*>(clus + 4 * k) + 3ll * j;
+        double v = 0.0;
+        unsigned __int128 q_hi = 0;
+        unsigned long long q_lo = 0;
+        if (N > 0) {
+            // floor(T / N) and T mod N by long division (N < 2^63)
+            t_hi += t_lo >> 64;
+            const unsigned long long un = (unsigned long long)N;
+            q_hi = t_hi / un;
+            const unsigned __int128 x = ((t_hi % un) << 64) | (unsigned long long)t_lo;
+            q_lo = (unsigned long long)(x / un);
+            const unsigned long long rem = (unsigned long long)(x % un);
+            v = dev2 / Nd - ((double)rem / Nd) * (inv * inv);
+        }
+        qw[0] = q_lo;
+        qw[1] = (unsigned long long)q_hi;
+        qw[2] = (unsigned long long)(q_hi >> 64);
         clus[j] = diff2;
-        clus[k + j] = 2.0 * cS - (double)N * cc;
+        clus[k + j] = v;
         clus[2 * k + j] = nn;
         clus[3 * k + j] = (N == 0) ? 1.0 : 0.0;
         c.cnorm[j] = (float)nn;
@@ -147,32 +269,39 @@ struct FinalizeSmem {
     double r_J[1024];
     double r_nn[1024];
     int r_empty[1024];
-    double Qtot;
+    unsigned __int128 r_q[32][3];
 };
 
 // Whole block (blockDim.x <= 1024, a power of two), after every center's
 // finalize_center_warp: movement, J and loop control from clus, in a fixed
-// order (thread 0 updates st).  Ends with the block synchronised.
+// order (thread 0 updates st).  The integer part of J, sum s^2 - sum_j
+// floor(T_j / N_j), is exact (256-bit); it is rounded to FP64 once and added
+// to the sum of the per-center remainders.  Ends with the block synchronised.
 static __device__ void finalize_reduce_block(int k, StageState* st, const TrajDev& tr,
                                              const double* clus, FinalizeSmem& sm)
 {
     double* traj_J = tr.J;
     double* traj_shift = tr.shift;
-    if (threadIdx.x == 0) {
-        double Q = st->Qtot;
-        if (st->mode == kModeFull) {
-            Q = split_value(st->q_lo, st->q_hi, st->inv_scaleG);
-            st->Qtot = Q;
-        }
-        sm.Qtot = Q;
-    }
+    const unsigned long long* qw = reinterpret_cast<const unsigned long long*>(clus + 4 * k);
     double sh = 0.0, jj = 0.0, mx = 0.0;
     int em = 0;
+    unsigned __int128 a0 = 0, a1 = 0, a2 = 0;    // sums of the limbs of floor(T_j / N_j)
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         sh = fmax(sh, clus[j]);
         jj += clus[k + j];
         mx = fmax(mx, clus[2 * k + j]);
         em += (int)clus[3 * k + j];
+        a0 += qw[3ll * j];
+        a1 += qw[3ll * j + 1];
+        a2 += qw[3ll * j + 2];
+    }
+    a0 = warp_sum_u128(a0);
+    a1 = warp_sum_u128(a1);
+    a2 = warp_sum_u128(a2);
+    if ((threadIdx.x & 31) == 0) {
+        sm.r_q[threadIdx.x >> 5][0] = a0;
+        sm.r_q[threadIdx.x >> 5][1] = a1;
+        sm.r_q[threadIdx.x >> 5][2] = a2;
     }
     sm.r_shift[threadIdx.x] = sh;
     sm.r_J[threadIdx.x] = jj;
@@ -189,7 +318,23 @@ static __device__ void finalize_reduce_block(int k, StageState* st, const TrajDe
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double J = sm.Qtot - sm.r_J[0];
+        // D = sum s^2 - sum_j floor(T_j / N_j)  (>= 0: Cauchy-Schwarz per cluster)
+        U256 D = {{0ull, 0ull, 0ull, 0ull}};
+        U256 Tq = {{0ull, 0ull, 0ull, 0ull}};
+        u256_add_at(D, (unsigned __int128)st->q[0], 0);
+        u256_add_at(D, (unsigned __int128)st->q[1] << 32, 0);
+        u256_add_at(D, (unsigned __int128)st->q[2], 1);
+        u256_add_at(D, (unsigned __int128)st->q[3] << 32, 1);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            u256_add_at(Tq, sm.r_q[w][0], 0);
+            u256_add_at(Tq, sm.r_q[w][1], 1);
+            u256_add_at(Tq, sm.r_q[w][2], 2);
+        }
+        u256_neg(Tq);
+        for (int i = 0; i < 4; ++i) u256_add_at(D, (unsigned __int128)Tq.w[i], i);
+        const double inv = st->inv_scaleF;
+        double J = u256_to_double(D) * (inv * inv) + sm.r_J[0];
+        if (J < 0.0) J = 0.0;   // only rounding of an exactly zero objective can go below
         double shift = sqrt(sm.r_shift[0]);
         int it = st->iter;
         if (traj_J) traj_J[it] = J;

@@ -4,9 +4,11 @@
 * Centers: |c_gpu - c_oracle| <= 1e-10 * max_t |c_oracle[j, t]| + 2^(E - 46) per
   coordinate, where 2^E > max|x|: the second term is the documented
   fixed-point grid of the exact cluster sums.
-* J: |J_gpu - J_oracle| <= 1e-9 * J_oracle + 1e-13 * sum_i ||x_i||^2; the
-  library forms J as sum ||x||^2 - sum_j (2 c_j.S_j - N_j ||c_j||^2), whose FP64
-  rounding is relative to sum ||x||^2.
+* J: |J_gpu - J_oracle| <= 1e-9 * J_oracle (an exactly zero J must be zero).
+  The library forms J without cancellation (exact integer within-cluster part
+  plus double-word center displacements), so its error is a few FP64 ulps of J
+  itself; only coordinates below the fixed-point grid (|x| < 2^(E-23)) could
+  add more, and the test data hold none that matter.
 """
 import math
 
@@ -31,9 +33,8 @@ def assert_centers_close(got, want, X, rel=1e-10):
     assert not bad.any(), f"{bad.sum()} center coordinates off; worst {np.max(np.abs(got - want) - tol)}"
 
 
-def assert_J_close(got, want, X, rel=1e-9):
-    q = float(np.sum(np.asarray(X, dtype=np.float64) ** 2))
-    assert abs(got - want) <= rel * abs(want) + 1e-13 * q, (got, want)
+def assert_J_close(got, want, X=None, rel=1e-9):
+    assert abs(got - want) <= rel * abs(want), (got, want, abs(got - want) / max(abs(want), 1e-300))
 
 
 def to_np(a):

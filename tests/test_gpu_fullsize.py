@@ -68,8 +68,7 @@ def _check_step(X, C_in, C_out, labels, J, k):
     assert bool(((C_out - mean).abs() <= tol).all())
     # J of this assignment against the centers it was made with
     Jref = _J_fp64(X, labels, C_in)
-    q = sum(float((X[a:a + (1 << 24)].double() ** 2).sum()) for a in range(0, n, 1 << 24))
-    assert abs(J - Jref) <= 1e-9 * Jref + 1e-13 * q
+    assert abs(J - Jref) <= 1e-9 * Jref, (J, Jref)
 
 
 def test_default_workload_full_size_step_and_fit():

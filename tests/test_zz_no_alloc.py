@@ -43,6 +43,24 @@ def test_noalloc_step_matches_step_on_consecutive_calls(n, d, k):
         C = want[0]                       # the second call starts from the updated centers
 
 
+@pytest.mark.parametrize("d,k", [(128, 1024), (64, 512)])
+def test_noalloc_step_at_its_size_limits(d, k):
+    # n at the stated maximum, with d and k where kmeans_step would pick its
+    # tensor-core form: the no-alloc step runs the CUDA-core form instead and
+    # must return the same labels, centers and J as kmeans_step
+    dev = torch.device("cuda:0")
+    n = 4_194_304
+    X = synth.vmf_mixture(n, d, k, seed=d, device=dev)
+    C = X[torch.randperm(n, generator=torch.Generator().manual_seed(2))[:k].to(dev)].double()
+    for call in range(2):
+        want = km.step(X, C)
+        got = km.step_noalloc(X, C)
+        assert torch.equal(got[1], want[1]), f"labels differ on call {call}"
+        assert torch.equal(got[0], want[0]), f"centers differ on call {call}"
+        assert got[2] == want[2] and got[3] == want[3] and got[4] == want[4]
+        C = want[0]
+
+
 def test_noalloc_rejects_shapes_beyond_its_limits():
     dev = torch.device("cuda:0")
     X = torch.zeros((8, 129), dtype=torch.float32, device=dev)
