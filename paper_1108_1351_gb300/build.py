@@ -3,6 +3,9 @@
 Each translation unit under ``csrc/`` is compiled in parallel into
 ``csrc/_build/`` and linked into ``paper_1108_1351_gb300/libkmeans2.so``.
 Rebuilds only what changed (object older than its source or a header).
+``build_probe()`` compiles the FP32 FMA throughput probe that the benchmark
+uses as its roofline denominator (``probe/fp32_peak.cu`` ->
+``libfp32peak.so``; not part of the library).
 """
 from __future__ import annotations
 
@@ -100,6 +103,32 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False,
     with open(stamp, "w") as fh:
         fh.write(arch)
     return LIB
+
+
+PROBE_SRC = os.path.join(HERE, "probe", "fp32_peak.cu")
+PROBE_LIB = os.path.join(HERE, "libfp32peak.so")
+PROBE_STAMP = os.path.join(HERE, "probe", "host_arch.txt")
+
+
+def build_probe(force: bool = False) -> str:
+    """Compile the FP32 FMA probe (one translation unit) for sm_103a."""
+    arch = platform.machine()
+    try:
+        with open(PROBE_STAMP) as fh:
+            force = force or fh.read().strip() != arch
+    except OSError:
+        force = True
+    if force or _stale(PROBE_LIB, [PROBE_SRC]):
+        tmp = PROBE_LIB + f".tmp{os.getpid()}"
+        cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-shared", "-o", tmp, PROBE_SRC]
+        p = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if p.returncode != 0:
+            print(p.stdout)
+            raise RuntimeError("building libfp32peak.so failed")
+        os.replace(tmp, PROBE_LIB)
+        with open(PROBE_STAMP, "w") as fh:
+            fh.write(arch)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

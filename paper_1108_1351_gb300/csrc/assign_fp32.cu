@@ -17,7 +17,7 @@
 // beyond the distances.
 //
 // Two forms:
-//  assign_small<D>     d <= 16.  Each thread owns P points in registers and
+//  assign_small<D>     d <= 16.  Each thread owns P points (2 or 4) in registers and
 //                      prefetches its next tile with cp.async; the k centers
 //                      (pre-scaled by -2, with ||c||^2) sit in shared memory,
 //                      interleaved in pairs and read as broadcast 128-bit
@@ -67,10 +67,16 @@ __device__ __forceinline__ void top2_merge(float& b1, float& b2, int& bi, float 
     }
 }
 
+// Points per thread and resident CTAs per SM, measured on GB300 (n = 1e8,
+// k = 32, d = 2 / 4 / 8; n = 5e7, k = 64, d = 16; best of P = 1..4 with 2-4
+// CTAs per SM): 4 points at 2 CTAs up to d = 4, 2 points at 4 CTAs (62
+// registers) for d = 5..8 (+7 % at d = 8), 4 points at 2 CTAs from d = 9 on
+// (+8 % at d = 16 over 2 points).
 template <int D>
 struct SmallCfg {
     static constexpr int DS = (D + 3) & ~3;       // floats per center (-2c) in shared memory
-    static constexpr int P = D <= 8 ? 4 : 2;      // points per thread
+    static constexpr int P = (D > 4 && D <= 8) ? 2 : 4;   // points per thread
+    static constexpr int MINB = (D > 4 && D <= 8) ? 4 : 2;  // resident CTAs per SM
     static constexpr int V = (D % 4 == 0) ? 4 : ((D % 2 == 0) ? 2 : 1);   // copy width (floats)
     static constexpr int NV = D / V;              // copies per point
     static constexpr int TILE = kThreads * P;     // points per tile
@@ -123,7 +129,7 @@ __device__ __forceinline__ void read_point(const float* sx, int p, int tid, floa
 // Centers are walked in chunks of 32 and in pairs; the running top-2 of packed
 // keys costs 2.5 min/max operations per distance (3-input min).
 template <int D>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, SmallCfg<D>::MINB)
 assign_small(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
              StageState* st, Accum acc, int* __restrict__ list, float kappa, float kpack,
              int use_sacc)
@@ -518,7 +524,7 @@ int launch_small(const float* X, long long n, const Centers& c, int* labels, Sta
 static size_t small_smem_min(int d, int k)
 {
     size_t ds = (size_t)((d + 3) & ~3) + 1;
-    size_t tile = (size_t)kThreads * (d <= 8 ? 4 : 2);
+    size_t tile = (size_t)kThreads * ((d > 4 && d <= 8) ? 2 : 4);
     return (size_t)((k + 31) & ~31) * ds * 4 + tile * d * 4 + tile * 4;
 }
 

@@ -11,7 +11,9 @@
 // tile.  The CUDA cores only split the points and run the epilogue: packed-key
 // top-2, the near-tie flag (a bound that covers the split, the tensor core's
 // FP32 accumulation and the key packing), labels and the exact fixed-point
-// cluster sums.
+// cluster sums.  A row inside the (looser) 3xTF32 bound is first re-decided on
+// the CUDA cores with the FP32 FMA chain of the CUDA-core kernels and their
+// tighter bound; only rows inside that bound go to the FP64 recheck list.
 //
 // Warp-specialised pipeline, one CTA per SM, 14 warps.  The unit of every
 // hand-off is a group of T 128-point tiles (T = 4, 2 or 1 as k grows), so
@@ -198,11 +200,37 @@ struct TcBars {
     uint64_t drain;
 };
 
+// The row's FP32 distances to every center by the CUDA-core FMA chain
+// (||c||^2 + sum_t fma(x_t, -2 c_t), t ascending), whose rounding tie_kappa
+// bounds, and their top-2 (lowest index on equal values).  For rows the
+// 3xTF32 bound cannot decide.
+template <int D>
+__device__ __forceinline__ void fp32_top2(const float* x, const Centers& c, float& b1, float& b2,
+                                          int& bi)
+{
+    b1 = INFINITY;
+    b2 = INFINITY;
+    bi = 0;
+    for (int j = 0; j < c.k; ++j) {
+        float a = __ldg(c.cnorm + j);
+        const float* cj = c.c32 + (long long)j * D;
+#pragma unroll
+        for (int t = 0; t < D; ++t) a = fmaf(x[t], -2.0f * __ldg(cj + t), a);
+        if (a < b1) {
+            b2 = b1;
+            b1 = a;
+            bi = j;
+        } else {
+            b2 = fminf(b2, a);
+        }
+    }
+}
+
 template <int D, int T>
 __global__ void __launch_bounds__(kThreads, 1)
 assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
             StageState* st, Accum acc, int* __restrict__ list, float kappa, float kpack,
-            int npad, uint32_t tmem_cols, TcLayout L)
+            float kappa32, int npad, uint32_t tmem_cols, TcLayout L)
 {
     using C = TcCfg<D>;
     constexpr int KD = C::KD;
@@ -507,7 +535,15 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
 #pragma unroll
                 for (int e = 0; e < D; ++e) xn2 = fmaf(x[e], x[e], xn2);
                 const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1[t]) + fabsf(B2[t]));
-                const bool flag = valid && (B2[t] - B1[t] <= thr);
+                bool flag = valid && (B2[t] - B1[t] <= thr);
+                int lab = BI[t];
+                if (flag) {
+                    // inside the 3xTF32 bound: re-decide with the FP32 FMA chain
+                    // and its tighter bound; FP64 only if that cannot decide
+                    float f1, f2;
+                    fp32_top2<D>(x, c, f1, f2, lab);
+                    flag = f2 - f1 <= kappa32 * (thr_base + xn2);
+                }
                 {
                     const unsigned m = __ballot_sync(0xffffffffu, flag);
                     if (m) {
@@ -522,7 +558,6 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                                         ? (from_ring ? lab_ring[((size_t)rs * T + t) * kRows + row]
                                                      : labels[p])
                                         : -1;
-                    const int lab = BI[t];
                     if (lab != old && label_ok(lab, c.k, st) && old_label_ok(old, c.k, st)) {
 #pragma unroll
                         for (int e = 0; e < D; ++e) {
@@ -631,8 +666,8 @@ int launch_tc_t(const float* X, long long n, const Centers& c, int* labels, Stag
     if (grid < 1) grid = 1;
     ++g_launches;
     assign_tc32<D, T><<<(int)grid, kThreads, L.total, s>>>(X, n, c, labels, st, acc, list,
-                                                           tc32_kappa(C::KD), kPackSlack, npad,
-                                                           cols, L);
+                                                           tc32_kappa(C::KD), kPackSlack,
+                                                           tie_kappa(D), npad, cols, L);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
