@@ -14,10 +14,12 @@ U[-10, 10]^8, Dirichlet(1) weights) with 2% uniform background noise, subset
 fraction 1%, tol 1e-5, max_iter 50 per stage, seed 0.  X is 16 GB, far larger
 than L2, so no flush is needed between steps.
 
-Under torchrun (N > 1) every rank fits its own replica of the workload (seed +
-rank) with no cross-rank exchange ("replicas"; the row-sharded fit is the
-separate shard-session API), and the value is the total over ranks divided by
-the slowest rank's time ("weak").
+Under torchrun (N > 1) the ranks run ONE row-sharded fit (the shard-session API
+over NCCL: each rank holds its own 5e8-row block of one data set, drawn from
+the same mixture with its own sample stream, and the ranks all-reduce the
+integer partials every iteration); the value is the global distance
+evaluations divided by the slowest rank's time, per-GPU rows fixed ("weak").
+``--parallelism replicas`` instead fits an independent replica per rank.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the only other place this file runs the oracle;
@@ -62,14 +64,15 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _gen(cfg, device, seed):
+def _gen(cfg, device, seed, sample_seed=None):
     import torch
     from paper_1108_1351_gb300 import synth
     n, d, k = cfg["n"], cfg["d"], cfg["k"]
     if cfg["gen"] == "iso":
         return synth.iso_gaussian_mixture(n, d, k, seed, device=device)
     if cfg["gen"] == "aniso":
-        return synth.aniso_gaussian_noise(n, d, k, seed, device=device, chunk=1 << 24)
+        return synth.aniso_gaussian_noise(n, d, k, seed, device=device, chunk=1 << 24,
+                                          sample_seed=sample_seed)
     if cfg["gen"] == "vmf":
         return synth.vmf_mixture(n, d, k, seed, device=device, chunk=1 << 20)
     raise ValueError(cfg["gen"])
@@ -365,20 +368,35 @@ def run_ours(args, cfg):
         dist.init_process_group("nccl", device_id=dev)
     km.load()
     n, d, k = cfg["n"], cfg["d"], cfg["k"]
-    X = _gen(cfg, dev, cfg["seed"] + rank)
+    sharded = ws > 1 and args.parallelism == "sharded"
+    if sharded:
+        # rank r's rows [r n, (r + 1) n) of one data set: the same mixture,
+        # its own sample stream (rank 0's block is the single-GPU workload)
+        X = _gen(cfg, dev, cfg["seed"], sample_seed=cfg["seed"] + 7919 * rank)
+    else:
+        X = _gen(cfg, dev, cfg["seed"] + rank)
     torch.cuda.synchronize()
     centers = torch.empty(k, d, dtype=torch.float64, device=dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def one(profile=None):
-        return km.fit(X, k, cfg["f"], cfg["seed"] + rank, cfg["tol"], cfg["max_iter"],
-                      centers_out=centers, labels_out=labels, stream=stream, profile=profile,
-                      precision=args.precision)
+        if sharded and profile is None:
+            return km.fit_data_parallel(X, rank * n, ws * n, k, cfg["f"], cfg["seed"], cfg["tol"],
+                                        cfg["max_iter"], precision=args.precision,
+                                        profile=launch_counter)
+        # the profiled fits of a sharded run time the same kernel on one
+        # rank's block (the launch a rank makes per iteration)
+        return km.fit(X, k, cfg["f"], cfg["seed"] + (0 if sharded else rank), cfg["tol"],
+                      cfg["max_iter"], centers_out=centers, labels_out=labels, stream=stream,
+                      profile=profile, precision=args.precision)
+
+    launch_counter = km.Profile()
 
     p32 = fp32_peak(dev, stream) if rank == 0 else None
     for _ in range(args.warmup):
         one()
+    launch_counter.kernel_launches = 0             # sharded: count the timed fits only
     gpu_id = None
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -403,20 +421,49 @@ def run_ours(args, cfg):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    timed_launches = int(launch_counter.kernel_launches)
     evals = sum(r.distance_evals for r in results)
-    ms_max, total_evals = reduce_over_ranks(ms, evals, ws, dev)
+    if sharded:
+        # every rank reports the global count of one fit: count it once
+        ms_max, total_evals = reduce_over_ranks(ms, evals / ws, ws, dev)
+    else:
+        ms_max, total_evals = reduce_over_ranks(ms, evals, ws, dev)
 
     # the distance kernel's own time for the roofline: separate profiled fits
     # (host-driven loop, CUDA events around every launch of the fused
     # distance kernel on the call's stream), after the timed region
     prof = km.Profile()
+    prng = torch.cuda.nvtx.range_start("profiled")   # the launch list's ncu range
     for _ in range(args.profile_fits):
         one(prof)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_end(prng)
 
     # end to end through the same C-ABI call with HOST buffers
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and sharded:
+        # each step: this rank's block host -> device, the sharded fit, its
+        # labels device -> host (the same rows as the device-resident run)
+        Xh = torch.empty((n, d), dtype=torch.float32, pin_memory=True)
+        Xh.copy_(X)
+        lh = torch.empty((n,), dtype=torch.int32, pin_memory=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_evals = 0
+        for _ in range(args.e2e_steps):
+            X.copy_(Xh, non_blocking=True)
+            r = one()
+            lh.copy_(r.labels)
+            e_evals += r.distance_evals
+        torch.cuda.synchronize()
+        te_ms, ee = reduce_over_ranks(1e3 * (time.perf_counter() - t0), e_evals / ws, ws, dev)
+        e2e = {"value": ee / (te_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * 4,
+               "per": "rank (each rank copies its own block)",
+               "steps": args.e2e_steps, "ms_per_step": te_ms / args.e2e_steps}
+        Xh_host = Xh[: min(n, 2_000_000)].numpy()
+    elif args.e2e_steps > 0:
         Xh = torch.empty((n, d), dtype=torch.float32, pin_memory=True)
         Xh.copy_(X)
         ch = torch.empty((k, d), dtype=torch.float64, pin_memory=True)
@@ -458,20 +505,24 @@ def run_ours(args, cfg):
         "data": "synthetic",
         "config": {"workload": args.config, "n": n, "d": d, "k": k, "subset_fraction": cfg["f"],
                    "tol": cfg["tol"], "max_iter": cfg["max_iter"], "seed": cfg["seed"],
-                   "parallelism": "replicas" if ws > 1 else "single",
+                   "parallelism": ("sharded" if sharded else "replicas") if ws > 1 else "single",
+                   "rows_per_gpu": n, "rows_total": n * ws if sharded else n,
                    "l2": "inputs larger than L2 (X is %.1f GB)" % (n * d * 4 / 1e9)
                    if n * d * 4 > 2e8 else "inputs smaller than L2"},
         "time_to_converge_s": (ms_max / args.steps) / 1e3,
-        "time_to_converge_note": "one whole fit; with tol 1e-5 and max_iter 50 per stage this "
-                                 "workload runs both stages to max_iter (see fit.converged_*)",
+        "time_to_converge_note": ("one whole fit to its stopping rule (tol %g, max_iter %d per "
+                                  "stage); fit.converged_* say whether tol or max_iter ended "
+                                  "each stage" % (cfg["tol"], cfg["max_iter"])),
         # each timed call's own wall time (host clock inside the library; rank 0)
         "time_to_converge_median_s": statistics.median(r.seconds for r in results) if results else None,
         "fit": {"J": r0.J, "iters_fast": r0.iters_fast, "iters_slow": r0.iters_slow,
                 "converged_fast": r0.converged_fast, "converged_slow": r0.converged_slow,
                 "rechecked_points": r0.rechecked_points, "distance_evals": r0.distance_evals,
                 "subset_size": r0.subset_size, "empty_clusters": r0.empty_clusters},
-        # kernels per fit (the profiled fits run the same kernels as the graph body) x steps
-        "gpu_launches": int(prof.kernel_launches) // max(1, args.profile_fits) * args.steps,
+        # kernels per fit (the profiled fits run the same kernels as the graph
+        # body; a sharded fit counts its own session's launches) x steps
+        "gpu_launches": (timed_launches if sharded else
+                         int(prof.kernel_launches) // max(1, args.profile_fits) * args.steps),
         "fp32_peak_probe": p32,
         "roofline": roofline,
         "clocks": clk,
@@ -940,6 +991,8 @@ def main():
                     help="profiled fits after the timed region (roofline kernel times)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--parallelism", default="sharded", choices=["sharded", "replicas"],
+                    help="N > 1: one row-sharded fit over NCCL, or one replica per rank")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()

@@ -494,7 +494,8 @@ class Shard:
 
     def __init__(self, X_local, row0: int, n_total: int, k: int, subset_fraction: float,
                  seed: int, tol: float, max_iter: int, *, tol_fast: float = 0.0,
-                 precision: str = "auto", init_centers=None, start_stage: int = 0, stream=None):
+                 precision: str = "auto", init_centers=None, start_stage: int = 0, stream=None,
+                 profile: "Profile | None" = None):
         lib = load()
         if not (_is_torch(X_local) and X_local.is_cuda):
             raise TypeError("Shard takes a CUDA tensor of this rank's rows")
@@ -513,6 +514,8 @@ class Shard:
         opt.init_centers = _ptr(self._C0)
         opt.start_stage = start_stage
         opt.stream = _stream_of(self.X, stream)
+        if profile is not None:
+            opt.profile = ctypes.addressof(profile)      # kernel launches of the session
         h = ctypes.c_void_p()
         with _device_of(self.X):
             rc = lib.kmeans2_shard_create(_ptr(self.X) if self.n_local else None, self.n_local,
@@ -572,13 +575,22 @@ def fit_data_parallel(X_local, row0: int, n_total: int, k: int, subset_fraction:
     make = shard_factory or Shard
     sh = make(X_local, row0, n_total, k, subset_fraction, seed, tol, max_iter, **kw)
     ops = {"sum": dist.ReduceOp.SUM, "max": dist.ReduceOp.MAX}
+    # a gloo group reduces host tensors: stage a device buffer through host
+    # memory (the shard's stream is synchronised when advance() returns, and
+    # the copy back is ordered before its next kernels on the same stream)
+    stage = dist.get_backend(group) == "gloo"
     try:
         while True:
             x = sh.advance()
             if x is None:
                 break
             op, buf = x
-            dist.all_reduce(buf, op=ops[op], group=group)
+            if stage and buf.is_cuda:
+                h = buf.cpu()
+                dist.all_reduce(h, op=ops[op], group=group)
+                buf.copy_(h)
+            else:
+                dist.all_reduce(buf, op=ops[op], group=group)
         return sh.result()
     finally:
         sh.close()

@@ -67,14 +67,18 @@ def aniso_gaussian_noise(n: int, d: int, k: int, seed: int, *, eig_lo: float = 0
                          eig_hi: float = 2.0, alpha: float = 1.0, noise: float = 0.02,
                          lo: float = -10.0, hi: float = 10.0, device="cpu",
                          chunk: int = 1 << 22, out: torch.Tensor | None = None,
-                         return_truth: bool = False):
+                         return_truth: bool = False, sample_seed: int | None = None):
     """Anisotropic Gaussian mixture with uniform background noise.
 
     Component j: mean ~ U[lo, hi]^d, covariance R_j diag(lambda) R_j^T with
     lambda log-uniform in [eig_lo, eig_hi] and R_j Haar-random; weights
     ~ Dirichlet(alpha).  Each point is noise with probability ``noise``; noise
     points are uniform over the per-dimension bounding box of the mixture
-    points.  Generated in chunks so that n = 5e8 fits beside its output."""
+    points.  Generated in chunks so that n = 5e8 fits beside its output.
+    The mixture comes from ``seed``, the points from ``sample_seed`` (default
+    ``seed``): blocks with the same seed and different sample seeds are
+    independent samples of one mixture (the row blocks of a data set split
+    over several GPUs)."""
     rng = np.random.default_rng(seed)
     means = rng.uniform(lo, hi, size=(k, d))
     L = np.empty((k, d, d))
@@ -87,7 +91,7 @@ def aniso_gaussian_noise(n: int, d: int, k: int, seed: int, *, eig_lo: float = 0
     mu = torch.as_tensor(means, dtype=torch.float32, device=device)
     Lt = torch.as_tensor(L, dtype=torch.float32, device=device)
 
-    g = _gen(device, seed)
+    g = _gen(device, seed if sample_seed is None else sample_seed)
     X = out if out is not None else torch.empty(n, d, dtype=torch.float32, device=device)
     is_noise = torch.rand(n, generator=g, device=device) < noise
     comp_all = torch.empty(n, dtype=torch.int32, device=device) if return_truth else None
