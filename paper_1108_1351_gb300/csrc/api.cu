@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -66,6 +67,18 @@ int set_max_dynamic_smem(const void* kernel, int bytes)
     KM2_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     g_attr_done.emplace_back(kernel, dev);
     return KMEANS2_OK;
+}
+
+int consumer_wait_tries(int normal)
+{
+#ifdef KM2_DEBUG_CHECKS
+    const char* v = std::getenv("KMEANS2_DEBUG_WAIT_TRIES");
+    if (v && *v) {
+        const long t = std::strtol(v, nullptr, 10);
+        if (t >= 0 && t < normal) return (int)t;
+    }
+#endif
+    return normal;
 }
 
 // A private blocking stream per thread and device, used when the caller passes

@@ -67,6 +67,14 @@ struct DeviceScratch {
     DeviceScratch& operator=(const DeviceScratch&) = delete;
 };
 
+// Wait limit (mbarrier try_wait rounds) of the consumer roles of the
+// tensor-core kernels -- the MMA issuer and the epilogues -- given the
+// kernel's normal limit.  Debug builds (KM2_DEBUG_CHECKS) take it from the
+// environment variable KMEANS2_DEBUG_WAIT_TRIES when set, so that a test can
+// make those waits run out and check the timeout status; producers and the
+// drain waits that let every issued copy and MMA finish keep their limits.
+int consumer_wait_tries(int normal);
+
 // Raises a kernel's dynamic shared-memory limit to `bytes` once per (kernel,
 // device) for the whole process, under a lock.  The value must be fixed per
 // kernel: worker threads that launch the same kernel concurrently then never

@@ -100,6 +100,7 @@ struct Bf16Args {
     int lab_bulk;            // old labels can be bulk-copied (16-byte aligned)
     uint32_t tmem_cols;
     float kappa, kpack;
+    int ctries;              // wait limit of the consumer roles (MMA issuer, epilogue)
 };
 
 // Accumulators per epilogue group: two (MMAs of the next chunk overlap the
@@ -136,10 +137,10 @@ static_assert(sizeof(Bars) + sizeof(SideRing) + kEpiWarps * kRecheckQ * 4 + 64 <
 // Bounded wait for the phase of `parity`; gives up early once another role
 // has aborted.  On its own timeout it raises the abort flag and the error.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         StageState* st)
+                                         StageState* st, int tries = kWaitTries)
 {
     const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
-    for (int i = 0; i < kWaitTries; ++i) {
+    for (int i = 0; i < tries; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -210,6 +211,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     if (st->error) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d, nch = a.nch, SB = a.sb;
+    const int ctries = a.ctries;
     const int mode = st->mode;
     const bool lab_bulk = a.lab_bulk != 0 && mode == kModeDelta;
     const int ksteps = d / 16;
@@ -322,19 +324,19 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             for (long long pr = 0; pr < npairs && ok; ++pr) {
                 const bool two = 2 * pr + 1 < cnt;
                 const uint32_t par = (uint32_t)(pr & 1);
-                if (!(ok = wait_bar(&bars.a_full[0], par, abort_v, st))) break;
-                if (two && !(ok = wait_bar(&bars.a_full[1], par, abort_v, st))) break;
+                if (!(ok = wait_bar(&bars.a_full[0], par, abort_v, st, ctries))) break;
+                if (two && !(ok = wait_bar(&bars.a_full[1], par, abort_v, st, ctries))) break;
                 tc::fence_after_sync();
                 for (int ch = 0; ch < nch && ok; ++ch) {
                     const int b0 = ch % kAccBufs<NC>, b1 = kAccBufs<NC> + ch % kAccBufs<NC>;
-                    if (!(ok = wait_bar(&bars.acc_empty[b0], ((phase >> b0) & 1u) ^ 1u, abort_v, st))) break;
-                    if (two && !(ok = wait_bar(&bars.acc_empty[b1], ((phase >> b1) & 1u) ^ 1u, abort_v, st)))
+                    if (!(ok = wait_bar(&bars.acc_empty[b0], ((phase >> b0) & 1u) ^ 1u, abort_v, st, ctries))) break;
+                    if (two && !(ok = wait_bar(&bars.acc_empty[b1], ((phase >> b1) & 1u) ^ 1u, abort_v, st, ctries)))
                         break;
                     tc::fence_after_sync();
                     const uint32_t d0 = tmem + (uint32_t)(b0 * NC), d1 = tmem + (uint32_t)(b1 * NC);
                     for (int ks = 0; ks < kslices; ++ks, ++q) {
                         const int slot = (int)(q % SB);
-                        if (!(ok = wait_bar(&bars.b_full[slot], (uint32_t)((q / SB) & 1), abort_v, st)))
+                        if (!(ok = wait_bar(&bars.b_full[slot], (uint32_t)((q / SB) & 1), abort_v, st, ctries)))
                             break;
                         tc::fence_after_sync();
                         const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes;
@@ -403,7 +405,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             for (int ch = 0; ch < nch; ++ch) {
                 const int b = g * kAccBufs<NC> + ch % kAccBufs<NC>;
                 bool w = wait_bar(&bars.acc_full[b], (phase >> (ch % kAccBufs<NC>)) & 1u, abort_v,
-                                  st);
+                                  st, ctries);
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 tc::fence_after_sync();
                 // 32 columns at a time through three register buffers: block i + 2
@@ -440,7 +442,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             const bool valid = p < a.n;
             const int r = (int)(i % kSR);
             {
-                const bool w = wait_bar(&bars.side_full[r], (uint32_t)((i / kSR) & 1), abort_v, st);
+                const bool w = wait_bar(&bars.side_full[r], (uint32_t)((i / kSR) & 1), abort_v, st, ctries);
                 if (!__all_sync(0xffffffffu, w)) break;
             }
             const bool in_ring = (long long)row < ((a.n - tile * kRows) & ~3ll);
@@ -706,6 +708,7 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     a.tmem_cols = cols;
     a.kappa = bf16_kappa(d);
     a.kpack = kPackSlack;
+    a.ctries = consumer_wait_tries(kWaitTries);
     ++g_launches;
     if (NC == 64)
         assign_bf16<64><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);

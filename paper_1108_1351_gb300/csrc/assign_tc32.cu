@@ -91,10 +91,10 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 
 // Bounded wait that also gives up once another role has aborted.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                         StageState* st)
+                                         StageState* st, int tries = kWaitTries)
 {
     const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
-    for (int i = 0; i < kWaitTries; ++i) {
+    for (int i = 0; i < tries; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -230,7 +230,7 @@ template <int D, int T>
 __global__ void __launch_bounds__(kThreads, 1)
 assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict__ labels,
             StageState* st, Accum acc, int* __restrict__ list, float kappa, float kpack,
-            float kappa32, int npad, uint32_t tmem_cols, TcLayout L)
+            float kappa32, int npad, uint32_t tmem_cols, TcLayout L, int ctries)
 {
     using C = TcCfg<D>;
     constexpr int KD = C::KD;
@@ -415,8 +415,8 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
             for (long long u = 0; u < units; ++u) {
                 const int sa = (int)(u % SA);
                 const int b = (int)(u & 1) * NB + (int)((u >> 1) % NB);
-                if (!wait_bar(&bars.a_full[sa], (uint32_t)((u / SA) & 1), abort_v, st)) break;
-                if (!wait_bar(&bars.acc_empty[b], ((phase >> b) & 1u) ^ 1u, abort_v, st)) break;
+                if (!wait_bar(&bars.a_full[sa], (uint32_t)((u / SA) & 1), abort_v, st, ctries)) break;
+                if (!wait_bar(&bars.acc_empty[b], ((phase >> b) & 1u) ^ 1u, abort_v, st, ctries)) break;
                 tc::fence_after_sync();
                 const int nt = tiles_in(u);
                 for (int t = 0; t < nt; ++t) {
@@ -475,8 +475,8 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
             const int slot = (int)((u >> 1) % NB);
             const int b = g * NB + slot;
             const int rs = (int)(u % RS);
-            bool w = wait_bar(&bars.acc_full[b], (phase >> slot) & 1u, abort_v, st);
-            w = w && wait_bar(&bars.raw_full[rs], (uint32_t)((u / RS) & 1), abort_v, st);
+            bool w = wait_bar(&bars.acc_full[b], (phase >> slot) & 1u, abort_v, st, ctries);
+            w = w && wait_bar(&bars.raw_full[rs], (uint32_t)((u / RS) & 1), abort_v, st, ctries);
             if (!__all_sync(0xffffffffu, w)) break;
             tc::fence_after_sync();
             const int nt = tiles_in(u);
@@ -667,7 +667,8 @@ int launch_tc_t(const float* X, long long n, const Centers& c, int* labels, Stag
     ++g_launches;
     assign_tc32<D, T><<<(int)grid, kThreads, L.total, s>>>(X, n, c, labels, st, acc, list,
                                                            tc32_kappa(C::KD), kPackSlack,
-                                                           tie_kappa(D), npad, cols, L);
+                                                           tie_kappa(D), npad, cols, L,
+                                                           consumer_wait_tries(kWaitTries));
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
