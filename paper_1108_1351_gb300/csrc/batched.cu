@@ -6,7 +6,9 @@
 //                     (job, first 1024-point tile, tile count); items of jobs
 //                     that are done, or beyond the current stage's points, are
 //                     skipped
-//   batch_recheck     one CTA per job: FP64 re-decision of its near ties
+//   batch_recheck     FP64 re-decision of the near ties of every running job
+//                     as one flat list (a scan of the jobs' flagged counts,
+//                     then one warp per flagged point over the whole GPU)
 //   batch_finalize    one CTA per job: means, movement, J, stop test, and the
 //                     switch from the fast to the slow stage (Section 2)
 //   batch_control     sets the graph's while condition: any job still running
@@ -217,19 +219,22 @@ __global__ void __launch_bounds__(kThreads) batch_reset_kernel(BatchInst* insts)
 
 // ---------------------------------------------------------------- assign
 
-template <int DC>
+// Tile shape of a dimension class: P points per thread (the autotuner picks P
+// among the values the registers allow), sub-tiles of kThreads * P points.
+template <int DC, int PP>
 struct BCfg {
-    static constexpr int P = DC <= 16 ? 4 : (DC <= 32 ? 2 : 1);   // points per thread
+    static constexpr int P = PP;                                  // points per thread
     static constexpr int SUB = kThreads * P;                      // points per sub-tile
     static constexpr int NSUB = kTile / SUB;
     static constexpr bool SACC = DC <= 32;                        // per-CTA partial sums
+    static_assert(kTile % SUB == 0, "a tile holds whole sub-tiles");
 };
 
 template <int DC>
 constexpr size_t batch_smem()
 {
     return (size_t)kMaxK * DC * 4 + (size_t)kMaxK * 4 +
-           (BCfg<DC>::SACC ? (size_t)kMaxK * DC * 8 + (size_t)kMaxK * 4 : 0);
+           (DC <= 32 ? (size_t)kMaxK * DC * 8 + (size_t)kMaxK * 4 : 0);
 }
 
 __device__ __forceinline__ float pack_key(float v, unsigned j)
@@ -237,11 +242,11 @@ __device__ __forceinline__ float pack_key(float v, unsigned j)
     return __uint_as_float((__float_as_uint(v) & ~31u) | j);
 }
 
-template <int DC>
+template <int DC, int PP>
 __global__ void __launch_bounds__(kThreads, 2)
 batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item)
 {
-    using C = BCfg<DC>;
+    using C = BCfg<DC, PP>;
     constexpr int P = C::P;
     extern __shared__ __align__(16) float smem[];
     float* sc = smem;                                         // kMaxK * DC: -2 c
@@ -426,15 +431,58 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
 
 // ---------------------------------------------------------------- recheck, finalize, control
 
-__global__ void __launch_bounds__(kThreads) batch_recheck_kernel(BatchInst* insts)
+// The recheck of the whole batch as one flat list: prefix[j] = flagged points
+// of the running jobs before job j, prefix[count] = all of them (one CTA,
+// sequential over thread slices: jobs in order, so the list order is fixed).
+__global__ void __launch_bounds__(1024) batch_recheck_scan_kernel(const BatchInst* insts, int count,
+                                                                  long long* prefix)
+{
+    __shared__ long long part[1024];
+    const int per = (count + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = min(count, (int)threadIdx.x * per), j1 = min(count, j0 + per);
+    auto flagged = [&](int j) -> long long {
+        const BatchInst& I = insts[j];
+        return (I.stage < 2 && I.st.error == 0) ? (long long)I.st.recheck_count : 0ll;
+    };
+    long long sum = 0;
+    for (int j = j0; j < j1; ++j) sum += flagged(j);
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) { const long long v = part[t]; part[t] = acc; acc += v; }
+        prefix[count] = acc;
+    }
+    __syncthreads();
+    long long acc = part[threadIdx.x];
+    for (int j = j0; j < j1; ++j) {
+        prefix[j] = acc;
+        acc += flagged(j);
+    }
+}
+
+// One warp per flagged point of the flat list (recheck_point): the work of
+// all jobs is spread over the whole GPU, so a job with many near ties no
+// longer holds one CTA for the rest of the iteration.
+__global__ void __launch_bounds__(kThreads) batch_recheck_flat_kernel(BatchInst* insts, int count,
+                                                                      const long long* prefix)
 {
     __shared__ float cache[kThreads / 32][256];     // k <= 256 in the batched form
-    BatchInst* I = insts + blockIdx.x;
-    if (I->stage >= 2 || I->st.error) return;
-    const float* X = I->stage == 0 ? I->Xs : I->X;
-    int* labels = I->stage == 0 ? I->lab_fast : I->lab_slow;
-    recheck_warps(X, I->d, I->c, labels, I->list, &I->st, I->acc, threadIdx.x >> 5,
-                  blockDim.x >> 5, cache[threadIdx.x >> 5], 256);
+    const long long total = prefix[count];
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+        // the job of entry w: the first j with prefix[j + 1] > w (warp-uniform)
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid + 1] > w) hi = mid; else lo = mid + 1;
+        }
+        BatchInst* I = insts + lo;
+        const float* X = I->stage == 0 ? I->Xs : I->X;
+        int* labels = I->stage == 0 ? I->lab_fast : I->lab_slow;
+        recheck_point(X, I->d, I->c, labels, I->list[w - prefix[lo]], &I->st, I->acc,
+                      cache[threadIdx.x >> 5], 256);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) batch_finalize_kernel(BatchInst* insts, int* active)
@@ -514,42 +562,53 @@ int dclass(int d)
     return 64;
 }
 
-template <int DC>
+template <int DC, int P>
 int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item,
                         cudaStream_t s, int sm_count)
 {
     const size_t sm = batch_smem<DC>();
-    KM2_TRY(set_max_dynamic_smem((const void*)batch_assign<DC>, (int)sm));
+    KM2_TRY(set_max_dynamic_smem((const void*)batch_assign<DC, P>, (int)sm));
     int per_sm = 0;
-    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_assign<DC>, kThreads, sm));
+    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_assign<DC, P>, kThreads,
+                                                           sm));
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)sm_count * per_sm;
     if (grid > nitems) grid = nitems;
     if (grid < 1) grid = 1;
     ++g_launches;
-    batch_assign<DC><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems, next_item);
+    batch_assign<DC, P><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems, next_item);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
 
-int launch_class(int dc, BatchInst* insts, const WorkItem* items, int nitems, int* next_item,
-                 cudaStream_t s, int sm_count)
+// Points per thread the autotuner may pick for a dimension class (as many as
+// the registers hold: a point is DC floats).
+std::vector<int> tile_points(int dc)
 {
-    switch (dc) {
-        case 2: return launch_batch_assign<2>(insts, items, nitems, next_item, s, sm_count);
-        case 4: return launch_batch_assign<4>(insts, items, nitems, next_item, s, sm_count);
-        case 8: return launch_batch_assign<8>(insts, items, nitems, next_item, s, sm_count);
-        case 16: return launch_batch_assign<16>(insts, items, nitems, next_item, s, sm_count);
-        case 32: return launch_batch_assign<32>(insts, items, nitems, next_item, s, sm_count);
-        default: return launch_batch_assign<64>(insts, items, nitems, next_item, s, sm_count);
-    }
+    if (dc <= 16) return {2, 4};
+    if (dc <= 32) return {1, 2};
+    return {1};
+}
+
+int launch_class(int dc, int p, BatchInst* insts, const WorkItem* items, int nitems,
+                 int* next_item, cudaStream_t s, int sm_count)
+{
+#define KM2_BA(DD, PP) \
+    if (dc == DD && p == PP) return launch_batch_assign<DD, PP>(insts, items, nitems, next_item, s, sm_count);
+    KM2_BA(2, 2) KM2_BA(2, 4) KM2_BA(4, 2) KM2_BA(4, 4) KM2_BA(8, 2) KM2_BA(8, 4)
+    KM2_BA(16, 2) KM2_BA(16, 4) KM2_BA(32, 1) KM2_BA(32, 2) KM2_BA(64, 1)
+#undef KM2_BA
+    set_last_error_text("batched form: no kernel for this tile shape");
+    return KMEANS2_ERR_UNSUPPORTED;
 }
 
 std::mutex g_tune_mu;
-std::map<int, int> g_tuned;          // dimension class -> tiles per work item
+// dimension class -> (points per thread, tiles per work item)
+std::map<int, std::pair<int, int>> g_tuned;
 
 struct ClassItems {
     int dc = 0;
+    int p = 0;
     int tpi = 0;
     std::vector<WorkItem> host;
     WorkItem* dev = nullptr;
@@ -645,6 +704,8 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         KM2_TRY(ws.alloc((void**)&dinst, sizeof(BatchInst) * (size_t)count, s));
         // active, iteration, 6 item counters, active count handed to the host
         KM2_TRY(ws.alloc((void**)&counters, 9 * sizeof(int), s));
+        long long* rprefix = nullptr;      // flat recheck list: per-job offsets, total
+        KM2_TRY(ws.alloc((void**)&rprefix, sizeof(long long) * ((size_t)count + 1), s));
         for (int j = 0; j < count; ++j) {
             const kmeans2_job& J = jobs[j];
             BatchInst& I = hi[j];
@@ -700,45 +761,51 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         for (auto& kv : members) {
             ClassItems ci;
             ci.dc = kv.first;
-            int tpi = 0;
+            int tpi = 0, pts = 0;
             {
                 std::lock_guard<std::mutex> lock(g_tune_mu);
                 auto f = g_tuned.find(ci.dc);
-                if (f != g_tuned.end()) tpi = f->second;
+                if (f != g_tuned.end()) { pts = f->second.first; tpi = f->second.second; }
             }
             if (tpi == 0) {
-                // time the real first pass for a few item sizes, resetting the sums between
-                // small items keep every SM busy once only a few jobs still run
+                // time the real first pass for each tile shape (points per thread)
+                // and item size (tiles per work item), resetting the sums between
+                // trials: small items keep every SM busy once only a few jobs still
+                // run, more points per thread reuse each center load more often
                 const int cand[4] = {1, 2, 4, 8};
                 static_assert(8 <= kMaxTilesPerItem, "item partial sums must stay below 2^62");
                 float best_ms = 0.f;
+                bool first = true;
                 cudaEvent_t e0, e1;
                 KM2_CUDA(cudaEventCreate(&e0));
                 KM2_CUDA(cudaEventCreate(&e1));
-                for (int c = 0; c < 4; ++c) {
-                    ClassItems trial;
-                    build_items(trial, kv.second, nvec, cand[c]);
-                    KM2_TRY(ws.alloc((void**)&trial.dev, sizeof(WorkItem) * (size_t)trial.count, s));
-                    KM2_CUDA(cudaMemcpyAsync(trial.dev, trial.host.data(),
-                                             sizeof(WorkItem) * (size_t)trial.count,
-                                             cudaMemcpyHostToDevice, s));
-                    KM2_CUDA(cudaMemsetAsync(counters + 2, 0, sizeof(int), s));
-                    KM2_CUDA(cudaEventRecord(e0, s));
-                    KM2_TRY(launch_class(ci.dc, dinst, trial.dev, trial.count, counters + 2, s,
-                                         ws.sm_count));
-                    KM2_CUDA(cudaEventRecord(e1, s));
-                    ++g_launches;
-                    batch_reset_kernel<<<count, kThreads, 0, s>>>(dinst);
-                    KM2_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    KM2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (c == 0 || ms < best_ms) { best_ms = ms; tpi = cand[c]; }
+                for (int p : tile_points(ci.dc)) {
+                    for (int c = 0; c < 4; ++c) {
+                        ClassItems trial;
+                        build_items(trial, kv.second, nvec, cand[c]);
+                        KM2_TRY(ws.alloc((void**)&trial.dev, sizeof(WorkItem) * (size_t)trial.count, s));
+                        KM2_CUDA(cudaMemcpyAsync(trial.dev, trial.host.data(),
+                                                 sizeof(WorkItem) * (size_t)trial.count,
+                                                 cudaMemcpyHostToDevice, s));
+                        KM2_CUDA(cudaMemsetAsync(counters + 2, 0, sizeof(int), s));
+                        KM2_CUDA(cudaEventRecord(e0, s));
+                        KM2_TRY(launch_class(ci.dc, p, dinst, trial.dev, trial.count, counters + 2,
+                                             s, ws.sm_count));
+                        KM2_CUDA(cudaEventRecord(e1, s));
+                        ++g_launches;
+                        batch_reset_kernel<<<count, kThreads, 0, s>>>(dinst);
+                        KM2_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        KM2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        if (first || ms < best_ms) { best_ms = ms; tpi = cand[c]; pts = p; first = false; }
+                    }
                 }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 std::lock_guard<std::mutex> lock(g_tune_mu);
-                g_tuned[ci.dc] = tpi;
+                g_tuned[ci.dc] = std::make_pair(pts, tpi);
             }
+            ci.p = pts;
             build_items(ci, kv.second, nvec, tpi);
             KM2_TRY(ws.alloc((void**)&ci.dev, sizeof(WorkItem) * (size_t)ci.count, s));
             KM2_CUDA(cudaMemcpyAsync(ci.dev, ci.host.data(), sizeof(WorkItem) * (size_t)ci.count,
@@ -768,7 +835,8 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             if (cudaEventRecord(fork, s) != cudaSuccess) return KMEANS2_ERR_CUDA;
             for (size_t c = 0; c < classes.size(); ++c) {
                 if (cudaStreamWaitEvent(side[c], fork, 0) != cudaSuccess) return KMEANS2_ERR_CUDA;
-                const int r = launch_class(classes[c].dc, dinst, classes[c].dev, classes[c].count,
+                const int r = launch_class(classes[c].dc, classes[c].p, dinst, classes[c].dev,
+                                           classes[c].count,
                                            counters + 2 + c, side[c], ws.sm_count);
                 if (r != KMEANS2_OK) return r;
                 if (cudaEventRecord(joins[c], side[c]) != cudaSuccess) return KMEANS2_ERR_CUDA;
@@ -788,8 +856,9 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
                 rc = launch_classes();
                 if (rc != KMEANS2_OK) break;
                 cudaEventRecord(e1, s);
-                ++g_launches;
-                batch_recheck_kernel<<<count, kThreads, 0, s>>>(dinst);
+                g_launches += 2;
+                batch_recheck_scan_kernel<<<1, 1024, 0, s>>>(dinst, count, rprefix);
+                batch_recheck_flat_kernel<<<ws.sm_count * 4, kThreads, 0, s>>>(dinst, count, rprefix);
                 ++g_launches;
                 batch_finalize_kernel<<<count, kThreads, 0, s>>>(dinst, counters);
                 ++g_launches;
@@ -833,7 +902,8 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             if (e != cudaSuccess) { set_last_error("cudaStreamBeginCaptureToGraph", e); rc = KMEANS2_ERR_CUDA; break; }
             rc = launch_classes();
             if (rc == KMEANS2_OK) {
-                batch_recheck_kernel<<<count, kThreads, 0, s>>>(dinst);
+                batch_recheck_scan_kernel<<<1, 1024, 0, s>>>(dinst, count, rprefix);
+                batch_recheck_flat_kernel<<<ws.sm_count * 4, kThreads, 0, s>>>(dinst, count, rprefix);
                 batch_finalize_kernel<<<count, kThreads, 0, s>>>(dinst, counters);
                 batch_control_kernel<<<1, 1, 0, s>>>(counters, counters + 1, counters + 2,
                                                      (int)classes.size(), cap,
@@ -857,7 +927,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             int iters = 0;
             KM2_CUDA(cudaMemcpyAsync(&iters, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
             KM2_CUDA(cudaStreamSynchronize(s));
-            g_launches += (long long)iters * ((long long)classes.size() + 3);
+            g_launches += (long long)iters * ((long long)classes.size() + 4);
         }
         if (rc == KMEANS2_OK) {
             // ---- results

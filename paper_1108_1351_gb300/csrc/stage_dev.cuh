@@ -388,90 +388,98 @@ static __device__ __forceinline__ void recheck_d4(const float* __restrict__ x, i
     }
 }
 
-// One warp per listed point.  Pass 1: FP32 D_j for every center on the CUDA
+// One warp: re-decide point i.  Pass 1: FP32 D_j for every center on the CUDA
 // cores (recheck_d4) and their minimum b1.  Pass 2: every center with
 // D_j <= b1 + tie_kappa (2 C2 + X2) -- a set that provably holds the FP64
 // argmin -- is evaluated exactly in the oracle's form (sum_t fma(x_t - c_t,
 // x_t - c_t, acc), t ascending) and the smallest wins, lowest index on ties.
+// The point's new label and the sums follow (delta mode: from its old label).
 // cache: per-warp shared memory of cache_cap floats for the pass-1 values
 // (pass 2 recomputes them when kpad > cache_cap or cache is null).
-// Warps w0, w0 + wstride, ... of the caller each take the listed points.
-static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers c,
-                                     int* __restrict__ labels, const int* __restrict__ list,
-                                     StageState* st, Accum acc, long long gw, long long nw,
-                                     float* cache, int cache_cap)
+static __device__ __forceinline__ void recheck_point(const float* __restrict__ X, int d,
+                                                     const Centers& c, int* __restrict__ labels,
+                                                     int i, StageState* st, const Accum& acc,
+                                                     float* cache, int cache_cap)
 {
-    const int count = st->recheck_count;
     const int mode = st->mode;
     const float scaleF = st->scaleF;
     const float c2x2 = 2.0f * st->cmax2;
     const float kap = tie_kappa(d);
     const int k = c.k;
     const bool cached = cache != nullptr && c.kpad <= cache_cap;
-    int lane = threadIdx.x & 31;
-    for (long long w = gw; w < count; w += nw) {
-        int i = list[w];
-        const float* x = X + (long long)i * d;
-        float x2 = 0.0f;
-        for (int t = lane; t < d; t += 32) { float v = __ldg(x + t); x2 = fmaf(v, v, x2); }
-        for (int o = 16; o; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
-        float b1 = INFINITY;
-        for (int j0 = lane; j0 < k; j0 += 128) {
-            float a[4];
+    const int lane = threadIdx.x & 31;
+    const float* x = X + (long long)i * d;
+    float x2 = 0.0f;
+    for (int t = lane; t < d; t += 32) { float v = __ldg(x + t); x2 = fmaf(v, v, x2); }
+    for (int o = 16; o; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    float b1 = INFINITY;
+    for (int j0 = lane; j0 < k; j0 += 128) {
+        float a[4];
+        recheck_d4(x, d, c, j0, a);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (j0 + 32 * q < k) b1 = fminf(b1, a[q]);
+            if (cached) cache[j0 + 32 * q] = a[q];
+        }
+    }
+    for (int o = 16; o; o >>= 1) b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+    const float lim = b1 + kap * (c2x2 + x2) * 1.0009765625f;
+    double best = DBL_MAX;
+    int bj = INT_MAX;
+    for (int j0 = lane; j0 < k; j0 += 128) {
+        float a[4];
+        if (cached) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = cache[j0 + 32 * q];
+        } else {
             recheck_d4(x, d, c, j0, a);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (j0 + 32 * q < k) b1 = fminf(b1, a[q]);
-                if (cached) cache[j0 + 32 * q] = a[q];
-            }
         }
-        for (int o = 16; o; o >>= 1) b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
-        const float lim = b1 + kap * (c2x2 + x2) * 1.0009765625f;
-        double best = DBL_MAX;
-        int bj = INT_MAX;
-        for (int j0 = lane; j0 < k; j0 += 128) {
-            float a[4];
-            if (cached) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) a[q] = cache[j0 + 32 * q];
-            } else {
-                recheck_d4(x, d, c, j0, a);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = j0 + 32 * q;
-                if (j < k && a[q] <= lim) {
-                    const double* cj64 = c.c64 + (long long)j * d;
-                    double a2 = 0.0;
-                    for (int t = 0; t < d; ++t) {
-                        double e = (double)__ldg(x + t) - cj64[t];
-                        a2 = fma(e, e, a2);
-                    }
-                    if (a2 < best || (a2 == best && j < bj)) { best = a2; bj = j; }
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + 32 * q;
+            if (j < k && a[q] <= lim) {
+                const double* cj64 = c.c64 + (long long)j * d;
+                double a2 = 0.0;
+                for (int t = 0; t < d; ++t) {
+                    double e = (double)__ldg(x + t) - cj64[t];
+                    a2 = fma(e, e, a2);
                 }
-            }
-        }
-        for (int o = 16; o; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
-        }
-        int old = (mode == kModeDelta) ? labels[i] : -1;
-        __syncwarp();   // every lane has read the old label before lane 0 rewrites it
-        if (bj != old && label_ok(bj, k, st) && old_label_ok(old, k, st)) {
-            for (int t = lane; t < d; t += 32) {
-                long long v = to_fixed(__ldg(x + t), scaleF);
-                split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, v);
-                if (old >= 0)
-                    split_add(acc.s_lo + (long long)old * d + t, acc.s_hi + (long long)old * d + t, -v);
-            }
-            if (lane == 0) {
-                atomicAdd(acc.cnt + bj, 1ull);
-                if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
-                labels[i] = bj;
+                if (a2 < best || (a2 == best && j < bj)) { best = a2; bj = j; }
             }
         }
     }
+    for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+    }
+    int old = (mode == kModeDelta) ? labels[i] : -1;
+    __syncwarp();   // every lane has read the old label before lane 0 rewrites it
+    if (bj != old && label_ok(bj, k, st) && old_label_ok(old, k, st)) {
+        for (int t = lane; t < d; t += 32) {
+            long long v = to_fixed(__ldg(x + t), scaleF);
+            split_add(acc.s_lo + (long long)bj * d + t, acc.s_hi + (long long)bj * d + t, v);
+            if (old >= 0)
+                split_add(acc.s_lo + (long long)old * d + t, acc.s_hi + (long long)old * d + t, -v);
+        }
+        if (lane == 0) {
+            atomicAdd(acc.cnt + bj, 1ull);
+            if (old >= 0) atomicAdd(acc.cnt + old, ~0ull);
+            labels[i] = bj;
+        }
+    }
+}
+
+// One warp per listed point (recheck_point); warps w0, w0 + wstride, ... of
+// the caller each take the listed points.
+static __device__ void recheck_warps(const float* __restrict__ X, int d, Centers c,
+                                     int* __restrict__ labels, const int* __restrict__ list,
+                                     StageState* st, Accum acc, long long gw, long long nw,
+                                     float* cache, int cache_cap)
+{
+    const int count = st->recheck_count;
+    for (long long w = gw; w < count; w += nw)
+        recheck_point(X, d, c, labels, list[w], st, acc, cache, cache_cap);
 }
 
 
