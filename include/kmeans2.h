@@ -41,10 +41,12 @@
  *    distances are farther apart than a rigorous rounding-error bound; the
  *    other points are re-evaluated in exactly that FP64 form.
  *  - Cluster sums are exact integer (fixed-point) sums of the FP32 inputs at a
- *    per-stage scale 2^F, F = 46 - E with E the smallest integer such that
- *    max|x| < 2^E (so a center is off the exact mean by at most 2^-(F+1) per
- *    coordinate, plus the FP64 rounding of the division), which makes every
- *    mode deterministic: results do not depend on thread scheduling.
+ *    per-stage scale 2^F, F = min(120, 46 - E) with E the smallest integer
+ *    such that max|x| < 2^E (so a center is off the exact mean by at most
+ *    2^-(F+1) per coordinate, plus the FP64 rounding of the division), which
+ *    makes every mode deterministic: results do not depend on thread
+ *    scheduling.  The cap keeps 2^F a finite FP32 scale: data with max|x| <
+ *    2^-74 keep the absolute grid 2^-120 and so fewer than 46 bits.
  *  - J (Eq. 3) is formed on the same fixed-point values, without cancellation:
  *    J = W + M with W = (sum_i ||s_i||^2 - sum_j ||s_j||^2 / N_j) 2^-2F, where s
  *    are the integer coordinates and s_j their exact cluster sums (exact

@@ -447,7 +447,8 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             }
             const bool in_ring = (long long)row < ((a.n - tile * kRows) & ~3ll);
             const float xx = valid ? (in_ring ? side.xn2[r][row] : __ldg(a.xn2 + p)) : 0.0f;
-            const float thr = a.kappa * (thr_base + xx) + a.kpack * (fabsf(B1) + fabsf(B2));
+            const float thr = a.kappa * (thr_base + xx) + tie_abs(3 * d + 3) +
+                              a.kpack * (fabsf(B1) + fabsf(B2));
             const bool flag = valid && (B2 - B1 <= thr);
             {
                 const unsigned m = __ballot_sync(0xffffffffu, flag);

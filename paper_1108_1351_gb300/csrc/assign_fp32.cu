@@ -267,7 +267,8 @@ assign_small(const float* __restrict__ X, long long n, Centers c, int* __restric
         for (int p = 0; p < P; ++p) {
             const long long i = base + (long long)p * kThreads + tid;
             const bool valid = i < n;
-            const float thr = kappa * (thr_base + xn2[p]) + kpack * (fabsf(B1[p]) + fabsf(B2[p]));
+            const float thr = kappa * (thr_base + xn2[p]) + tie_abs(D + 1) +
+                              kpack * (fabsf(B1[p]) + fabsf(B2[p]));
             const bool flag = valid && (B2[p] - B1[p] <= thr);
             recheck_append(flag, (int)i, list, &st->recheck_count);
             if (valid && !flag && label_ok(BI[p], k, st) && old_label_ok(oldl[p], k, st)) {
@@ -459,7 +460,7 @@ assign_large(const float* __restrict__ X, long long n, int d, Centers c, int* __
         for (int r = 0; r < 8; ++r) {
             const long long i = base + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
             const bool valid = i < n;
-            const bool flag = valid && (b2[r] - b1[r] <= kappa * (c2x2 + xn2[r]));
+            const bool flag = valid && (b2[r] - b1[r] <= kappa * (c2x2 + xn2[r]) + tie_abs(d + 1));
             recheck_append(flag && tx == 0, (int)i, list, &st->recheck_count);
             if (!valid) continue;
             const float* xr = X + i * d;

@@ -534,7 +534,8 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                 float xn2 = 0.f;
 #pragma unroll
                 for (int e = 0; e < D; ++e) xn2 = fmaf(x[e], x[e], xn2);
-                const float thr = kappa * (thr_base + xn2) + kpack * (fabsf(B1[t]) + fabsf(B2[t]));
+                const float thr = kappa * (thr_base + xn2) + tie_abs(3 * D + 3) +
+                                  kpack * (fabsf(B1[t]) + fabsf(B2[t]));
                 bool flag = valid && (B2[t] - B1[t] <= thr);
                 int lab = BI[t];
                 if (flag) {
@@ -542,7 +543,7 @@ assign_tc32(const float* __restrict__ X, long long n, Centers c, int* __restrict
                     // and its tighter bound; FP64 only if that cannot decide
                     float f1, f2;
                     fp32_top2<D>(x, c, f1, f2, lab);
-                    flag = f2 - f1 <= kappa32 * (thr_base + xn2);
+                    flag = f2 - f1 <= kappa32 * (thr_base + xn2) + tie_abs(D + 1);
                 }
                 {
                     const unsigned m = __ballot_sync(0xffffffffu, flag);

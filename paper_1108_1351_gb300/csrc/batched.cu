@@ -366,7 +366,8 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
                     float xn2 = 0.f;
 #pragma unroll
                     for (int t = 0; t < DC; ++t) xn2 = fmaf(x[p][t], x[p][t], xn2);
-                    const float thr = kappa * (thr_base + xn2) + kPackSlack * (fabsf(B1[p]) + fabsf(B2[p]));
+                    const float thr = kappa * (thr_base + xn2) + tie_abs(d + 1) +
+                                      kPackSlack * (fabsf(B1[p]) + fabsf(B2[p]));
                     const bool flag = valid && (B2[p] - B1[p] <= thr);
                     if (mode == kModeFull && valid) {
 #pragma unroll

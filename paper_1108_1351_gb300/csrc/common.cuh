@@ -243,6 +243,19 @@ __host__ __device__ inline float tie_kappa(int d)
     return 2.0f * (float)(d + 3) * 5.9604644775390625e-8f * 1.0625f;
 }
 
+// Absolute floor of the near-tie bound.  The relative bounds above hold for
+// FP32 values in the normal range; below 2^-126 a result keeps an absolute
+// error of up to 2^-126 (IEEE subnormal rounding on the CUDA cores, possible
+// flushing to zero inside the tensor cores), and a packed key adds at most 31
+// subnormal steps.  With nt products per key, each rounded and accumulated,
+// two keys lose at most (4 nt + 16) 2^-126 more: for data of ordinary size
+// this is far below the relative term; for tiny data (max|x| below about
+// 2^-50) it takes over and flags more points, which the FP64 recheck decides.
+__host__ __device__ inline float tie_abs(int nt)
+{
+    return (float)(4 * nt + 16) * 1.1754943508222875e-38f;
+}
+
 // The small-d kernel compares packed keys: D_j with the center's index within
 // its chunk of 32 written into the 5 low mantissa bits, compared as floats.  A
 // key differs from D_j by less than 2^-18 |D_j|, so the two keys of a point

@@ -390,7 +390,7 @@ static __device__ __forceinline__ void recheck_d4(const float* __restrict__ x, i
 
 // One warp: re-decide point i.  Pass 1: FP32 D_j for every center on the CUDA
 // cores (recheck_d4) and their minimum b1.  Pass 2: every center with
-// D_j <= b1 + tie_kappa (2 C2 + X2) -- a set that provably holds the FP64
+// D_j <= b1 + tie_kappa (2 C2 + X2) + tie_abs -- a set that provably holds the FP64
 // argmin -- is evaluated exactly in the oracle's form (sum_t fma(x_t - c_t,
 // x_t - c_t, acc), t ascending) and the smallest wins, lowest index on ties.
 // The point's new label and the sums follow (delta mode: from its old label).
@@ -423,7 +423,7 @@ static __device__ __forceinline__ void recheck_point(const float* __restrict__ X
         }
     }
     for (int o = 16; o; o >>= 1) b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
-    const float lim = b1 + kap * (c2x2 + x2) * 1.0009765625f;
+    const float lim = b1 + kap * (c2x2 + x2) * 1.0009765625f + tie_abs(d + 1);
     double best = DBL_MAX;
     int bj = INT_MAX;
     for (int j0 = lane; j0 < k; j0 += 128) {

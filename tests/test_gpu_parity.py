@@ -158,6 +158,27 @@ def test_step_far_from_origin_forces_rechecks():
 
 
 @pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16"])
+def test_step_below_the_fixed_point_range(form):
+    # max|x| ~ 1e-29 < 2^-74: the fixed-point scale stays at its cap 2^120, so
+    # the cluster sums keep about 20 bits here.  Labels are still the oracle's;
+    # centers meet the capped grid and J its rounding bound: each coordinate
+    # moves by at most 2^-121 on the grid, i.e. |J - J_o| <= 1e-9 J_o +
+    # 2^-120 sum_i ||x_i - c||_1 + n d 2^-242 (plus the same for the centers).
+    X0 = _mixture(40_000, 32, 20, seed=43, spread=3.0)
+    C = _centers_from(X0, 20, seed=4, jitter=0.3)
+    X = (X0 * np.float32(1e-30)).astype(np.float32)
+    C = C * 1e-30
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision=form)
+    ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
+    assert np.array_equal(to_np(lab), olab)
+    assert_centers_close(to_np(cn), ocn, X)
+    l1 = float(np.abs(X.astype(np.float64) - C[olab]).sum() + np.abs(X.astype(np.float64) - ocn[olab]).sum())
+    assert abs(J - oJ) <= 1e-9 * oJ + 2.0 ** -120 * l1 + 2 * X.size * 2.0 ** -242, (J, oJ)
+    assert em == oem
+
+
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16"])
 def test_step_far_from_origin_each_form(form):
     # x ~ 1e3 +- 1e-2 in d = 16: sum ||x||^2 / J ~ 1e10, so J must be formed
     # without cancellation to meet 1e-9 relative
