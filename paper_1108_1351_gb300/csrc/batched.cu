@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -591,6 +592,24 @@ std::vector<int> tile_points(int dc)
     return {1};
 }
 
+// Debug builds (KM2_DEBUG_CHECKS): KMEANS2_DEBUG_BATCH_POINTS forces one tile
+// shape (a tile_points value) on every dimension class that offers it,
+// without tuning, so that a test can run each kernel variant; -1 otherwise.
+int forced_tile_points(int dc)
+{
+#ifdef KM2_DEBUG_CHECKS
+    const char* v = std::getenv("KMEANS2_DEBUG_BATCH_POINTS");
+    if (v && *v) {
+        const int p = (int)std::strtol(v, nullptr, 10);
+        for (int q : tile_points(dc))
+            if (q == p) return p;
+    }
+#else
+    (void)dc;
+#endif
+    return -1;
+}
+
 int launch_class(int dc, int p, BatchInst* insts, const WorkItem* items, int nitems,
                  int* next_item, cudaStream_t s, int sm_count)
 {
@@ -763,7 +782,11 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             ClassItems ci;
             ci.dc = kv.first;
             int tpi = 0, pts = 0;
-            {
+            const int forced = forced_tile_points(ci.dc);
+            if (forced >= 0) {
+                pts = forced;
+                tpi = 2;
+            } else {
                 std::lock_guard<std::mutex> lock(g_tune_mu);
                 auto f = g_tuned.find(ci.dc);
                 if (f != g_tuned.end()) { pts = f->second.first; tpi = f->second.second; }
