@@ -126,6 +126,9 @@ def test_server_host_buffers():
 
 def test_server_admits_arrivals_while_running():
     # a long job first; a short one arriving while it runs starts before it ends
+    # (when it finishes depends on how the GPU interleaves the two jobs'
+    # kernels: the long job's persistent tensor-core kernel fills every SM
+    # while it runs, so the short job advances only between its launches)
     XA = _data(2_000_000, 128, 1024, 41)
     XB = _data(20_000, 4, 8, 42)
     with km.Server(max_slots=2) as srv:
@@ -138,7 +141,6 @@ def test_server_admits_arrivals_while_running():
         a = srv.wait(ta)
     assert a.status == 0 and b.status == 0
     assert b.t_admit < a.t_done
-    assert b.t_done < a.t_done
     _same(b.result, km.fit(XB, 8, 0.1, 42, 1e-6, 50))
 
 
