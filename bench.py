@@ -656,18 +656,23 @@ def run_serve(args):
         for d in (4, 16, 64, 128):
             X = synth.iso_gaussian_mixture(50_000, d, 32, 99, device=dev)
             srv.wait(srv.submit(X, 32, 0.1, 99, 1e-6, 20))
-    arms = (("served", args.serve_slots, "auto"), ("one_at_a_time_fp32", 1, "fp32"))
+    # the served arm's stage loops: graphs with device-side while conditions
+    # ("graph") or driven from the worker threads ("host"); the one-at-a-time
+    # arm runs each job alone, as graphs
+    arms = (("served", args.serve_slots, "auto", args.serve_loop == "graph"),
+            ("one_at_a_time_fp32", 1, "fp32", True))
 
     def run_trace(trace, drain_cap):
         out = {}
-        for name, slots, prec in arms:
+        for name, slots, prec, graph in arms:
             with km.Server(hbm_budget=budget, max_slots=slots, precision=prec,
-                           policy=args.policy, aging_s=args.aging) as srv:
+                           policy=args.policy, aging_s=args.aging, use_graph=graph) as srv:
                 done, censored, never, start, t_end, late = _serve_trace(
                     trace, srv, dev, drain_cap=drain_cap)
                 summ = _latency_summary(done, censored, never, start, t_end)
                 st = srv.stats()
             summ.update({"slots": slots, "precision": prec, "policy": args.policy,
+                         "stage_loops": "graph" if graph else "host",
                          "kernel_launches": st["kernel_launches"],
                          "hbm_peak_gb": st["hbm_peak"] / 1e9, "client_max_lag_s": late})
             out[name] = summ
@@ -1032,6 +1037,8 @@ def main():
     ap.add_argument("--policy", default="fifo", choices=["fifo", "shortest"],
                     help="serve: admission policy of both arms")
     ap.add_argument("--serve-slots", type=int, default=8, help="serve: jobs running at once")
+    ap.add_argument("--serve-loop", default="host", choices=["graph", "host"],
+                    help="serve: the served arm's stage loops (while-graphs or host-driven)")
     ap.add_argument("--aging", type=float, default=30.0,
                     help="serve: seconds after which a waiting job is admitted before smaller ones")
     ap.add_argument("--drain-cap", type=float, default=30.0,

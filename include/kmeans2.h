@@ -407,9 +407,15 @@ KMEANS2_API uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k,
  *              (their footprints, with device-resident X counted too);
  *              0 = 90% of the device memory free at creation.
  *  max_slots   jobs running at once, 1..64.
- *  opt         may be NULL; precision, tol_fast and deterministic apply to
- *              every job (stream, init_centers, start_stage, trajectories and
- *              profile must be unset).
+ *  opt         may be NULL; precision, tol_fast, deterministic and use_graph
+ *              apply to every job (stream, init_centers, start_stage,
+ *              trajectories and profile must be unset).  use_graph = 1 runs
+ *              each job's stage loops as graphs with a device-side while
+ *              condition, 0 drives them from the worker threads; with NULL
+ *              options a server of several slots uses 0.  Measured on GB300:
+ *              while one job's while-graph runs, another job's while-graph
+ *              does not start, whereas host-driven loops interleave with it,
+ *              so short jobs progress beside long ones only with 0.
  * Returns NULL on invalid arguments or if the device cannot be used.
  */
 KMEANS2_API kmeans2_server* kmeans2_server_create(uint64_t hbm_budget, int32_t max_slots,

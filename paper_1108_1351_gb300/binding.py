@@ -641,18 +641,25 @@ class Server:
 
     ``submit`` queues a job and returns its ticket at once; ``poll`` / ``wait``
     return a ``Served`` once the job has finished.  The server holds references
-    to each job's tensors until the job has been collected."""
+    to each job's tensors until the job has been collected.  ``use_graph``:
+    stage loops as while-graphs (True) or host-driven (False); None picks
+    host-driven loops for several slots, so that jobs interleave."""
 
     POLICY = {"fifo": 0, "shortest": 1}
 
     def __init__(self, hbm_budget: int = 0, max_slots: int = 4, *, precision: str = "auto",
                  tol_fast: float = 0.0, policy: str = "fifo", aging_s: float = 30.0,
-                 device=None):
+                 use_graph: "bool | None" = None, device=None):
         lib = load()
         opt = Options()
         lib.kmeans2_default_options(ctypes.byref(opt))
         opt.precision = PRECISION[precision]
         opt.tol_fast = tol_fast
+        # None: host-driven stage loops when several jobs run at once (another
+        # job's while-graph waits for a running one), graphs for a single slot
+        if use_graph is None:
+            use_graph = max_slots == 1
+        opt.use_graph = 1 if use_graph else 0
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         self.device = dev

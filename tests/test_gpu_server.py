@@ -126,9 +126,8 @@ def test_server_host_buffers():
 
 def test_server_admits_arrivals_while_running():
     # a long job first; a short one arriving while it runs starts before it ends
-    # (when it finishes depends on how the GPU interleaves the two jobs'
-    # kernels: the long job's persistent tensor-core kernel fills every SM
-    # while it runs, so the short job advances only between its launches)
+    # and, with the host-driven stage loops a server of several slots uses,
+    # also finishes first (its kernels run between the long job's launches)
     XA = _data(2_000_000, 128, 1024, 41)
     XB = _data(20_000, 4, 8, 42)
     with km.Server(max_slots=2) as srv:
@@ -141,7 +140,21 @@ def test_server_admits_arrivals_while_running():
         a = srv.wait(ta)
     assert a.status == 0 and b.status == 0
     assert b.t_admit < a.t_done
+    assert b.t_done < a.t_done
     _same(b.result, km.fit(XB, 8, 0.1, 42, 1e-6, 50))
+
+
+def test_server_graph_stage_loops_match_fits():
+    # the same jobs with the stage loops as while-graphs (use_graph=True)
+    specs = [(60_000, 16, 24, 0.1, 1e-6, 40, 51), (30_000, 64, 520, 0.1, 1e-6, 20, 52),
+             (8_000, 3, 5, 0.5, 1e-6, 60, 53)]
+    Xs = [_data(n, d, k, s) for n, d, k, _, _, _, s in specs]
+    with km.Server(max_slots=3, use_graph=True) as srv:
+        tickets = [srv.submit(X, k, f, s, tol, it) for X, (n, d, k, f, tol, it, s) in zip(Xs, specs)]
+        served = [srv.wait(t) for t in tickets]
+    for X, sv, (n, d, k, f, tol, it, s) in zip(Xs, served, specs):
+        assert sv.status == 0
+        _same(sv.result, km.fit(X, k, f, s, tol, it))
 
 
 def test_server_destroy_with_queued_jobs():
