@@ -121,7 +121,10 @@ typedef struct kmeans2_options {
                                    1 = skip the fast stage (resume a slow stage) */
     int32_t use_graph;          /* 1 (default when options are NULL): run each stage
                                    loop as one CUDA graph with a device-side while
-                                   loop; 0: one host round trip per iteration */
+                                   loop; 0: one host round trip per iteration.
+                                   Fits meant to run side by side on several
+                                   streams should use 0: on GB300 a second
+                                   while-graph waits for a running one to end */
     void* stream;               /* cudaStream_t, NULL = legacy default stream */
     /* Optional HOST arrays of capacity max_iter receiving one value per
        iteration (Figs. 4-11 and Table 1 track exactly these trajectories). */
