@@ -343,8 +343,9 @@ def test_release_memory_between_fits_keeps_results():
 
 @pytest.mark.parametrize("form", ["fp32", "bf16"])
 def test_step_many_near_ties_with_many_centers(form):
-    # far from the origin with k * d >= 32768: thousands of flagged points go
-    # through the recheck that takes eight points per warp; labels stay exact
+    # far from the origin with k * d = 38400: thousands of flagged points go
+    # through the FP64 recheck (each reading all k d FP32 center values);
+    # labels stay exact
     rng = np.random.default_rng(21)
     n, d, k = 30000, 64, 600
     X = (200.0 + rng.normal(size=(n, d)) * 0.05).astype(np.float32)
