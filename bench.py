@@ -207,10 +207,16 @@ def roofline_of(form: str, d: int, k: int, prof, clk, p32=None):
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     achieved = prof.assign_flops / (prof.assign_ms * 1e-3) / 1e12 if prof.assign_ms > 0 else None
-    if form == "bf16":
+    if form in ("bf16", "fp16"):
         kernel, bound = "assign_bf16", "tensor"
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_source = f"{src} bf16_tflops_sustained (kernel timed inside a long fit)"
+        if form == "fp16":
+            # the single-pass instantiation (its time includes the split-BF16
+            # second pass over the rows it leaves undecided)
+            nc = 256 if k >= 512 else (128 if k > 64 else 64)
+            kernel = f"assign_bf16<{nc},1>"
+            peak_source += "; dense FP16 and BF16 tensor rates are equal (nominal)"
     elif form == "tf32x3":
         kernel, bound = "assign_tc32", "tensor"
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * TF32_PER_BF16
@@ -1052,7 +1058,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--parallelism", default="sharded", choices=["sharded", "replicas"],
                     help="N > 1: one row-sharded fit over NCCL, or one replica per rank")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "tf32x3"],
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "fp16", "tf32x3"],
                     help="distance-kernel form (every form returns the same labels)")
     args = ap.parse_args()
     if args.config == "sharded":

@@ -96,6 +96,11 @@ extern "C" {
 #define KMEANS2_PRECISION_TF32X3 3    /* cross term on the tensor cores as three TF32
                                          products of the exact hi/lo split of the FP32
                                          operands; d in {4, 8, 16, 32}, k <= 256 */
+#define KMEANS2_PRECISION_FP16 4      /* cross term on the tensor cores in one FP16 pass
+                                         (operands scaled by powers of two into the FP16
+                                         range, one product, FP32 accumulation); rows
+                                         inside its bound are re-run in the split-BF16
+                                         form before the FP64 recheck; same shapes as BF16 */
 
 /* Optional per-call measurement, filled by the library when options->profile
    is set.  A profiled call runs each stage loop from the host (no graph) and

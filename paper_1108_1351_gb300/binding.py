@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libkmeans2_debug.so" if os.environ.get("KMEANS2_
                         else "libkmeans2.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "kmeans2.h")
 
-PRECISION = {"fp32": 0, "bf16": 1, "auto": 2, "tf32x3": 3}
+PRECISION = {"fp32": 0, "bf16": 1, "auto": 2, "tf32x3": 3, "fp16": 4}
 _lock = threading.Lock()
 _lib = None
 
@@ -411,7 +411,7 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                      subset_size=res.subset_size, rechecked_points=res.rechecked_points,
                      distance_evals=res.distance_evals, shift_fast=res.shift_fast,
                      shift_slow=res.shift_slow, seconds=res.seconds,
-                     precision_used={0: "fp32", 1: "bf16", 3: "tf32x3"}.get(res.precision_used, "?"),
+                     precision_used={0: "fp32", 1: "bf16", 3: "tf32x3", 4: "fp16"}.get(res.precision_used, "?"),
                      traj=traj)
 
 
@@ -611,7 +611,7 @@ def _fit_result(r, cen, lab, traj=None) -> FitResult:
                      subset_size=r.subset_size, rechecked_points=r.rechecked_points,
                      distance_evals=r.distance_evals, shift_fast=r.shift_fast,
                      shift_slow=r.shift_slow, seconds=r.seconds,
-                     precision_used={0: "fp32", 1: "bf16", 3: "tf32x3"}.get(r.precision_used, "?"),
+                     precision_used={0: "fp32", 1: "bf16", 3: "tf32x3", 4: "fp16"}.get(r.precision_used, "?"),
                      traj=traj or {})
 
 

@@ -234,19 +234,35 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     // padding centers: the largest finite key, so that packing an index into
     // its low mantissa bits never makes a NaN and it never wins or ties
     KM2_TRY(fill_f32(w.c.cnorm, cn_len, FLT_MAX, s));
-    if (w.form == KMEANS2_PRECISION_BF16)
-        KM2_TRY(ws.alloc((void**)&w.cb, bf16_cb_bytes(d, k), s));
+    if (tc16_form(w.form))
+        KM2_TRY(ws.alloc((void**)&w.cb,
+                         bf16_cb_bytes(d, k, w.form == KMEANS2_PRECISION_FP16), s));
     return KMEANS2_OK;
 }
 
-// BF16 form: per-stage copy of the stage's points as BF16 tiles + ||x||^2.
+// 16-bit tensor-core forms: per-stage copy of the stage's points as BF16
+// (FP16) tiles + ||x||^2.  After stage_init: the FP16 scale depends on F.
 int prepare_stage_points(const float* X, long long n, int d, Workspace& w, DeviceScratch& ws,
                          cudaStream_t s)
 {
-    if (w.form != KMEANS2_PRECISION_BF16) return KMEANS2_OK;
-    KM2_TRY(ws.alloc((void**)&w.xt, bf16_xt_bytes(n, d), s));
+    if (!tc16_form(w.form)) return KMEANS2_OK;
+    const int single = w.form == KMEANS2_PRECISION_FP16;
+    KM2_TRY(ws.alloc((void**)&w.xt, bf16_xt_bytes(n, d, single), s));
     KM2_TRY(ws.alloc((void**)&w.xn2, (size_t)n * sizeof(float), s));
-    return launch_convert_x_bf16(X, n, d, w.xt, w.xn2, s, ws.sm_count);
+    if (single) {
+        // the second pass's buffers for this stage's undecided rows
+        StageB& b = w.sb;
+        b.cap = stage_b_cap(n);
+        KM2_TRY(ws.alloc((void**)&b.Xc, (size_t)b.cap * d * sizeof(float), s));
+        KM2_TRY(ws.alloc((void**)&b.Xt, bf16_xt_bytes(b.cap, d, 0), s));
+        KM2_TRY(ws.alloc((void**)&b.xn2, (size_t)b.cap * sizeof(float), s));
+        KM2_TRY(ws.alloc((void**)&b.lab, (size_t)b.cap * sizeof(int), s));
+        KM2_TRY(ws.alloc((void**)&b.list, (size_t)b.cap * sizeof(int), s));
+        KM2_TRY(ws.alloc((void**)&b.st, sizeof(StageState), s));
+        KM2_TRY(ws.alloc((void**)&b.nb, sizeof(long long), s));
+        if (!b.cb) KM2_TRY(ws.alloc((void**)&b.cb, bf16_cb_bytes(d, w.c.k, 0), s));
+    }
+    return launch_convert_x_bf16(X, n, d, w.xt, w.xn2, w.st, single, s, ws.sm_count);
 }
 
 // The fused distance kernel of the chosen form.
@@ -255,9 +271,14 @@ int launch_assign(const float* X, long long n, int d, Workspace& w, int* labels,
 {
     if (w.form == KMEANS2_PRECISION_TF32X3)
         return launch_assign_tc32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
-    if (w.form == KMEANS2_PRECISION_BF16)
-        return launch_assign_bf16(X, w.xt, w.xn2, w.cb, n, d, w.c, labels, w.st, w.acc, w.list, s,
-                                  sm_count);
+    if (w.form == KMEANS2_PRECISION_FP16) {
+        KM2_TRY(launch_assign_bf16(X, w.xt, w.xn2, w.cb, n, d, w.c, labels, w.st, w.acc, w.list,
+                                   1, s, sm_count));
+        return launch_stage_b(X, d, w.c, labels, w.st, w.acc, w.list, w.sb, s, sm_count);
+    }
+    if (tc16_form(w.form))
+        return launch_assign_bf16(X, w.xt, w.xn2, w.cb, n, d, w.c, labels, w.st, w.acc, w.list,
+                                  0, s, sm_count);
     return launch_assign_fp32(X, n, d, w.c, labels, w.st, w.acc, w.list, s, sm_count);
 }
 
@@ -275,6 +296,14 @@ int choose_form(int requested, int d, int k, const float* X, int* form)
                 return KMEANS2_ERR_UNSUPPORTED;
             }
             *form = KMEANS2_PRECISION_BF16;
+            return KMEANS2_OK;
+        case KMEANS2_PRECISION_FP16:
+            if (!bf) {
+                set_last_error_text("the FP16 tensor-core form needs d a multiple of 16 in "
+                                    "[16, 128] and 16-byte aligned X");
+                return KMEANS2_ERR_UNSUPPORTED;
+            }
+            *form = KMEANS2_PRECISION_FP16;
             return KMEANS2_OK;
         case KMEANS2_PRECISION_TF32X3:
             if (!tc) {
@@ -611,7 +640,7 @@ uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fr
     add(N * 4);
     add((unsigned long long)kClusSlots * K * 8);
     add(2 * (unsigned long long)max_iter * 8);
-    if (form == KMEANS2_PRECISION_BF16) add(bf16_cb_bytes(d, k));
+    if (tc16_form(form)) add(bf16_cb_bytes(d, k, form == KMEANS2_PRECISION_FP16));
     if (labels_on_host) add(N * 4);
     // fast stage: S_s indices, init positions, X_s, its labels
     add(m * 8);
@@ -626,11 +655,22 @@ uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fr
         add((cnt + 4095) / 4096 * 12);
     }
     add(K * 8);
-    if (form == KMEANS2_PRECISION_BF16) {
-        add(bf16_xt_bytes((long long)m, d));
+    if (tc16_form(form)) {
+        const int single = form == KMEANS2_PRECISION_FP16;
+        add(bf16_xt_bytes((long long)m, d, single));
         add(m * 4);
-        add(bf16_xt_bytes(n, d));
+        add(bf16_xt_bytes(n, d, single));
         add(N * 4);
+        if (single) {   // the second pass: compact rows of both stages, split slices
+            for (long long rows : {(long long)m, (long long)n}) {
+                const unsigned long long cap = (unsigned long long)stage_b_cap(rows);
+                add(cap * D * 4);
+                add(bf16_xt_bytes((long long)cap, d, 0));
+                add(cap * 12);
+                add(sizeof(StageState) + 8);
+            }
+            add(bf16_cb_bytes(d, k, 0));
+        }
     }
     return b + (unsigned long long)allocs * 1024ull + (4ull << 20);
 }

@@ -114,14 +114,37 @@ int launch_assign_tc32(const float* X, long long n, int d, const Centers& c, int
 
 // assign_bf16.cu: tensor-core split-BF16 form, d a multiple of 16 in [16, 128]
 int assign_bf16_supported(int d, int k, const float* X);
-size_t bf16_xt_bytes(long long n, int d);
-size_t bf16_cb_bytes(int d, int k);
+// single = 1: the single-pass FP16 variant (one operand part, scaled by powers
+// of two taken from the stage's fixed-point exponent and max ||c||^2)
+size_t bf16_xt_bytes(long long n, int d, int single);
+size_t bf16_cb_bytes(int d, int k, int single);
 int launch_convert_x_bf16(const float* X, long long n, int d, unsigned char* Xt, float* xn2,
-                          cudaStream_t s, int sm_count);
+                          const StageState* st, int single, cudaStream_t s, int sm_count);
 int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2,
                        unsigned char* Cb, long long n, int d, const Centers& c, int* labels,
-                       StageState* st, const Accum& acc, int* list, cudaStream_t s,
-                       int sm_count);
+                       StageState* st, const Accum& acc, int* list, int single, cudaStream_t s,
+                       int sm_count, const long long* n_dev = nullptr);
+// Second pass of the single-pass FP16 form: buffers for up to `cap` rows that
+// its bound could not decide, re-run through the split-BF16 kernel.
+struct StageB {
+    long long cap = 0;
+    float* Xc = nullptr;          // cap x d FP32 rows
+    unsigned char* Xt = nullptr;  // their split-BF16 tiles
+    float* xn2 = nullptr;         // cap
+    int* lab = nullptr;           // cap
+    int* list = nullptr;          // cap: the pass's own undecided rows
+    StageState* st = nullptr;     // the pass's stage state
+    long long* nb = nullptr;      // rows the pass takes (device)
+    unsigned char* cb = nullptr;  // split-BF16 center slices
+};
+long long stage_b_cap(long long n);
+int launch_stage_b(const float* X, int d, const Centers& c, int* labels, StageState* st,
+                   const Accum& acc, int* list, const StageB& b, cudaStream_t s, int sm_count);
+// the two 16-bit tensor-core forms share the kernel, its tiles and its sizes
+inline bool tc16_form(int form)
+{
+    return form == KMEANS2_PRECISION_BF16 || form == KMEANS2_PRECISION_FP16;
+}
 
 // assign_fp32.cu
 int assign_fp32_supported(int d, int k);
@@ -149,6 +172,7 @@ struct Workspace {
     unsigned char* xt = nullptr;
     float* xn2 = nullptr;
     unsigned char* cb = nullptr;
+    StageB sb{};                   // FP16 form: its second pass
 };
 
 int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, int d,

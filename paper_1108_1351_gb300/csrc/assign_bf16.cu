@@ -42,6 +42,7 @@
 #include <cstdint>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "api_internal.h"
 #include "tc_common.cuh"
@@ -92,6 +93,7 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
 
 struct Bf16Args {
     const float* X;          // FP32 master rows (sums, ||x||^2 in full mode)
+    const long long* n_dev;  // when set, the row count is read here (n is its bound)
     const unsigned char* Xt; // BF16 tiles
     const float* xn2;        // FP32 ||x||^2 per point
     const unsigned char* Cb; // BF16 -2c slices
@@ -100,8 +102,27 @@ struct Bf16Args {
     int lab_bulk;            // old labels can be bulk-copied (16-byte aligned)
     uint32_t tmem_cols;
     float kappa, kpack;
+    float kabs;              // single-pass form: coefficient of the bound's absolute term
     int ctries;              // wait limit of the consumer roles (MMA issuer, epilogue)
 };
+
+// Scales of the single-pass FP16 operands: x as x 2^-a with a = E - 14, where
+// max|x| < 2^E (the stage's recorded max|x|), and m = -2c as m 2^-b with
+// b = Em + 1 - 14, where 2 sqrt(C2) < 2^Em for C2 = st->cmax2 >= max_j
+// ||c_j||^2 (one extra bit covers the rounding of sqrtf).  Every scaled operand
+// stays below 2^14 in magnitude, inside the FP16 range; the accumulator then
+// holds D 2^-(a + b), whose argmin is D's.  The conversion kernels and the
+// epilogue derive a, b and E the same way.
+__device__ __forceinline__ void f16_scales(const StageState* st, int& ea, int& eb, int& E)
+{
+    E = 0;
+    const float mx = __uint_as_float(st->maxabs_bits);
+    if (mx > 0.0f) frexpf(mx, &E);
+    ea = E - 14;
+    int em = 0;
+    frexpf(2.0f * sqrtf(st->cmax2), &em);
+    eb = em + 1 - 14;
+}
 
 // Accumulators per epilogue group: two (MMAs of the next chunk overlap the
 // epilogue of this one) while 2 groups x 2 x NC columns fit in TMEM's 512;
@@ -196,7 +217,10 @@ __device__ __forceinline__ void top2_cols(const uint32_t* r, int j0, float& B1, 
     }
 }
 
-template <int NC>
+// SINGLE = 0: split BF16 (two parts per operand, three MMAs per K-step);
+// SINGLE = 1: one FP16 part per operand (scaled, f16_scales), one MMA per K-step.
+// The norm slice is BF16 in both (its own MMA against the BF16 ones tile).
+template <int NC, int SINGLE>
 __global__ void __launch_bounds__(kThreads, 1)
 assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Accum acc,
             int* __restrict__ list)
@@ -211,14 +235,16 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     if (st->error) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d, nch = a.nch, SB = a.sb;
+    const long long n = a.n_dev ? min(*a.n_dev, a.n) : a.n;
     const int ctries = a.ctries;
     const int mode = st->mode;
     const bool lab_bulk = a.lab_bulk != 0 && mode == kModeDelta;
     const int ksteps = d / 16;
     const int kslices = ksteps + 1;                              // data K-steps + the norm slice
+    constexpr uint32_t kParts = SINGLE ? 1u : 2u;                // operand parts
     const uint32_t Ahalf = (uint32_t)ksteps * 4096u;             // one part of a tile
-    const uint32_t Abytes = 2u * Ahalf;
-    const uint32_t Sbytes = (uint32_t)NC * 64u;                  // one (chunk, K-step) slice
+    const uint32_t Abytes = kParts * Ahalf;
+    const uint32_t Sbytes = (uint32_t)NC * 32u * kParts;         // one (chunk, K-step) slice
     unsigned char* sA = smem;                                    // kSA x Abytes
     unsigned char* sB = smem + kSA * Abytes;                     // SB x Sbytes
     unsigned char* sOnes = sB + (size_t)SB * Sbytes;             // 128 x 16 BF16: [1, 1, 1, 0, ...]
@@ -261,7 +287,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
 
-    const long long ntiles = (a.n + kRows - 1) / kRows;
+    const long long ntiles = (n + kRows - 1) / kRows;
     const long long cnt = (long long)blockIdx.x < ntiles
                               ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
@@ -278,7 +304,7 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 bulk_load(sA + (size_t)s * Abytes, a.Xt + (size_t)tile * Abytes, Abytes,
                           &bars.a_full[s]);
                 // ||x||^2 and old labels of the tile's first rows & ~3 points
-                const long long rows = a.n - tile * kRows < kRows ? a.n - tile * kRows : kRows;
+                const long long rows = n - tile * kRows < kRows ? n - tile * kRows : kRows;
                 const uint32_t vb = (uint32_t)(rows & ~3ll) * 4u;
                 const uint32_t lb = lab_bulk ? vb : 0u;
                 mbar_expect_tx(&bars.side_full[r], vb + lb);
@@ -314,7 +340,8 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     } else if (warp == 2) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = tc::instr_desc(1u, (uint32_t)NC, (uint32_t)kRows);
+            const uint32_t idesc = tc::instr_desc(1u, (uint32_t)NC, (uint32_t)kRows);     // BF16
+            const uint32_t idesc16 = tc::instr_desc(0u, (uint32_t)NC, (uint32_t)kRows);   // FP16
             uint32_t phase = 0u;             // bit b: parity of accumulator b's next use
             long long q = 0;
             bool ok = true;
@@ -340,7 +367,15 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                             break;
                         tc::fence_after_sync();
                         const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes;
-                        if (ks < ksteps) {
+                        if (ks < ksteps && SINGLE) {
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                if (t == 1 && !two) break;
+                                const uint32_t dt = t ? d1 : d0;
+                                const uint32_t ah = sAaddr + (uint32_t)t * Abytes + (uint32_t)ks * 4096u;
+                                tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc16, ks > 0 ? 1u : 0u);
+                            }
+                        } else if (ks < ksteps) {
                             const uint32_t bl = bh + (uint32_t)NC * 32u;
 #pragma unroll
                             for (int t = 0; t < 2; ++t) {
@@ -384,6 +419,17 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
         const float scaleF = st->scaleF;
         const float thr_base = 2.0f * st->cmax2;
+        // single-pass form: the keys are D 2^-(ea + eb); the bound is formed in
+        // unscaled units (with its floor) and scaled the same way
+        const float tabs = tie_abs(SINGLE ? d + 3 : 3 * d + 3);   // products per key
+        int kexp = 0;
+        float kabs = 0.0f;
+        if (SINGLE) {
+            int ea, eb, E;
+            f16_scales(st, ea, eb, E);
+            kexp = -(ea + eb);
+            kabs = ldexpf(a.kabs, 2 * E + kexp) + ldexpf(a.kabs * st->cmax2, kexp) + tabs;
+        }
         int* rq = rqs[ew];
         int rq_n = 0;                                      // warp-uniform queue length
         // hands the queued flagged points to the global recheck list (one atomic)
@@ -439,15 +485,15 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
             // ---- decide row `row` of tile i
             const long long tile = blockIdx.x + i * gridDim.x;
             const long long p = tile * kRows + row;
-            const bool valid = p < a.n;
+            const bool valid = p < n;
             const int r = (int)(i % kSR);
             {
                 const bool w = wait_bar(&bars.side_full[r], (uint32_t)((i / kSR) & 1), abort_v, st, ctries);
                 if (!__all_sync(0xffffffffu, w)) break;
             }
-            const bool in_ring = (long long)row < ((a.n - tile * kRows) & ~3ll);
+            const bool in_ring = (long long)row < ((n - tile * kRows) & ~3ll);
             const float xx = valid ? (in_ring ? side.xn2[r][row] : __ldg(a.xn2 + p)) : 0.0f;
-            const float thr = a.kappa * (thr_base + xx) + tie_abs(3 * d + 3) +
+            const float thr = ldexpf(a.kappa * (thr_base + xx) + tabs, kexp) + kabs +
                               a.kpack * (fabsf(B1) + fabsf(B2));
             const bool flag = valid && (B2 - B1 <= thr);
             {
@@ -588,6 +634,194 @@ __global__ void convert_norm_kernel(const float* __restrict__ cnorm, int k, int 
     }
 }
 
+
+// Single-pass form: X -> one FP16 part per tile, x 2^-ea (f16_scales), in the
+// K-major core-matrix layout, and FP32 ||x||^2 (unscaled); one warp per row.
+__global__ void convert_x_f16_kernel(const float* __restrict__ X, long long n, int d,
+                                     unsigned char* __restrict__ Xt, float* __restrict__ xn2,
+                                     long long ntiles, const StageState* st)
+{
+    const int lane = threadIdx.x & 31;
+    int ea, eb, E;
+    f16_scales(st, ea, eb, E);
+    const long long nrows = ntiles * kRows;
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const size_t Apart = (size_t)kRows * d * 2;
+    for (; w < nrows; w += nw) {
+        const long long tile = w / kRows;
+        const int r = (int)(w - tile * kRows);
+        unsigned char* base = Xt + (size_t)tile * Apart;
+        float s2 = 0.f;
+        for (int t0 = 4 * lane; t0 < d; t0 += 128) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (w < n) v = __ldg(reinterpret_cast<const float4*>(X + w * d + t0));
+            s2 = fmaf(v.x, v.x, s2); s2 = fmaf(v.y, v.y, s2);
+            s2 = fmaf(v.z, v.z, s2); s2 = fmaf(v.w, v.w, s2);
+            const int ks = t0 >> 4, kc = (t0 >> 3) & 1, e = t0 & 7;
+            const __half2 h0 = __floats2half2_rn(ldexpf(v.x, -ea), ldexpf(v.y, -ea));
+            const __half2 h1 = __floats2half2_rn(ldexpf(v.z, -ea), ldexpf(v.w, -ea));
+            uint2 ph;
+            ph.x = *reinterpret_cast<const uint32_t*>(&h0);
+            ph.y = *reinterpret_cast<const uint32_t*>(&h1);
+            *reinterpret_cast<uint2*>(base + (size_t)ks * 4096 + tc::tile_offset(r, kc) + e * 2) = ph;
+        }
+        for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0 && w < n) xn2[w] = s2;
+    }
+}
+
+// Single-pass form: -2c 2^-eb -> FP16 slices (NC * 32 bytes per chunk and
+// K-step); padding centers are zero.
+__global__ void convert_c_f16_kernel(const float* __restrict__ c32, int k, int d, int NC, int nch,
+                                     unsigned char* __restrict__ Cb, const StageState* st)
+{
+    int ea, eb, E;
+    f16_scales(st, ea, eb, E);
+    const long long total = (long long)nch * NC * d;
+    const int kslices = d / 16 + 1;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / d), t = (int)(e - (long long)j * d);
+        const int ch = j / NC, jj = j - ch * NC;
+        const float m = j < k ? -2.0f * c32[(long long)j * d + t] : 0.0f;
+        const int ks = t >> 4, kc = (t >> 3) & 1, el = t & 7;
+        const size_t off = ((size_t)ch * kslices + ks) * NC * 32 + tc::tile_offset(jj, kc) + el * 2;
+        *reinterpret_cast<__half*>(Cb + off) = __float2half_rn(ldexpf(m, -eb));
+    }
+}
+
+// Single-pass form: the norm slice of every chunk, ||c_j||^2 2^-(ea + eb) as
+// three BF16 parts in the first columns of row j (BF16 operands: the norm MMA
+// runs with a BF16 instruction descriptor against the BF16 ones tile).
+__global__ void convert_norm_single_kernel(const float* __restrict__ cnorm, int k, int d, int NC,
+                                           int nch, unsigned char* __restrict__ Cb,
+                                           const StageState* st)
+{
+    int ea, eb, E;
+    f16_scales(st, ea, eb, E);
+    const int kslices = d / 16 + 1;
+    const int total = nch * NC;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        const int ch = j / NC, jj = j - ch * NC;
+        const float nrm = j < k ? ldexpf(cnorm[j], -(ea + eb)) : 3.3895313892515355e38f;
+        const __nv_bfloat16 nh = __float2bfloat16_rn(nrm);
+        const float r1 = nrm - __bfloat162float(nh);
+        const __nv_bfloat16 nm = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(nm);
+        const __nv_bfloat16 nl = __float2bfloat16_rn(r2);
+        unsigned char* base = Cb + ((size_t)ch * kslices + (kslices - 1)) * NC * 32;
+        uint4 v0;
+        v0.x = (uint32_t)__bfloat16_as_ushort(nh) | ((uint32_t)__bfloat16_as_ushort(nm) << 16);
+        v0.y = (uint32_t)__bfloat16_as_ushort(nl);
+        v0.z = 0u;
+        v0.w = 0u;
+        *reinterpret_cast<uint4*>(base + tc::tile_offset(jj, 0)) = v0;
+        *reinterpret_cast<uint4*>(base + tc::tile_offset(jj, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+
+// ---- second pass of the single-pass form: the rows its bound could not
+// decide go through the split-BF16 kernel (a bound 2^-7 of the single pass's),
+// and only the rows that one cannot decide reach the FP64 recheck.
+
+// *nb = the number of listed rows when they fit the pass's buffers (cap), else
+// 0 (the FP64 recheck then takes them all); st2 = the stage state with an
+// empty list of its own.
+__global__ void stageb_prep_kernel(StageState* st, StageState* st2, long long* nb, long long cap)
+{
+    const int count = st->recheck_count;
+    const bool run = st->error == 0 && count > 0 && (long long)count <= cap;
+    *nb = run ? (long long)count : 0ll;
+    *st2 = *st;
+    st2->recheck_count = 0;
+}
+
+// Compact copies of the listed rows: FP32 rows (the pass's sums read them),
+// split-BF16 tiles, FP32 ||x||^2 and the old labels; rows past the count up to
+// the tile boundary are zero.  One warp per row.
+__global__ void stageb_compact_kernel(const float* __restrict__ X, int d, const int* __restrict__ list,
+                                      const long long* nb, const int* __restrict__ labels,
+                                      const StageState* st, float* __restrict__ Xc,
+                                      unsigned char* __restrict__ Xt, float* __restrict__ xn2,
+                                      int* __restrict__ lab)
+{
+    const long long count = *nb;
+    const int lane = threadIdx.x & 31;
+    const bool delta = st->mode == kModeDelta;
+    const long long nrows = (count + kRows - 1) / kRows * kRows;
+    const size_t Ahalf = (size_t)kRows * d * 2;
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (; w < nrows; w += nw) {
+        const long long tile = w / kRows;
+        const int r = (int)(w - tile * kRows);
+        unsigned char* base = Xt + (size_t)tile * 2 * Ahalf;
+        const bool live = w < count;
+        const long long i = live ? (long long)list[w] : 0;
+        float s2 = 0.f;
+        for (int t0 = 4 * lane; t0 < d; t0 += 128) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (live) {
+                v = __ldg(reinterpret_cast<const float4*>(X + i * d + t0));
+                *reinterpret_cast<float4*>(Xc + w * d + t0) = v;
+            }
+            s2 = fmaf(v.x, v.x, s2); s2 = fmaf(v.y, v.y, s2);
+            s2 = fmaf(v.z, v.z, s2); s2 = fmaf(v.w, v.w, s2);
+            const int ks = t0 >> 4, kc = (t0 >> 3) & 1, e = t0 & 7;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(v.z, v.w);
+            const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+            __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+            __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+            uint2 ph, pl;
+            ph.x = *reinterpret_cast<uint32_t*>(&h0);
+            ph.y = *reinterpret_cast<uint32_t*>(&h1);
+            pl.x = *reinterpret_cast<uint32_t*>(&l0);
+            pl.y = *reinterpret_cast<uint32_t*>(&l1);
+            const size_t off = (size_t)ks * 4096 + tc::tile_offset(r, kc) + e * 2;
+            *reinterpret_cast<uint2*>(base + off) = ph;
+            *reinterpret_cast<uint2*>(base + Ahalf + off) = pl;
+        }
+        for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0 && live) {
+            xn2[w] = s2;
+            lab[w] = delta ? labels[i] : -1;
+        }
+    }
+}
+
+// The pass's decisions back to the stage: labels of the compact rows, and its
+// own list of undecided rows (compact indices) turned into row indices.
+__global__ void stageb_scatter_kernel(const int* __restrict__ list, const long long* nb,
+                                      const int* __restrict__ lab, int* __restrict__ labels,
+                                      int* __restrict__ list2, const StageState* st2)
+{
+    const long long count = *nb;
+    if (count == 0) return;
+    const long long c2 = st2->recheck_count;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride)
+        labels[list[e]] = lab[e];
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < c2; f += stride)
+        list2[f] = list[list2[f]];
+}
+
+// The stage's recheck list and count become the pass's (error carried over).
+__global__ void stageb_finish_kernel(int* __restrict__ list, const int* __restrict__ list2,
+                                     const long long* nb, StageState* st, const StageState* st2)
+{
+    if (*nb == 0) return;
+    const long long c2 = st2->recheck_count;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < c2; f += stride)
+        list[f] = list2[f];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->recheck_count = (int)c2;
+        if (st2->error) st->error = st2->error;
+    }
+}
 }  // namespace
 
 // Per key (derivation in the design notes): with |x - xh - xl| <= 2^-18 |x| and
@@ -606,6 +840,35 @@ float bf16_kappa(int d)
     const double a2 = nt * 0x1p-23 + 0x1p-23 + 0x1p-27;                         // ||c||^2
     const double kb = fmax(a1 / 2.0, (a1 / 2.0 + a2) / 2.0);
     return (float)(2.0 * kb * 1.0625);
+}
+
+// Single-pass FP16 form, per key.  Rounding the scaled operands to FP16 costs
+// at most u = 2^-11 relative plus eta = 2^-14 absolute (scaled units; eta also
+// covers FP16 subnormals flushed to zero).  The relative part leaves (2u + u^2)
+// |x_t||m_t| per dimension, i.e. 2 (2u + u^2) sum_t |x_t||c_t|; the FP32
+// accumulation of nt = d + 3 exact products (an FP16 x FP16 product is exact
+// in FP32): nt 2^-23 (2 |x||c| + ||c||^2); FP32 centers and ||c||^2 and the BF16
+// norm parts as in the split form.  The absolute part, back in unscaled units
+// with 2^b <= sqrt(C2) 2^-11, 2^a = 2^(E - 14), sum_t |x_t| <= sqrt(d) |x| and
+// sum_t |m_t| <= 2 sqrt(d) sqrt(C2):
+//   eta (1 + u) sqrt(d) |x| sqrt(C2) 2^-11   <= (1 + u) sqrt(d) 2^-26 (X2 + C2)
+//   eta (1 + u) 2 sqrt(d) sqrt(C2) 2^(E-14)  <= (1 + u) sqrt(d) 2^-28 (4^E + C2)
+//   d eta^2 2^(a + b)                        <= d 2^-55 (4^E + C2)
+// The first joins the relative coefficient; the other two, for two keys, are
+// f16_kabs x (4^E + C2).
+float f16_kappa(int d)
+{
+    const double u = 0x1p-11, nt = d + 3.0;
+    const double a1 = 2.0 * (2.0 * u + u * u) + 2.0 * nt * 0x1p-23 + 0x1p-23;   // |x||c|
+    const double a2 = nt * 0x1p-23 + 0x1p-23 + 0x1p-27;                         // ||c||^2
+    const double kb = fmax(a1 / 2.0, (a1 / 2.0 + a2) / 2.0) + (1.0 + u) * sqrt((double)d) * 0x1p-26;
+    return (float)(2.0 * kb * 1.0625);
+}
+
+float f16_kabs(int d)
+{
+    const double u = 0x1p-11;
+    return (float)(2.0 * ((1.0 + u) * sqrt((double)d) * 0x1p-28 + d * 0x1p-55) * 1.0625);
 }
 
 // Two A stages of a 128-row tile (hi + lo parts) and at least two B slices of
@@ -627,57 +890,71 @@ int assign_bf16_supported(int d, int k, const float* X)
 // A read), else 128.  Two epilogue groups x kAccBufs accumulators x NC
 // columns fill at most the 512 TMEM columns of the SM.  Columns past k hold
 // zero centers with the padding norm, so they never win.
-int bf16_chunk(int d, int k)
+int bf16_chunk(int d, int k, int single)
 {
     (void)d;
+    (void)single;
     return k <= 64 ? 64 : (k >= 512 ? 256 : 128);
 }
 
-size_t bf16_xt_bytes(long long n, int d)
+size_t bf16_xt_bytes(long long n, int d, int single)
 {
-    return (size_t)((n + kRows - 1) / kRows) * kRows * (size_t)d * 2 * 2;
+    return (size_t)((n + kRows - 1) / kRows) * kRows * (size_t)d * 2 * (single ? 1 : 2);
 }
 
-size_t bf16_cb_bytes(int d, int k)
+size_t bf16_cb_bytes(int d, int k, int single)
 {
-    const int nc = bf16_chunk(d, k);
+    const int nc = bf16_chunk(d, k, single);
     const int nch = (k + nc - 1) / nc;
-    return (size_t)nch * nc * 64 * (size_t)(d / 16 + 1);
+    return (size_t)nch * nc * (single ? 32 : 64) * (size_t)(d / 16 + 1);
 }
 
 int launch_convert_x_bf16(const float* X, long long n, int d, unsigned char* Xt, float* xn2,
-                          cudaStream_t s, int sm_count)
+                          const StageState* st, int single, cudaStream_t s, int sm_count)
 {
     const long long ntiles = (n + kRows - 1) / kRows;
     long long blocks = (ntiles * kRows * 32 + 255) / 256;
     if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
     ++g_launches;
-    convert_x_kernel<<<(int)blocks, 256, 0, s>>>(X, n, d, Xt, xn2, ntiles);
+    if (single)
+        convert_x_f16_kernel<<<(int)blocks, 256, 0, s>>>(X, n, d, Xt, xn2, ntiles, st);
+    else
+        convert_x_kernel<<<(int)blocks, 256, 0, s>>>(X, n, d, Xt, xn2, ntiles);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
 
 int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2,
                        unsigned char* Cb, long long n, int d, const Centers& c, int* labels,
-                       StageState* st, const Accum& acc, int* list, cudaStream_t s, int sm_count)
+                       StageState* st, const Accum& acc, int* list, int single, cudaStream_t s,
+                       int sm_count, const long long* n_dev)
 {
-    const int NC = bf16_chunk(d, c.k);
+    const int NC = bf16_chunk(d, c.k, single);
     const int nch = (c.k + NC - 1) / NC;
-    // this iteration's centers into BF16 chunks
+    // this iteration's centers into BF16 (FP16) chunks
     {
         const long long total = (long long)nch * NC * d;
         long long blocks = (total + 255) / 256;
         if (blocks > 4096) blocks = 4096;
         ++g_launches;
-        convert_c_kernel<<<(int)blocks, 256, 0, s>>>(c.c32, c.k, d, NC, nch, Cb);
+        if (single)
+            convert_c_f16_kernel<<<(int)blocks, 256, 0, s>>>(c.c32, c.k, d, NC, nch, Cb, st);
+        else
+            convert_c_kernel<<<(int)blocks, 256, 0, s>>>(c.c32, c.k, d, NC, nch, Cb);
         KM2_CUDA(cudaGetLastError());
         ++g_launches;
-        convert_norm_kernel<<<(nch * NC + 255) / 256, 256, 0, s>>>(c.cnorm, c.k, d, NC, nch, Cb);
+        if (single)
+            convert_norm_single_kernel<<<(nch * NC + 255) / 256, 256, 0, s>>>(c.cnorm, c.k, d, NC,
+                                                                               nch, Cb, st);
+        else
+            convert_norm_kernel<<<(nch * NC + 255) / 256, 256, 0, s>>>(c.cnorm, c.k, d, NC, nch,
+                                                                        Cb);
         KM2_CUDA(cudaGetLastError());
     }
     uint32_t cols = 32;
     while (cols < (uint32_t)(kEpiGroups * (NC >= 256 ? 1 : 2) * NC)) cols <<= 1;
-    const size_t abytes = (size_t)4 * kRows * d, sbytes = (size_t)NC * 64;
+    const size_t parts = single ? 1 : 2;
+    const size_t abytes = parts * 2 * kRows * d, sbytes = (size_t)NC * 32 * parts;
     int sb = (int)((kSmemBudget - kStaticSmem - kSA * abytes - 4096) / sbytes);
     if (sb > kMaxSB) sb = kMaxSB;
     if (sb < 2) {
@@ -687,15 +964,19 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     const size_t smem = kSA * abytes + (size_t)sb * sbytes + 4096;
     // one fixed limit for both instantiations (the static part holds the
     // barriers, the side ring and the recheck queues)
-    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<64>, kSmemBudget - kStaticSmem));
-    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<128>, kSmemBudget - kStaticSmem));
-    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<256>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<64, 0>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<128, 0>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<256, 0>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<64, 1>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<128, 1>, kSmemBudget - kStaticSmem));
+    KM2_TRY(set_max_dynamic_smem((const void*)assign_bf16<256, 1>, kSmemBudget - kStaticSmem));
     const long long tiles = (n + kRows - 1) / kRows;
     long long grid = sm_count;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
     Bf16Args a;
     a.X = X;
+    a.n_dev = n_dev;
     a.Xt = Xt;
     a.xn2 = xn2;
     a.Cb = Cb;
@@ -707,16 +988,58 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     a.sb = sb;
     a.lab_bulk = (reinterpret_cast<uintptr_t>(labels) & 15) == 0 ? 1 : 0;
     a.tmem_cols = cols;
-    a.kappa = bf16_kappa(d);
+    a.kappa = single ? f16_kappa(d) : bf16_kappa(d);
+    a.kabs = single ? f16_kabs(d) : 0.0f;
     a.kpack = kPackSlack;
     a.ctries = consumer_wait_tries(kWaitTries);
     ++g_launches;
-    if (NC == 64)
-        assign_bf16<64><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
-    else if (NC == 128)
-        assign_bf16<128><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
-    else
-        assign_bf16<256><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+    if (single) {
+        if (NC == 64)
+            assign_bf16<64, 1><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+        else if (NC == 128)
+            assign_bf16<128, 1><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+        else
+            assign_bf16<256, 1><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+    } else {
+        if (NC == 64)
+            assign_bf16<64, 0><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+        else if (NC == 128)
+            assign_bf16<128, 0><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+        else
+            assign_bf16<256, 0><<<(int)grid, kThreads, smem, s>>>(a, c, labels, st, acc, list);
+    }
+    KM2_CUDA(cudaGetLastError());
+    return KMEANS2_OK;
+}
+
+// Rows the second pass takes at most: a quarter of the stage (more undecided
+// rows than that go to the FP64 recheck; a single pass that leaves so many is
+// the wrong form for the data anyway).
+long long stage_b_cap(long long n)
+{
+    const long long cap = n / 4 + 1024;
+    return cap < n ? cap : n;
+}
+
+int launch_stage_b(const float* X, int d, const Centers& c, int* labels, StageState* st,
+                   const Accum& acc, int* list, const StageB& b, cudaStream_t s, int sm_count)
+{
+    g_launches += 4;
+    stageb_prep_kernel<<<1, 1, 0, s>>>(st, b.st, b.nb, b.cap);
+    KM2_CUDA(cudaGetLastError());
+    const long long rows = (b.cap + kRows - 1) / kRows * kRows;
+    long long blocks = (rows * 32 + 255) / 256;
+    if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
+    stageb_compact_kernel<<<(int)blocks, 256, 0, s>>>(X, d, list, b.nb, labels, st, b.Xc, b.Xt,
+                                                      b.xn2, b.lab);
+    KM2_CUDA(cudaGetLastError());
+    KM2_TRY(launch_assign_bf16(b.Xc, b.Xt, b.xn2, b.cb, b.cap, d, c, b.lab, b.st, acc, b.list, 0,
+                               s, sm_count, b.nb));
+    long long sb = (b.cap + 255) / 256;
+    if (sb > (long long)sm_count * 8) sb = (long long)sm_count * 8;
+    stageb_scatter_kernel<<<(int)sb, 256, 0, s>>>(list, b.nb, b.lab, labels, b.list, b.st);
+    KM2_CUDA(cudaGetLastError());
+    stageb_finish_kernel<<<(int)sb, 256, 0, s>>>(list, b.list, b.nb, st, b.st);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }

@@ -50,6 +50,7 @@ def _forms(d, k):
         forms.append("tf32x3")
     if d % 16 == 0 and 16 <= d <= 128:
         forms.append("bf16")
+        forms.append("fp16")
     return forms
 
 

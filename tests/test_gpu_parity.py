@@ -104,13 +104,15 @@ BF16_SHAPES = [(20000, 16, 40), (50001, 64, 300), (30000, 128, 1024), (100_000, 
                (200_003, 96, 777)]
 
 
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
 @pytest.mark.parametrize("n,d,k", BF16_SHAPES)
-def test_step_bf16_form_matches_oracle(n, d, k):
-    """BF16 tensor-core cross term + FP64 recheck: labels still bit-exact."""
+def test_step_bf16_form_matches_oracle(n, d, k, form):
+    """16-bit tensor-core cross term (split BF16; single-pass FP16 with its
+    split-BF16 second pass) + FP64 recheck: labels still bit-exact."""
     X = _mixture(n, d, k, seed=5 * n + d + k, spread=3.0)
     C = _centers_from(X, k, seed=d + 2, jitter=0.3)
     Xd = torch.as_tensor(X, device=DEV)
-    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision="bf16")
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision=form)
     ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
     assert np.array_equal(to_np(lab), olab)
     assert_centers_close(to_np(cn), ocn, X)
@@ -118,13 +120,52 @@ def test_step_bf16_form_matches_oracle(n, d, k):
     assert em == oem
 
 
-def test_fit_bf16_vmf_matches_oracle():
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+def test_fit_bf16_vmf_matches_oracle(form):
     X = to_np(synth.vmf_mixture(60000, 128, 256, seed=7))
     Xd = torch.as_tensor(X, device=DEV)
-    r = km.fit(Xd, 256, 0.05, 3, 1e-6, 15, precision="bf16", trajectories=True)
+    r = km.fit(Xd, 256, 0.05, 3, 1e-6, 15, precision=form, trajectories=True)
     o = oracle.fit(X, 256, 0.05, 3, 1e-6, 15, nthreads=NT)
-    assert r.precision_used == "bf16"
+    assert r.precision_used == form
     _assert_fit_equal(r, o, X)
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-12, 3e4, 1e13])
+def test_step_fp16_scaled_operands_over_the_range(scale):
+    # the single-pass FP16 form scales x and -2c by powers of two taken from
+    # max|x| and max ||c||^2; tiny and huge data (outside FP16's own range)
+    # and a set of centers much smaller than the data still give the oracle's
+    # labels
+    X0 = _mixture(40_000, 32, 20, seed=41, spread=3.0)
+    C = _centers_from(X0, 20, seed=3, jitter=0.3)
+    C[:5] *= 1e-3                                         # small centers
+    X = (X0 * np.float32(scale)).astype(np.float32)
+    C = C * scale
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision="fp16")
+    ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
+    assert np.array_equal(to_np(lab), olab)
+    assert_centers_close(to_np(cn), ocn, X)
+    assert_J_close(J, oJ, X)
+    assert em == oem
+
+
+def test_fp16_second_pass_overflow_goes_to_the_fp64_recheck():
+    # every row a near tie (all points on the bisector of two centers): far
+    # more undecided rows than the second pass takes (n / 4 + 1024), so the
+    # FP64 recheck decides them all; labels still the oracle's
+    rng = np.random.default_rng(77)
+    n, d = 60_000, 32
+    X = rng.normal(size=(n, d)).astype(np.float32)
+    X[:, 0] = 0.0
+    C = np.zeros((2, d))
+    C[0, 0], C[1, 0] = 1.0, -1.0
+    Xd = torch.as_tensor(X, device=DEV)
+    cn, lab, J, sh, em = km.step(Xd, torch.as_tensor(C, device=DEV), precision="fp16")
+    ocn, olab, oJ, osh, oem = oracle.lloyd_step(X, C, nthreads=NT)
+    assert np.array_equal(to_np(lab), olab)
+    assert_centers_close(to_np(cn), ocn, X)
+    assert_J_close(J, oJ, X)
 
 
 def test_tf32x3_rejects_unsupported_shape():
@@ -157,7 +198,7 @@ def test_step_far_from_origin_forces_rechecks():
     assert_J_close(J, oJ, X)
 
 
-@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16"])
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16", "fp16"])
 def test_step_below_the_fixed_point_range(form):
     # max|x| ~ 1e-29 < 2^-74: the fixed-point scale stays at its cap 2^120, so
     # the cluster sums keep about 20 bits here.  Labels are still the oracle's;
@@ -178,7 +219,7 @@ def test_step_below_the_fixed_point_range(form):
     assert em == oem
 
 
-@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16"])
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "bf16", "fp16"])
 def test_step_far_from_origin_each_form(form):
     # x ~ 1e3 +- 1e-2 in d = 16: sum ||x||^2 / J ~ 1e10, so J must be formed
     # without cancellation to meet 1e-9 relative
@@ -341,7 +382,7 @@ def test_release_memory_between_fits_keeps_results():
     assert torch.equal(a.labels, b.labels) and torch.equal(a.centers, b.centers) and a.J == b.J
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16"])
+@pytest.mark.parametrize("form", ["fp32", "bf16", "fp16"])
 def test_step_many_near_ties_with_many_centers(form):
     # far from the origin with k * d = 38400: thousands of flagged points go
     # through the FP64 recheck (each reading all k d FP32 center values);

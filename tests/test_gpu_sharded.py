@@ -38,10 +38,11 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("n,d,k,prec", [(200_003, 8, 32, "fp32"), (120_001, 64, 100, "bf16"),
+                                        (90_001, 64, 300, "fp16"),
                                         (60_002, 16, 20, "tf32x3"), (30_001, 3, 7, "fp32")])
 @pytest.mark.parametrize("shards", [1, 2, 3, 7])
 def test_sharded_equals_unsharded(n, d, k, prec, shards):
-    if prec == "bf16":
+    if prec in ("bf16", "fp16"):
         X = synth.vmf_mixture(n, d, k, 3, device=DEV)
     else:
         X = synth.aniso_gaussian_noise(n, d, k, 3, device=DEV)

@@ -1,6 +1,6 @@
 """The bounded device-side waits of the tensor-core kernels (GPU).
 
-Every mbarrier wait in the split-BF16 and 3xTF32 kernels has an iteration
+Every mbarrier wait in the 16-bit and 3xTF32 tensor-core kernels has an iteration
 limit; when it runs out the CTA records KMEANS2_ERR_TIMEOUT, the other roles
 see the abort, each role lets its own bulk copies and MMAs finish, TMEM is
 freed and the kernel returns.  The debug build (KMEANS2_DEBUG=1) takes the
@@ -31,7 +31,7 @@ dev = torch.device("cuda", 0)
 Xb = synth.vmf_mixture(40_000, 64, 600, 5, device=dev)
 Xt = synth.aniso_gaussian_noise(50_001, 8, 32, 6, device=dev)
 out = {"lib": km.LIB_PATH}
-for name, X, k in (("bf16", Xb, 600), ("tf32x3", Xt, 32)):
+for name, X, k in (("bf16", Xb, 600), ("fp16", Xb, 600), ("tf32x3", Xt, 32)):
     C = X[:k].double()
     os.environ["KMEANS2_DEBUG_WAIT_TRIES"] = "0"
     try:
@@ -64,7 +64,7 @@ def test_consumer_wait_timeout_reports_status_and_next_calls_are_correct():
     assert r.returncode == 0, r.stderr[-3000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out.pop("lib").endswith("libkmeans2_debug.so")
-    for name in ("bf16", "tf32x3"):
+    for name in ("bf16", "fp16", "tf32x3"):
         status, same = out[name]
         assert status == -5, (name, status)            # KMEANS2_ERR_TIMEOUT
         assert same, name
