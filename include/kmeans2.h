@@ -91,8 +91,13 @@ extern "C" {
                                          split in two BF16 parts, three products, FP32
                                          accumulation); d a multiple of 16 in [16, 128] */
 #define KMEANS2_PRECISION_AUTO 2      /* fastest form measured for the shape (default):
-                                         BF16 for d in {64, 80, ..., 128} and k >= 512,
-                                         else FP32 */
+                                         for d in {64, 80, ..., 128} and k >= 512,
+                                         kmeans2_fit starts the fast stage in FP16 and
+                                         moves to BF16 if its first iteration leaves
+                                         more than 10 % of the rows undecided; the slow
+                                         stage runs FP16 if the fast stage left at most
+                                         5 % per iteration, else BF16 (the other entry
+                                         points take BF16 there); FP32 otherwise */
 #define KMEANS2_PRECISION_TF32X3 3    /* cross term on the tensor cores as three TF32
                                          products of the exact hi/lo split of the FP32
                                          operands; d in {4, 8, 16, 32}, k <= 256 */
@@ -160,13 +165,18 @@ typedef struct kmeans2_result {
     int32_t converged_fast;     /* 1 if the fast stage met its tolerance */
     int32_t converged_slow;     /* 1 if the slow stage met tol */
     int32_t empty_clusters;     /* clusters left without points in the last iteration */
-    int32_t precision_used;     /* the form that ran: KMEANS2_PRECISION_FP32, _BF16 or _TF32X3 */
+    int32_t precision_used;     /* the form of the slow stage: KMEANS2_PRECISION_FP32,
+                                   _BF16, _FP16 or _TF32X3 */
     int64_t subset_size;        /* m = |S_s| */
     int64_t rechecked_points;   /* points re-evaluated in FP64, summed over iterations */
     int64_t distance_evals;     /* K Q_f m + K Q_s n (Section 3 cost model) */
     double shift_fast;          /* last fast-stage max center movement */
     double shift_slow;          /* last slow-stage max center movement */
     double seconds;             /* wall time of the call */
+    int64_t undecided_fast;     /* FP16 form: rows its single pass left undecided
+                                   (second pass), summed over the fast stage's
+                                   iterations; 0 for the other forms */
+    int64_t undecided_slow;     /* the same over the slow stage */
 } kmeans2_result;
 
 /* ---------------------------------------------------------------- entry points */

@@ -99,6 +99,8 @@ class Result(ctypes.Structure):
         ("shift_fast", ctypes.c_double),
         ("shift_slow", ctypes.c_double),
         ("seconds", ctypes.c_double),
+        ("undecided_fast", ctypes.c_int64),
+        ("undecided_slow", ctypes.c_int64),
     ]
 
 
@@ -357,6 +359,7 @@ class FitResult:
     seconds: float
     precision_used: str
     traj: dict = field(default_factory=dict)
+    undecided: tuple = (0, 0)     # FP16 form: rows its single pass left undecided per stage
 
 
 def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int, *,
@@ -412,7 +415,7 @@ def fit(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,
                      distance_evals=res.distance_evals, shift_fast=res.shift_fast,
                      shift_slow=res.shift_slow, seconds=res.seconds,
                      precision_used={0: "fp32", 1: "bf16", 3: "tf32x3", 4: "fp16"}.get(res.precision_used, "?"),
-                     traj=traj)
+                     traj=traj, undecided=(res.undecided_fast, res.undecided_slow))
 
 
 def fit_streamed(X, k: int, subset_fraction: float, seed: int, tol: float, max_iter: int,

@@ -234,9 +234,8 @@ int alloc_workspace(Workspace& w, DeviceScratch& ws, long long list_cap, int k, 
     // padding centers: the largest finite key, so that packing an index into
     // its low mantissa bits never makes a NaN and it never wins or ties
     KM2_TRY(fill_f32(w.c.cnorm, cn_len, FLT_MAX, s));
-    if (tc16_form(w.form))
-        KM2_TRY(ws.alloc((void**)&w.cb,
-                         bf16_cb_bytes(d, k, w.form == KMEANS2_PRECISION_FP16), s));
+    // (the split layout: a fit may switch from FP16 to split BF16 between stages)
+    if (tc16_form(w.form)) KM2_TRY(ws.alloc((void**)&w.cb, bf16_cb_bytes(d, k, 0), s));
     return KMEANS2_OK;
 }
 
@@ -456,11 +455,15 @@ int map_stage_error(int err)
 
 // Run one stage on device-resident X (n x d) from the centers in w.c (FP64
 // master already set).  The caller has zeroed w.st and recorded max|x| in it.
+// Share of a stage's rows the single-pass FP16 form may leave undecided in its
+// first iteration before an AUTO fit moves that stage to the split form.
+constexpr double kFp16ProbeMaxUndecided = 0.10;
+
 int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, double tol,
               int max_iter, bool use_graph, cudaStream_t s, int sm_count, StageState& out,
               double* traj_J_host, double* traj_shift_host, kmeans2_profile* prof,
               const char* name = "kmeans2 stage", double* traj_c_host = nullptr,
-              int64_t* traj_n_host = nullptr)
+              int64_t* traj_n_host = nullptr, bool probe16 = false)
 {
     NvtxRange stage_range(name);
     size_t kd = (size_t)w.c.k * d;
@@ -471,10 +474,29 @@ int run_stage(const float* X, long long n, int d, Workspace& w, int* labels, dou
     KM2_TRY(launch_stage_init(w.st, d, tol, max_iter, s));
     KM2_TRY(launch_qsum(X, n, d, w.st, s, sm_count));
     KM2_TRY(prepare_stage_points(X, n, d, w, *w.ws, s));
-    if (use_graph && !prof)
-        KM2_TRY(run_loop_graph(X, n, d, w, labels, s, sm_count));
-    else
-        KM2_TRY(run_loop_host(X, n, d, w, labels, max_iter, s, sm_count, prof));
+    bool finished = false;
+    int remaining = max_iter;
+    if (probe16 && w.form == KMEANS2_PRECISION_FP16) {
+        // one FP16 iteration from the host; if its single pass left too many
+        // rows undecided, the rest of the stage runs the split form (every
+        // form decides each row exactly, so the switch changes no result)
+        KM2_TRY(run_loop_host(X, n, d, w, labels, 1, s, sm_count, prof));
+        StageState p;
+        KM2_CUDA(cudaMemcpyAsync(&p, w.st, sizeof(StageState), cudaMemcpyDeviceToHost, s));
+        KM2_CUDA(cudaStreamSynchronize(s));
+        finished = p.done != 0 || p.error != 0;
+        remaining = max_iter - 1;
+        if (!finished && (double)p.undecided16_total > kFp16ProbeMaxUndecided * (double)n) {
+            w.form = KMEANS2_PRECISION_BF16;
+            KM2_TRY(prepare_stage_points(X, n, d, w, *w.ws, s));
+        }
+    }
+    if (!finished) {
+        if (use_graph && !prof)
+            KM2_TRY(run_loop_graph(X, n, d, w, labels, s, sm_count));
+        else
+            KM2_TRY(run_loop_host(X, n, d, w, labels, remaining, s, sm_count, prof));
+    }
     KM2_CUDA(cudaMemcpyAsync(&out, w.st, sizeof(StageState), cudaMemcpyDeviceToHost, s));
     KM2_CUDA(cudaStreamSynchronize(s));
     if (out.error) return map_stage_error(out.error);
@@ -640,7 +662,7 @@ uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fr
     add(N * 4);
     add((unsigned long long)kClusSlots * K * 8);
     add(2 * (unsigned long long)max_iter * 8);
-    if (tc16_form(form)) add(bf16_cb_bytes(d, k, form == KMEANS2_PRECISION_FP16));
+    if (tc16_form(form)) add(bf16_cb_bytes(d, k, 0));
     if (labels_on_host) add(N * 4);
     // fast stage: S_s indices, init positions, X_s, its labels
     add(m * 8);
@@ -656,21 +678,38 @@ uint64_t kmeans2_fit_footprint(int64_t n, int32_t d, int32_t k, double subset_fr
     }
     add(K * 8);
     if (tc16_form(form)) {
-        const int single = form == KMEANS2_PRECISION_FP16;
+        // a stage's 16-bit tiles and ||x||^2, and for the single-pass form its
+        // second pass's compact rows; AUTO (FP16 fast stage, then FP16 or split
+        // BF16) counts the larger slow stage
+        auto second = [&](long long rows) {
+            const unsigned long long cap = (unsigned long long)stage_b_cap(rows);
+            add(cap * D * 4);
+            add(bf16_xt_bytes((long long)cap, d, 0));
+            add(cap * 12);
+            add(sizeof(StageState) + 8);
+        };
+        const bool adaptive = precision == KMEANS2_PRECISION_AUTO;
+        const int single = form == KMEANS2_PRECISION_FP16 || adaptive;
         add(bf16_xt_bytes((long long)m, d, single));
         add(m * 4);
-        add(bf16_xt_bytes(n, d, single));
-        add(N * 4);
-        if (single) {   // the second pass: compact rows of both stages, split slices
-            for (long long rows : {(long long)m, (long long)n}) {
-                const unsigned long long cap = (unsigned long long)stage_b_cap(rows);
-                add(cap * D * 4);
-                add(bf16_xt_bytes((long long)cap, d, 0));
-                add(cap * 12);
-                add(sizeof(StageState) + 8);
-            }
-            add(bf16_cb_bytes(d, k, 0));
+        if (single) second((long long)m);
+        if (single && !adaptive) {
+            add(bf16_xt_bytes(n, d, 1));
+            second(n);
+        } else if (!single) {
+            add(bf16_xt_bytes(n, d, 0));
+        } else {
+            const unsigned long long b0 = b;
+            const int a0 = allocs;
+            add(bf16_xt_bytes(n, d, 1));
+            second(n);
+            const unsigned long long fp16_slow = b - b0;
+            b = b0;
+            allocs = a0 + 5;
+            b += std::max(fp16_slow, (unsigned long long)bf16_xt_bytes(n, d, 0));
         }
+        add(N * 4);
+        if (single) add(bf16_cb_bytes(d, k, 0));
     }
     return b + (unsigned long long)allocs * 1024ull + (4ull << 20);
 }
@@ -810,6 +849,12 @@ int kmeans_step_noalloc(const float* X, int64_t n, int32_t d, int32_t k,
 
 namespace {
 
+// Share of a fast stage's rows (per iteration) that the single-pass FP16 form
+// may leave undecided for AUTO to keep it in the slow stage: its pass costs
+// ~0.85 of the split form's, and its second pass re-runs the undecided rows
+// through the split kernel.
+constexpr double kFp16MaxUndecided = 0.05;
+
 // The two-stage fit on Xd, n*d FP32 points the device can read (its own
 // memory or page-locked host memory), 16-byte aligned; arguments checked.
 int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fraction,
@@ -825,6 +870,13 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
     const long long m = kmeans2_subset_size(n, k, subset_fraction);
     Workspace w;
     KM2_TRY(choose_form(o.precision, d, k, Xd, &w.form));
+    // AUTO on a 16-bit tensor-core shape: the fast stage runs the single-pass
+    // FP16 form and the slow stage keeps it only if that left few rows
+    // undecided there (on tie-heavy data its second pass and the FP64 recheck
+    // would cost more than the split form saves; measured)
+    const bool adaptive = o.precision == KMEANS2_PRECISION_AUTO &&
+                          w.form == KMEANS2_PRECISION_BF16 && o.start_stage == 0;
+    if (adaptive) w.form = KMEANS2_PRECISION_FP16;
     KM2_TRY(alloc_workspace(w, ws, n, k, d, max_iter, s));
     if (o.traj_centers_fast || o.traj_centers_slow)
         KM2_TRY(ws.alloc((void**)&w.traj_c, sizeof(double) * (size_t)max_iter * k * d, s));
@@ -862,11 +914,18 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
         if (!o.init_centers) KM2_TRY(launch_init_centers(Xs, d, pos, k, w.c.c64, s));
         KM2_TRY(run_stage(Xs, m, d, w, labels_s, tol_fast, max_iter, use_graph, s, ws.sm_count,
                           fs, o.traj_J_fast, o.traj_shift_fast, o.profile, "kmeans2 fast stage",
-                          o.traj_centers_fast, o.traj_counts_fast));
+                          o.traj_centers_fast, o.traj_counts_fast, adaptive));
         rr.iters_fast = fs.iter;
         rr.converged_fast = fs.converged;
         rr.shift_fast = fs.shift;
         rr.rechecked_points += fs.rechecked_total;
+        rr.undecided_fast = fs.undecided16_total;
+        if (adaptive && w.form == KMEANS2_PRECISION_FP16) {
+            const double undecided = fs.iter > 0 && m > 0
+                                         ? (double)fs.undecided16_total / ((double)fs.iter * (double)m)
+                                         : 1.0;
+            if (undecided > kFp16MaxUndecided) w.form = KMEANS2_PRECISION_BF16;
+        }
     }
     // slow stage on S_n from the fast stage's final centers (Section 2; Section 5)
     KM2_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StageState), s));
@@ -875,12 +934,14 @@ int fit_on(const float* Xd, int64_t n, int32_t d, int32_t k, double subset_fract
     KM2_TRY(run_stage(Xd, n, d, w, labels, tol, max_iter, use_graph, s, ws.sm_count, ss,
                       o.traj_J_slow, o.traj_shift_slow, o.profile, "kmeans2 slow stage",
                       o.traj_centers_slow, o.traj_counts_slow));
+    rr.precision_used = w.form;
     rr.iters_slow = ss.iter;
     rr.converged_slow = ss.converged;
     rr.shift_slow = ss.shift;
     rr.J = ss.J;
     rr.empty_clusters = ss.empty;
     rr.rechecked_points += ss.rechecked_total;
+    rr.undecided_slow = ss.undecided16_total;
     rr.distance_evals = (int64_t)rr.iters_fast * m * k + (int64_t)rr.iters_slow * n * k;
 
     KM2_CUDA(cudaMemcpyAsync(centers_out, w.c.c64, sizeof(double) * (size_t)k * d,

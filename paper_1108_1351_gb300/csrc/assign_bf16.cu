@@ -734,6 +734,7 @@ __global__ void stageb_prep_kernel(StageState* st, StageState* st2, long long* n
     const int count = st->recheck_count;
     const bool run = st->error == 0 && count > 0 && (long long)count <= cap;
     *nb = run ? (long long)count : 0ll;
+    st->undecided16_total += count;
     *st2 = *st;
     st2->recheck_count = 0;
 }

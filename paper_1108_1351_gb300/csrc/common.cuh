@@ -53,6 +53,8 @@ struct StageState {
     // sum of s^2 over every coordinate of the stage's points (s = round(x 2^F)),
     // exact: the value is sum_w q[w] 2^(32 w) (qsum pass, wide_add4)
     unsigned long long q[4];
+    // single-pass FP16 form: rows its bound left undecided, summed over the stage
+    long long undecided16_total;
 };
 
 // Per-center scratch of finalize, in doubles per center (finalize_center_warp).

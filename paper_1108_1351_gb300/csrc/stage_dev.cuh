@@ -63,6 +63,7 @@ static __device__ void stage_init_dev(StageState* st, int d, double tol, int max
     st->tol = tol;
     st->recheck_count = 0;
     st->rechecked_total = 0;
+    st->undecided16_total = 0;
     for (int w = 0; w < 4; ++w) st->q[w] = 0ull;
     st->J = 0.0;
     st->shift = 0.0;

@@ -59,8 +59,8 @@ CASES = [
     # CUDA-core form, d = 8, uneven split
     dict(n=200_003, d=8, k=32, f=0.05, seed=5, tol=1e-6, max_iter=40, precision="fp32",
          data_seed=11, cut=77_777),
-    # split-BF16 tensor-core form (AUTO picks it at d = 64, k >= 512)
-    dict(n=60_001, d=64, k=520, f=0.1, seed=6, tol=1e-6, max_iter=20, precision="auto",
+    # split-BF16 tensor-core form
+    dict(n=60_001, d=64, k=520, f=0.1, seed=6, tol=1e-6, max_iter=20, precision="bf16",
          data_seed=12, cut=31_000),
 ]
 
