@@ -410,6 +410,8 @@ static __device__ __forceinline__ void recheck_point(const float* __restrict__ X
     const bool cached = cache != nullptr && c.kpad <= cache_cap;
     const int lane = threadIdx.x & 31;
     const float* x = X + (long long)i * d;
+    // the old label's load (a random row of the labels) overlaps the passes
+    const int old = (mode == kModeDelta) ? labels[i] : -1;
     float x2 = 0.0f;
     for (int t = lane; t < d; t += 32) { float v = __ldg(x + t); x2 = fmaf(v, v, x2); }
     for (int o = 16; o; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
@@ -449,12 +451,15 @@ static __device__ __forceinline__ void recheck_point(const float* __restrict__ X
             }
         }
     }
+    // lowest (distance, index) over the lanes; the FP64 sums of squares are
+    // non-negative, so their bit patterns order as the values do and the
+    // comparison stays off the (narrow) FP64 pipe
+    unsigned long long bb = (unsigned long long)__double_as_longlong(best);
     for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bb, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob < bb || (ob == bb && oj < bj)) { bb = ob; bj = oj; }
     }
-    int old = (mode == kModeDelta) ? labels[i] : -1;
     __syncwarp();   // every lane has read the old label before lane 0 rewrites it
     if (bj != old && label_ok(bj, k, st) && old_label_ok(old, k, st)) {
         for (int t = lane; t < d; t += 32) {
