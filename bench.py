@@ -1006,6 +1006,7 @@ def run_batched(args):
                                "value": sum(r.distance_evals for r in singles) / (ms_single * 1e-3),
                                "speedup_of_batched": ms_single / ms_max},
         "sampled_instances_identical": bool(same), "sampled": int(len(sample)),
+        "tile_shapes": {str(dd): km.batched_tile_shape(dd) for dd in dims},
         "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -360,9 +360,11 @@ typedef struct kmeans2_job {
  * phase of an iteration (distances, recheck, update) is one launch over all
  * jobs still running, each job carries its own stage (fast, slow, done) and
  * convergence flag on the device, and the whole loop runs as one CUDA graph
- * with a device-side while condition.  Work is cut into items of a number of
- * 1024-point tiles chosen by a built-in autotuner (timed on the first call for
- * each dimension class, then cached for the process).  Each job's result equals
+ * with a device-side while condition.  Jobs are grouped by dimension class
+ * (d rounded up to 2, 4, 8, 16, 32 or 64); per class a built-in autotuner picks
+ * the distance kernel's tile shape (point slots per lane, lanes sharing a
+ * point) and the 1024-point tiles per work item, timed on the first call for
+ * that class and then cached for the process.  Each job's result equals
  * kmeans2_fit on that job alone.
  *
  *  jobs      count descriptors (host array).
@@ -375,6 +377,18 @@ typedef struct kmeans2_job {
  */
 KMEANS2_API int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs,
                                     kmeans2_result* results, const kmeans2_options* opt);
+
+/*
+ * kmeans2_batched_tile_shape -- the choice the batched form's autotuner made in
+ * this process for the dimension class of d: point slots per lane
+ * (*points), lanes that share each point (*lanes; 1 = whole points per
+ * thread) and 1024-point tiles per work item (*tiles).  Output pointers are
+ * host memory and must not be NULL.  Returns KMEANS2_OK, or
+ * KMEANS2_ERR_INVALID when d is outside [1, 64] or no kmeans2_fit_batched call
+ * of this process has tuned that class yet (outputs untouched).
+ */
+KMEANS2_API int kmeans2_batched_tile_shape(int32_t d, int32_t* points, int32_t* lanes,
+                                           int32_t* tiles);
 
 /*
  * Serving: continuous batching of independent two-stage fits.  (The paper has

@@ -6,11 +6,11 @@ library ``libkmeans2.so`` (C ABI in ``include/kmeans2.h``).  This package only
 binds it (``binding``) and provides seeded synthetic inputs (``synth``).
 """
 from .binding import (FitResult, KMeans2Error, LIB_PATH, Profile, Served, Server, Shard,
-                      declared_symbols, fit, fit_batched, fit_data_parallel, fit_sharded,
+                      batched_tile_shape, declared_symbols, fit, fit_batched, fit_data_parallel, fit_sharded,
                       fit_streamed, footprint, load, release_memory, sample, step, step_noalloc,
                       strerror, subset_size, version)
 
 __all__ = ["FitResult", "KMeans2Error", "LIB_PATH", "Profile", "Served", "Server", "Shard",
-           "declared_symbols", "fit", "fit_batched", "fit_data_parallel", "fit_sharded",
+           "batched_tile_shape", "declared_symbols", "fit", "fit_batched", "fit_data_parallel", "fit_sharded",
            "fit_streamed", "footprint", "load", "release_memory", "sample", "step",
            "step_noalloc", "strerror", "subset_size", "version"]

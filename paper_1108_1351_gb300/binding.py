@@ -187,6 +187,9 @@ def load():
         lib.kmeans2_fit_batched.restype = ctypes.c_int
         lib.kmeans2_fit_batched.argtypes = [i32, ctypes.POINTER(Job), ctypes.POINTER(Result),
                                             ctypes.POINTER(Options)]
+        lib.kmeans2_batched_tile_shape.restype = ctypes.c_int
+        lib.kmeans2_batched_tile_shape.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                                   ctypes.POINTER(i32)]
         lib.kmeans_step_noalloc.restype = ctypes.c_int
         lib.kmeans_step_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P]
         lib.kmeans2_fit_footprint.restype = u64
@@ -858,6 +861,16 @@ def fit_batched(Xs, ks, subset_fraction, seeds, tol, max_iter, *, tol_fast: floa
                              distance_evals=r.distance_evals, shift_fast=r.shift_fast,
                              shift_slow=r.shift_slow, seconds=r.seconds, precision_used="fp32"))
     return out, rc
+
+
+def batched_tile_shape(d: int):
+    """The batched autotuner's choice for the dimension class of d in this
+    process (kmeans2_batched_tile_shape): (point slots per lane, lanes per
+    point, tiles per work item), or None before a batched call has tuned it."""
+    lib = load()
+    p, g, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = lib.kmeans2_batched_tile_shape(int(d), ctypes.byref(p), ctypes.byref(g), ctypes.byref(t))
+    return (p.value, g.value, t.value) if rc == 0 else None
 
 
 def step(X, centers, *, precision: str = "auto", stream=None, centers_out=None, labels_out=None,

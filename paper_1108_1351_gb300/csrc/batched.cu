@@ -14,13 +14,16 @@
 //   batch_control     sets the graph's while condition: any job still running
 // and the loop is captured once as a CUDA graph with a device-side WHILE node.
 // The arithmetic of every step is the single-fit arithmetic (stage_dev.cuh,
-// the same packed-key top-2, bound and exact sums), so each job's result equals
-// kmeans2_fit on that job alone.
+// the same packed-key top-2, near-tie bound and exact sums).  A tile shape in
+// which several lanes share a point adds that point's FP32 terms in another
+// order, which the bound covers, so every decision, and with it each job's
+// result, equals kmeans2_fit on that job alone.
 //
-// Work items hold a number of tiles chosen per dimension class by an
-// autotuner: on the first call for a class it times the real first pass of
-// the batch for a few item sizes (resetting the sums between trials) and keeps
-// the fastest for the rest of the process.  CTAs claim items from an atomic
+// The tile shape (point slots per lane, lanes per point) and the tiles per
+// work item are chosen per dimension class by an autotuner: on the first call
+// for a class it times the real first pass of the batch and a delta pass
+// after it for each shape and a few item sizes (resetting the sums between
+// trials) and keeps the fastest for the rest of the process.  CTAs claim items from an atomic
 // counter, largest jobs first, so the iterations in which only a few large
 // jobs still run keep every SM busy.
 #include <algorithm>
@@ -218,18 +221,46 @@ __global__ void __launch_bounds__(kThreads) batch_reset_kernel(BatchInst* insts)
     }
 }
 
+// Sets every job's pass mode (autotuning trials: a delta pass after the full one).
+__global__ void __launch_bounds__(kThreads) batch_mode_kernel(BatchInst* insts, int count, int mode)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) insts[j].st.mode = mode;
+}
+
 // ---------------------------------------------------------------- assign
 
-// Tile shape of a dimension class: P points per thread (the autotuner picks P
-// among the values the registers allow), sub-tiles of kThreads * P points.
-template <int DC, int PP>
+// Tile shape of a dimension class.  G lanes share each point: lane q of a
+// group holds coordinates 4 (c G + q) .. 4 (c G + q) + 3 (c = 0, 1, ...) of
+// the group's P points, so every center value a lane reads from shared memory
+// serves P FMAs while the lane keeps only P DC / G coordinates in registers.
+// The G partial dot products of a point are added across the group with xor
+// shuffles (P - P / G per center); afterwards each lane owns R = P / G points
+// (their top-2, decision and label).  Slot s of lane q holds the group's
+// point s ^ (q R), so every shuffle round adds the upper half of the slots
+// into the lower half with the same code in every lane.  G = 1 is the plain
+// form (P whole points per thread).  The autotuner picks (P, G) among the
+// shapes the registers allow.
+template <int DC, int PP, int GG>
 struct BCfg {
-    static constexpr int P = PP;                                  // points per thread
-    static constexpr int SUB = kThreads * P;                      // points per sub-tile
+    static constexpr int P = PP;                     // point slots per lane
+    static constexpr int G = GG;                     // lanes per point
+    static constexpr int R = P / G;                  // points each lane decides
+    static constexpr int DG = DC / G;                // coordinates per lane and point
+    static constexpr int GROUPS = kThreads / G;      // lane groups per CTA
+    static constexpr int SUB = GROUPS * P;           // points per sub-tile
     static constexpr int NSUB = kTile / SUB;
-    static constexpr bool SACC = DC <= 32;                        // per-CTA partial sums
+    static constexpr bool SACC = DC <= 32;           // per-CTA partial sums
+    static_assert(P % G == 0 && (G == 1 || DC % (4 * G) == 0), "G divides the point slots and the float4 chunks");
     static_assert(kTile % SUB == 0, "a tile holds whole sub-tiles");
 };
+
+// Coordinate held in element tt of a lane's point (lane q of a group of G).
+template <int G>
+__device__ __forceinline__ int lane_dim(int tt, int q)
+{
+    return G == 1 ? tt : 4 * ((tt >> 2) * G + q) + (tt & 3);
+}
 
 template <int DC>
 constexpr size_t batch_smem()
@@ -243,12 +274,25 @@ __device__ __forceinline__ float pack_key(float v, unsigned j)
     return __uint_as_float((__float_as_uint(v) & ~31u) | j);
 }
 
-template <int DC, int PP>
+// Adds the G partial values of each point across the lane group (lanes
+// q ^ m, m = G/2 .. 1): afterwards slots 0 .. R-1 hold whole sums.
+template <int P, int G>
+__device__ __forceinline__ void group_reduce(float (&a)[P])
+{
+    constexpr int R = P / G;
+#pragma unroll
+    for (int m = G / 2; m >= 1; m >>= 1) {
+#pragma unroll
+        for (int s = 0; s < m * R; ++s) a[s] += __shfl_xor_sync(0xffffffffu, a[s + m * R], m);
+    }
+}
+
+template <int DC, int PP, int GG>
 __global__ void __launch_bounds__(kThreads, 2)
 batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item)
 {
-    using C = BCfg<DC, PP>;
-    constexpr int P = C::P;
+    using C = BCfg<DC, PP, GG>;
+    constexpr int P = C::P, G = C::G, R = C::R, DG = C::DG;
     extern __shared__ __align__(16) float smem[];
     float* sc = smem;                                         // kMaxK * DC: -2 c
     float* ss = sc + kMaxK * DC;                              // kMaxK: ||c||^2
@@ -257,6 +301,10 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
     __shared__ unsigned long long sq[4];     // this item's sum of s^2 (wide_add4 words)
     __shared__ int s_item;
     const int tid = threadIdx.x;
+    const int q = tid % G;                   // lane within its group
+    const int gi = tid / G;                  // group
+    // ||c||^2 enters each point's sum through lane 0 of its group
+    const float own0 = q == 0 ? 1.0f : 0.0f;
 
     // items are claimed dynamically (largest jobs first), so the CTAs stay busy
     // when only a few jobs are still running
@@ -301,112 +349,179 @@ batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item
         for (long long tile = w.tile0; tile < t_end; ++tile) {
             for (int sub = 0; sub < C::NSUB; ++sub) {
                 const long long base = tile * kTile + (long long)sub * C::SUB;
-                float x[P][DC];
+                float x[P][DG];
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const long long i = base + (long long)p * kThreads + tid;
+                for (int s = 0; s < P; ++s) {
+                    const long long i = base + (long long)(s ^ (q * R)) * C::GROUPS + gi;
                     if constexpr (DC % 4 == 0) {
                         if ((d & 3) == 0) {
                             // rows are 16-byte aligned: one 128-bit load per 4 coordinates
 #pragma unroll
-                            for (int q = 0; q < DC / 4; ++q) {
+                            for (int cc = 0; cc < DG / 4; ++cc) {
+                                const int t0 = lane_dim<G>(4 * cc, q);
                                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (i < npts && 4 * q < d)
-                                    v = __ldg(reinterpret_cast<const float4*>(X + i * d) + q);
-                                x[p][4 * q] = v.x; x[p][4 * q + 1] = v.y;
-                                x[p][4 * q + 2] = v.z; x[p][4 * q + 3] = v.w;
+                                if (i < npts && t0 < d)
+                                    v = __ldg(reinterpret_cast<const float4*>(X + i * d + t0));
+                                x[s][4 * cc] = v.x; x[s][4 * cc + 1] = v.y;
+                                x[s][4 * cc + 2] = v.z; x[s][4 * cc + 3] = v.w;
                             }
                             continue;
                         }
                     }
 #pragma unroll
-                    for (int t = 0; t < DC; ++t) x[p][t] = (i < npts && t < d) ? __ldg(X + i * d + t) : 0.0f;
+                    for (int tt = 0; tt < DG; ++tt) {
+                        const int t = lane_dim<G>(tt, q);
+                        x[s][tt] = (i < npts && t < d) ? __ldg(X + i * d + t) : 0.0f;
+                    }
                 }
-                float B1[P], B2[P];
-                int BI[P];
+                float B1[R], B2[R];
+                int BI[R];
 #pragma unroll
-                for (int p = 0; p < P; ++p) { B1[p] = INFINITY; B2[p] = INFINITY; BI[p] = 0; }
+                for (int r = 0; r < R; ++r) { B1[r] = INFINITY; B2[r] = INFINITY; BI[r] = 0; }
                 for (int ch = 0; ch < kc; ch += 32) {
-                    float b1[P], b2[P];
+                    float b1[R], b2[R];
 #pragma unroll
-                    for (int p = 0; p < P; ++p) { b1[p] = INFINITY; b2[p] = INFINITY; }
+                    for (int r = 0; r < R; ++r) { b1[r] = INFINITY; b2[r] = INFINITY; }
 #pragma unroll 2
                     for (unsigned jj = 0; jj < 32; jj += 2) {
                         const float* c0 = sc + (ch + jj) * DC;
                         const float* c1 = c0 + DC;
-                        const float s0 = ss[ch + jj], s1 = ss[ch + jj + 1];
+                        const float s0 = ss[ch + jj] * own0, s1 = ss[ch + jj + 1] * own0;
+                        float a0[P], a1[P];
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            float d0 = s0, d1 = s1;
+                        for (int s = 0; s < P; ++s) { a0[s] = s0; a1[s] = s1; }
+                        if constexpr (G == 1) {
 #pragma unroll
-                            for (int t = 0; t < DC; ++t) {
-                                d0 = fmaf(x[p][t], c0[t], d0);
-                                d1 = fmaf(x[p][t], c1[t], d1);
+                            for (int s = 0; s < P; ++s) {
+#pragma unroll
+                                for (int t = 0; t < DC; ++t) {
+                                    a0[s] = fmaf(x[s][t], c0[t], a0[s]);
+                                    a1[s] = fmaf(x[s][t], c1[t], a1[s]);
+                                }
                             }
-                            const float k0 = pack_key(d0, jj), k1 = pack_key(d1, jj | 1u);
+                        } else {
+#pragma unroll
+                            for (int cc = 0; cc < DG / 4; ++cc) {
+                                const int t0 = lane_dim<G>(4 * cc, q);
+                                const float4 u0 = *reinterpret_cast<const float4*>(c0 + t0);
+                                const float4 u1 = *reinterpret_cast<const float4*>(c1 + t0);
+#pragma unroll
+                                for (int s = 0; s < P; ++s) {
+                                    a0[s] = fmaf(x[s][4 * cc], u0.x, a0[s]);
+                                    a1[s] = fmaf(x[s][4 * cc], u1.x, a1[s]);
+                                    a0[s] = fmaf(x[s][4 * cc + 1], u0.y, a0[s]);
+                                    a1[s] = fmaf(x[s][4 * cc + 1], u1.y, a1[s]);
+                                    a0[s] = fmaf(x[s][4 * cc + 2], u0.z, a0[s]);
+                                    a1[s] = fmaf(x[s][4 * cc + 2], u1.z, a1[s]);
+                                    a0[s] = fmaf(x[s][4 * cc + 3], u0.w, a0[s]);
+                                    a1[s] = fmaf(x[s][4 * cc + 3], u1.w, a1[s]);
+                                }
+                            }
+                            group_reduce<P, G>(a0);
+                            group_reduce<P, G>(a1);
+                        }
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const float k0 = pack_key(a0[r], jj), k1 = pack_key(a1[r], jj | 1u);
                             const float lo = fminf(k0, k1), hi = fmaxf(k0, k1);
-                            b2[p] = fmin3(b2[p], hi, fmaxf(b1[p], lo));
-                            b1[p] = fminf(b1[p], lo);
+                            b2[r] = fmin3(b2[r], hi, fmaxf(b1[r], lo));
+                            b1[r] = fminf(b1[r], lo);
                         }
                     }
 #pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (b1[p] < B1[p]) {
-                            B2[p] = fminf(B1[p], b2[p]);
-                            B1[p] = b1[p];
-                            BI[p] = ch | (int)(__float_as_uint(b1[p]) & 31u);
+                    for (int r = 0; r < R; ++r) {
+                        if (b1[r] < B1[r]) {
+                            B2[r] = fminf(B1[r], b2[r]);
+                            B1[r] = b1[r];
+                            BI[r] = ch | (int)(__float_as_uint(b1[r]) & 31u);
                         } else {
-                            B2[p] = fminf(B2[p], b1[p]);
+                            B2[r] = fminf(B2[r], b1[r]);
                         }
                     }
                 }
+                float xn2[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const long long i = base + (long long)p * kThreads + tid;
-                    const bool valid = i < npts;
-                    float xn2 = 0.f;
+                for (int s = 0; s < P; ++s) {
+                    float a = 0.f;
 #pragma unroll
-                    for (int t = 0; t < DC; ++t) xn2 = fmaf(x[p][t], x[p][t], xn2);
-                    const float thr = kappa * (thr_base + xn2) + tie_abs(d + 1) +
-                                      kPackSlack * (fabsf(B1[p]) + fabsf(B2[p]));
-                    const bool flag = valid && (B2[p] - B1[p] <= thr);
-                    if (mode == kModeFull && valid) {
+                    for (int tt = 0; tt < DG; ++tt) a = fmaf(x[s][tt], x[s][tt], a);
+                    xn2[s] = a;
+                }
+                group_reduce<P, G>(xn2);
+                if (mode == kModeFull) {
 #pragma unroll
-                        for (int t = 0; t < DC; ++t)
-                            if (t < d) qloc += sq_fixed(x[p][t], scaleF);
+                    for (int s = 0; s < P; ++s) {
+                        if (base + (long long)(s ^ (q * R)) * C::GROUPS + gi < npts) {
+#pragma unroll
+                            for (int tt = 0; tt < DG; ++tt)
+                                if (lane_dim<G>(tt, q) < d) qloc += sq_fixed(x[s][tt], scaleF);
+                        }
                     }
+                }
+                // decisions of the lane's own points: the new label where it
+                // changed (else -1) and the old one
+                int dec[R], olds[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const long long i = base + (long long)(r + q * R) * C::GROUPS + gi;
+                    const bool valid = i < npts;
+                    // a key adds up to d + G - 1 rounded products and sums
+                    const float thr = kappa * (thr_base + xn2[r]) + tie_abs(d + G) +
+                                      kPackSlack * (fabsf(B1[r]) + fabsf(B2[r]));
+                    const bool flag = valid && (B2[r] - B1[r] <= thr);
                     recheck_append(flag, (int)i, I->list, &st->recheck_count);
+                    dec[r] = -1;
+                    olds[r] = -1;
                     if (valid && !flag) {
-                        const int lab = BI[p];
+                        const int lab = BI[r];
                         const int old = (mode == kModeDelta) ? labels[i] : -1;
                         if (lab != old && label_ok(lab, I->c.k, st) &&
                             old_label_ok(old, I->c.k, st)) {
-#pragma unroll
-                            for (int t = 0; t < DC; ++t) {
-                                if (t >= d) break;
-                                const long long v = to_fixed(x[p][t], scaleF);
-                                if (C::SACC) {
-                                    atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * DC + t),
-                                              (unsigned long long)v);
-                                    if (old >= 0)
-                                        atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * DC + t),
-                                                  (unsigned long long)(-v));
-                                } else {
-                                    split_add(I->acc.s_lo + (long long)lab * d + t,
-                                              I->acc.s_hi + (long long)lab * d + t, v);
-                                    if (old >= 0)
-                                        split_add(I->acc.s_lo + (long long)old * d + t,
-                                                  I->acc.s_hi + (long long)old * d + t, -v);
-                                }
-                            }
-                            if (C::SACC) {
-                                atomicAdd(scnt + lab, 1);
-                                if (old >= 0) atomicAdd(scnt + old, -1);
-                            } else {
-                                atomicAdd(I->acc.cnt + lab, 1ull);
-                                if (old >= 0) atomicAdd(I->acc.cnt + old, ~0ull);
-                            }
+                            dec[r] = lab;
+                            olds[r] = old;
                             labels[i] = lab;
+                        }
+                    }
+                }
+                // exact sums: every lane moves its coordinates of each of its
+                // slots' points whose label changed (the decision comes from
+                // the point's owner, lane q ^ (s / R), slot s % R)
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    int lab = dec[s % R], old = olds[s % R];
+                    if constexpr (G > 1) {
+                        if (s / R != 0) {
+                            lab = __shfl_xor_sync(0xffffffffu, lab, s / R);
+                            old = __shfl_xor_sync(0xffffffffu, old, s / R);
+                        }
+                    }
+                    if (lab < 0) continue;
+#pragma unroll
+                    for (int tt = 0; tt < DG; ++tt) {
+                        const int t = lane_dim<G>(tt, q);
+                        if (t >= d) break;
+                        const long long v = to_fixed(x[s][tt], scaleF);
+                        if (C::SACC) {
+                            atomicAdd(reinterpret_cast<unsigned long long*>(sacc + lab * DC + t),
+                                      (unsigned long long)v);
+                            if (old >= 0)
+                                atomicAdd(reinterpret_cast<unsigned long long*>(sacc + old * DC + t),
+                                          (unsigned long long)(-v));
+                        } else {
+                            split_add(I->acc.s_lo + (long long)lab * d + t,
+                                      I->acc.s_hi + (long long)lab * d + t, v);
+                            if (old >= 0)
+                                split_add(I->acc.s_lo + (long long)old * d + t,
+                                          I->acc.s_hi + (long long)old * d + t, -v);
+                        }
+                    }
+                    if (s < R) {   // the owner counts its point once
+                        if (C::SACC) {
+                            atomicAdd(scnt + lab, 1);
+                            if (old >= 0) atomicAdd(scnt + old, -1);
+                        } else {
+                            atomicAdd(I->acc.cnt + lab, 1ull);
+                            if (old >= 0) atomicAdd(I->acc.cnt + old, ~0ull);
                         }
                     }
                 }
@@ -564,71 +679,84 @@ int dclass(int d)
     return 64;
 }
 
-template <int DC, int P>
+template <int DC, int P, int G>
 int launch_batch_assign(BatchInst* insts, const WorkItem* items, int nitems, int* next_item,
                         cudaStream_t s, int sm_count)
 {
     const size_t sm = batch_smem<DC>();
-    KM2_TRY(set_max_dynamic_smem((const void*)batch_assign<DC, P>, (int)sm));
+    KM2_TRY(set_max_dynamic_smem((const void*)batch_assign<DC, P, G>, (int)sm));
     int per_sm = 0;
-    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_assign<DC, P>, kThreads,
-                                                           sm));
+    KM2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_assign<DC, P, G>,
+                                                           kThreads, sm));
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)sm_count * per_sm;
     if (grid > nitems) grid = nitems;
     if (grid < 1) grid = 1;
     ++g_launches;
-    batch_assign<DC, P><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems, next_item);
+    batch_assign<DC, P, G><<<(int)grid, kThreads, sm, s>>>(insts, items, nitems, next_item);
     KM2_CUDA(cudaGetLastError());
     return KMEANS2_OK;
 }
 
-// Points per thread the autotuner may pick for a dimension class (as many as
-// the registers hold: a point is DC floats).
-std::vector<int> tile_points(int dc)
+// Tile shape of the distance kernel: point slots per lane and lanes per point.
+struct TileShape {
+    int p = 0;
+    int g = 0;
+};
+
+// Tile shapes the autotuner may pick for a dimension class: as many point
+// slots as the registers hold (a lane keeps p DC / g floats); shared points
+// (g > 1) for the wide classes, where one point per thread would spend a
+// shared-memory read on every FMA.
+std::vector<TileShape> tile_shapes(int dc)
 {
-    if (dc <= 16) return {2, 4};
-    if (dc <= 32) return {1, 2};
-    return {1};
+    if (dc <= 16) return {{2, 1}, {4, 1}};
+    if (dc <= 32) return {{1, 1}, {2, 1}, {4, 2}, {4, 4}};
+    return {{1, 1}, {2, 2}, {4, 4}};
 }
 
-// Debug builds (KM2_DEBUG_CHECKS): KMEANS2_DEBUG_BATCH_POINTS forces one tile
-// shape (a tile_points value) on every dimension class that offers it,
-// without tuning, so that a test can run each kernel variant; -1 otherwise.
-int forced_tile_points(int dc)
+// Debug builds (KM2_DEBUG_CHECKS): KMEANS2_DEBUG_BATCH_POINTS = "p" or "pxg"
+// forces one tile shape on every dimension class that offers it, without
+// tuning, so that a test can run each kernel variant; p = 0 otherwise.
+TileShape forced_tile_shape(int dc)
 {
 #ifdef KM2_DEBUG_CHECKS
     const char* v = std::getenv("KMEANS2_DEBUG_BATCH_POINTS");
     if (v && *v) {
-        const int p = (int)std::strtol(v, nullptr, 10);
-        for (int q : tile_points(dc))
-            if (q == p) return p;
+        char* end = nullptr;
+        TileShape f;
+        f.p = (int)std::strtol(v, &end, 10);
+        f.g = (end && *end == 'x') ? (int)std::strtol(end + 1, nullptr, 10) : 1;
+        for (const TileShape& t : tile_shapes(dc))
+            if (t.p == f.p && t.g == f.g) return f;
     }
 #else
     (void)dc;
 #endif
-    return -1;
+    return TileShape{};
 }
 
-int launch_class(int dc, int p, BatchInst* insts, const WorkItem* items, int nitems,
+int launch_class(int dc, TileShape sh, BatchInst* insts, const WorkItem* items, int nitems,
                  int* next_item, cudaStream_t s, int sm_count)
 {
-#define KM2_BA(DD, PP) \
-    if (dc == DD && p == PP) return launch_batch_assign<DD, PP>(insts, items, nitems, next_item, s, sm_count);
-    KM2_BA(2, 2) KM2_BA(2, 4) KM2_BA(4, 2) KM2_BA(4, 4) KM2_BA(8, 2) KM2_BA(8, 4)
-    KM2_BA(16, 2) KM2_BA(16, 4) KM2_BA(32, 1) KM2_BA(32, 2) KM2_BA(64, 1)
+#define KM2_BA(DD, PP, GG)                                                                  \
+    if (dc == DD && sh.p == PP && sh.g == GG)                                               \
+        return launch_batch_assign<DD, PP, GG>(insts, items, nitems, next_item, s, sm_count);
+    KM2_BA(2, 2, 1) KM2_BA(2, 4, 1) KM2_BA(4, 2, 1) KM2_BA(4, 4, 1) KM2_BA(8, 2, 1)
+    KM2_BA(8, 4, 1) KM2_BA(16, 2, 1) KM2_BA(16, 4, 1) KM2_BA(32, 1, 1) KM2_BA(32, 2, 1)
+    KM2_BA(32, 4, 2) KM2_BA(32, 4, 4) KM2_BA(64, 1, 1) KM2_BA(64, 2, 2) KM2_BA(64, 4, 4)
 #undef KM2_BA
     set_last_error_text("batched form: no kernel for this tile shape");
     return KMEANS2_ERR_UNSUPPORTED;
 }
 
 std::mutex g_tune_mu;
-// dimension class -> (points per thread, tiles per work item)
-std::map<int, std::pair<int, int>> g_tuned;
+// dimension class -> (tile shape, tiles per work item)
+std::map<int, std::pair<TileShape, int>> g_tuned;
 
 struct ClassItems {
     int dc = 0;
-    int p = 0;
+    TileShape shape;
     int tpi = 0;
     std::vector<WorkItem> host;
     WorkItem* dev = nullptr;
@@ -657,6 +785,19 @@ void build_items(ClassItems& ci, const std::vector<int>& members, const std::vec
 }  // namespace km2
 
 using namespace km2;
+
+extern "C" int kmeans2_batched_tile_shape(int32_t d, int32_t* points, int32_t* lanes,
+                                          int32_t* tiles)
+{
+    if (d < 1 || d > kMaxD || !points || !lanes || !tiles) return KMEANS2_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto f = g_tuned.find(dclass(d));
+    if (f == g_tuned.end()) return KMEANS2_ERR_INVALID;
+    *points = f->second.first.p;
+    *lanes = f->second.first.g;
+    *tiles = f->second.second;
+    return KMEANS2_OK;
+}
 
 extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmeans2_result* results,
                                    const kmeans2_options* opt)
@@ -781,29 +922,31 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
         for (auto& kv : members) {
             ClassItems ci;
             ci.dc = kv.first;
-            int tpi = 0, pts = 0;
-            const int forced = forced_tile_points(ci.dc);
-            if (forced >= 0) {
-                pts = forced;
+            int tpi = 0;
+            TileShape shape = forced_tile_shape(ci.dc);
+            if (shape.p > 0) {
                 tpi = 2;
             } else {
                 std::lock_guard<std::mutex> lock(g_tune_mu);
                 auto f = g_tuned.find(ci.dc);
-                if (f != g_tuned.end()) { pts = f->second.first; tpi = f->second.second; }
+                if (f != g_tuned.end()) { shape = f->second.first; tpi = f->second.second; }
             }
             if (tpi == 0) {
-                // time the real first pass for each tile shape (points per thread)
-                // and item size (tiles per work item), resetting the sums between
-                // trials: small items keep every SM busy once only a few jobs still
-                // run, more points per thread reuse each center load more often
+                // time the real first pass and a delta pass after it for each
+                // tile shape and item size (tiles per work item), resetting the
+                // sums between trials: small items keep every SM busy once only a
+                // few jobs still run, more point slots per lane reuse each center
+                // load more often
                 const int cand[4] = {1, 2, 4, 8};
                 static_assert(8 <= kMaxTilesPerItem, "item partial sums must stay below 2^62");
                 float best_ms = 0.f;
                 bool first = true;
-                cudaEvent_t e0, e1;
+                cudaEvent_t e0, e1, e2, e3;
                 KM2_CUDA(cudaEventCreate(&e0));
                 KM2_CUDA(cudaEventCreate(&e1));
-                for (int p : tile_points(ci.dc)) {
+                KM2_CUDA(cudaEventCreate(&e2));
+                KM2_CUDA(cudaEventCreate(&e3));
+                for (const TileShape& sh : tile_shapes(ci.dc)) {
                     for (int c = 0; c < 4; ++c) {
                         ClassItems trial;
                         build_items(trial, kv.second, nvec, cand[c]);
@@ -811,25 +954,43 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
                         KM2_CUDA(cudaMemcpyAsync(trial.dev, trial.host.data(),
                                                  sizeof(WorkItem) * (size_t)trial.count,
                                                  cudaMemcpyHostToDevice, s));
+                        // the full first pass, then a delta pass over the labels it
+                        // wrote (same centers: no label moves), which is what the
+                        // later iterations of a fit cost
                         KM2_CUDA(cudaMemsetAsync(counters + 2, 0, sizeof(int), s));
                         KM2_CUDA(cudaEventRecord(e0, s));
-                        KM2_TRY(launch_class(ci.dc, p, dinst, trial.dev, trial.count, counters + 2,
+                        KM2_TRY(launch_class(ci.dc, sh, dinst, trial.dev, trial.count, counters + 2,
                                              s, ws.sm_count));
                         KM2_CUDA(cudaEventRecord(e1, s));
-                        ++g_launches;
+                        g_launches += 2;
                         batch_reset_kernel<<<count, kThreads, 0, s>>>(dinst);
-                        KM2_CUDA(cudaEventSynchronize(e1));
-                        float ms = 0.f;
+                        batch_mode_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+                            dinst, count, kModeDelta);
+                        KM2_CUDA(cudaMemsetAsync(counters + 2, 0, sizeof(int), s));
+                        KM2_CUDA(cudaEventRecord(e2, s));
+                        KM2_TRY(launch_class(ci.dc, sh, dinst, trial.dev, trial.count, counters + 2,
+                                             s, ws.sm_count));
+                        KM2_CUDA(cudaEventRecord(e3, s));
+                        g_launches += 2;
+                        batch_reset_kernel<<<count, kThreads, 0, s>>>(dinst);
+                        batch_mode_kernel<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+                            dinst, count, kModeFull);
+                        KM2_CUDA(cudaEventSynchronize(e3));
+                        float ms = 0.f, ms2 = 0.f;
                         KM2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                        if (first || ms < best_ms) { best_ms = ms; tpi = cand[c]; pts = p; first = false; }
+                        KM2_CUDA(cudaEventElapsedTime(&ms2, e2, e3));
+                        ms += ms2;
+                        if (first || ms < best_ms) { best_ms = ms; tpi = cand[c]; shape = sh; first = false; }
                     }
                 }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
+                cudaEventDestroy(e2);
+                cudaEventDestroy(e3);
                 std::lock_guard<std::mutex> lock(g_tune_mu);
-                g_tuned[ci.dc] = std::make_pair(pts, tpi);
+                g_tuned[ci.dc] = std::make_pair(shape, tpi);
             }
-            ci.p = pts;
+            ci.shape = shape;
             build_items(ci, kv.second, nvec, tpi);
             KM2_TRY(ws.alloc((void**)&ci.dev, sizeof(WorkItem) * (size_t)ci.count, s));
             KM2_CUDA(cudaMemcpyAsync(ci.dev, ci.host.data(), sizeof(WorkItem) * (size_t)ci.count,
@@ -859,7 +1020,7 @@ extern "C" int kmeans2_fit_batched(int32_t count, const kmeans2_job* jobs, kmean
             if (cudaEventRecord(fork, s) != cudaSuccess) return KMEANS2_ERR_CUDA;
             for (size_t c = 0; c < classes.size(); ++c) {
                 if (cudaStreamWaitEvent(side[c], fork, 0) != cudaSuccess) return KMEANS2_ERR_CUDA;
-                const int r = launch_class(classes[c].dc, classes[c].p, dinst, classes[c].dev,
+                const int r = launch_class(classes[c].dc, classes[c].shape, dinst, classes[c].dev,
                                            classes[c].count,
                                            counters + 2 + c, side[c], ws.sm_count);
                 if (r != KMEANS2_OK) return r;

@@ -1,9 +1,10 @@
 """Every kernel variant of the batched form gives the single-fit results (GPU).
 
 The batched form picks, per dimension class, a tile shape by timing: the
-points per thread of its distance kernel.  Which one wins depends on the GPU
-and the workload, so the debug build (KMEANS2_DEBUG=1) accepts
-KMEANS2_DEBUG_BATCH_POINTS to force one shape on every class that offers it.
+point slots per lane of its distance kernel and the lanes that share a point
+("p" or "pxg").  Which one wins depends on the GPU and the workload, so the
+debug build (KMEANS2_DEBUG=1) accepts KMEANS2_DEBUG_BATCH_POINTS to force one
+shape on every class that offers it.
 A mixed batch (d from 3 to 64, d both a multiple of 4 and not, k from 1 to
 256) runs under each forced shape in a child process; labels, centers, J and
 iteration counts must equal kmeans2_fit on each job alone (release library,
@@ -74,7 +75,7 @@ def test_each_batched_tile_shape_equals_single_fits():
     build.build(debug=True)
     ref = _run(False)
     assert ref["lib"].endswith("libkmeans2.so")
-    for points in (1, 2, 4):
+    for points in ("1", "2", "4", "2x2", "4x2", "4x4"):
         got = _run(True, points)
         assert got["lib"].endswith("libkmeans2_debug.so")
         assert got["rc"] == 0, points
