@@ -151,3 +151,21 @@ def test_binding_rejects_mismatched_buffers_before_any_device_work(lib):
 
 def test_batched_binding_accepts_an_empty_job_list(lib):
     assert km.fit_batched([], [], 0.1, [], 1e-6, 10) == ([], 0)
+
+
+def test_batched_tile_shape_query_rejects_bad_arguments(lib):
+    """kmeans2_batched_tile_shape is host-only: d outside [1, 64] or a NULL
+    output is KMEANS2_ERR_INVALID, and before any batched call has tuned a
+    dimension class there is nothing to report."""
+    one = ctypes.c_int32(-7)
+    out = [ctypes.c_int32(-7) for _ in range(3)]
+    refs = [ctypes.byref(v) for v in out]
+    invalid = lib.kmeans2_batched_tile_shape(0, *refs)
+    assert invalid != 0 and km.strerror(invalid)
+    assert lib.kmeans2_batched_tile_shape(65, *refs) == invalid
+    assert lib.kmeans2_batched_tile_shape(8, None, ctypes.byref(one), ctypes.byref(one)) == invalid
+    assert [v.value for v in out] == [-7, -7, -7] and one.value == -7
+    assert km.batched_tile_shape(0) is None and km.batched_tile_shape(65) is None
+    import torch
+    if not torch.cuda.is_available():
+        assert km.batched_tile_shape(8) is None

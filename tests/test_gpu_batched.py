@@ -88,3 +88,20 @@ def test_batched_profiled_host_loop_equals_graph():
     want = sum(2.0 * (r.iters_fast * r.subset_size + r.iters_slow * s.n) * s.k * s.d
                for r, s in zip(b, specs))
     assert abs(prof.assign_flops - want) <= 1e-9 * want
+
+
+def test_batched_reports_its_tile_shapes():
+    """After a batched call the autotuner's choice is queryable per dimension
+    class, and it is one of the shapes that class offers."""
+    specs = [s for s in synth.instance_specs(64, seed=5, n_lo=2000, n_hi=20000, k_lo=2, k_hi=64)]
+    Xs = [synth.instance_data(s, device=DEV) for s in specs]
+    res, rc = km.fit_batched(Xs, [s.k for s in specs], 0.1, [s.seed for s in specs], 1e-5, 10)
+    assert rc == 0
+    offered = {2: {(2, 1), (4, 1)}, 8: {(2, 1), (4, 1)},
+               32: {(1, 1), (2, 1), (4, 2), (4, 4)}, 64: {(1, 1), (2, 2), (4, 4)}}
+    for d in sorted({s.d for s in specs}):
+        got = km.batched_tile_shape(d)
+        assert got is not None, d
+        p, g, tiles = got
+        assert (p, g) in offered[d], (d, got)
+        assert tiles in (1, 2, 4, 8), (d, got)
