@@ -198,6 +198,45 @@ def fp32_peak(dev, stream):
     return res
 
 
+def select_loop_ceiling(dev, stream, peak):
+    """The inner loop of the small-d distance kernel (d = 8, two points per
+    thread, centers as interleaved pairs in shared memory) timed alone by the
+    probe library: with the kernel's packed-key top-2, and with one minimum
+    per center pair instead (loads and FMAs only).  TFLOP/s of each (2 flop
+    per FMA, best of three launches) and as a fraction of `peak`; None if the
+    probe library cannot be loaded."""
+    import ctypes
+    import torch
+    path = os.path.join(ROOT, "paper_1108_1351_gb300", "libfp32peak.so")
+    try:
+        lib = ctypes.CDLL(path)
+        fn = lib.fp32_select_probe
+    except (OSError, AttributeError):
+        return None
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)]
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 4
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def run(mode, iters):
+        ms, fmas = ctypes.c_float(), ctypes.c_double()
+        rc = fn(mode, blocks, iters, ctypes.c_void_p(out.data_ptr()), sp, ctypes.byref(ms),
+                ctypes.byref(fmas))
+        if rc != 0:
+            raise RuntimeError(f"fp32_select_probe failed ({rc})")
+        return 2.0 * fmas.value / (ms.value * 1e-3) / 1e12, ms.value
+
+    res = {"loop": "d = 8, 2 points per thread, 32 centers per chunk, no global memory"}
+    for mode, name in ((0, "with_top2"), (1, "fma_only")):
+        rate, ms = run(mode, 200)                              # warm-up and calibration
+        iters = max(200, int(200 * 50.0 / max(ms, 1e-3)))     # ~50 ms per launch
+        best = max(run(mode, iters)[0] for _ in range(3))
+        res[name] = {"tflops": best, "frac": best / peak if peak else None}
+    return res
+
+
 def roofline_of(form: str, d: int, k: int, prof, clk, p32=None):
     """Roofline entry of the distance kernel the fit ran (the dominant kernel):
     algorithmic FLOP = 2 N k d per launch (the cross term only), achieved =
@@ -504,6 +543,9 @@ def run_ours(args, cfg):
     roofline = roofline_of(r0.precision_used, d, k, prof, clk, p32)
     roofline["measured"] = (f"{args.profile_fits} profiled fits after the timed region, CUDA "
                             f"events around each launch of the distance kernel")
+    if roofline.get("kernel") == "assign_small<8>":
+        # what the kernel's own inner loop reaches with nothing else around it
+        roofline["loop_ceiling"] = select_loop_ceiling(dev, stream, roofline.get("peak"))
     line = {
         "metric": METRIC, "value": total_evals / (ms_max * 1e-3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
