@@ -98,7 +98,8 @@ struct Bf16Args {
     const float* xn2;        // FP32 ||x||^2 per point
     const unsigned char* Cb; // BF16 -2c slices
     long long n;
-    int d, k, nc, nch, sb;   // chunk width NC, chunk count, B ring depth
+    int d, k, nc, nch, sb;   // chunk width NC, chunk count, B ring depth (slots)
+    int kps;                 // K-steps per B ring slot
     int lab_bulk;            // old labels can be bulk-copied (16-byte aligned)
     uint32_t tmem_cols;
     float kappa, kpack;
@@ -244,7 +245,13 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     constexpr uint32_t kParts = SINGLE ? 1u : 2u;                // operand parts
     const uint32_t Ahalf = (uint32_t)ksteps * 4096u;             // one part of a tile
     const uint32_t Abytes = kParts * Ahalf;
-    const uint32_t Sbytes = (uint32_t)NC * 32u * kParts;         // one (chunk, K-step) slice
+    // A slot of the B ring holds kps consecutive (chunk, K-step) slices of one
+    // chunk (contiguous in Cb): one bulk copy and one commit per slot, so the
+    // commits per chunk drop from d/16 + 1 to (d/16 + 1) / kps.
+    const int kPerSlot = a.kps;
+    const uint32_t Kbytes = (uint32_t)NC * 32u * kParts;         // one (chunk, K-step) slice
+    const uint32_t Sbytes = Kbytes * (uint32_t)kPerSlot;         // one slot of the B ring
+    const int kunits = (kslices + kPerSlot - 1) / kPerSlot;      // slots per chunk
     unsigned char* sA = smem;                                    // kSA x Abytes
     unsigned char* sB = smem + kSA * Abytes;                     // SB x Sbytes
     unsigned char* sOnes = sB + (size_t)SB * Sbytes;             // 128 x 16 BF16: [1, 1, 1, 0, ...]
@@ -319,20 +326,21 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                 tc::mbar_wait(&bars.side_full[i % kSR], (uint32_t)((i / kSR) & 1), kWaitTries);
         }
     } else if (warp == 1) {
-        // ---------------- B producer: slice q = (unit, K-step) -> stage q % SB
+        // ---------------- B producer: slot q = (pair, chunk, K-step group) -> stage q % SB
         if (lane == 0) {
             // slices go once per PAIR of tiles (both tiles' MMAs read each slice)
-            const long long total = ((cnt + 1) / 2) * nch * kslices;
+            const long long total = ((cnt + 1) / 2) * nch * kunits;
             long long q = 0;
             for (; q < total; ++q) {
                 const int slot = (int)(q % SB);
                 if (!wait_bar(&bars.b_empty[slot], (uint32_t)(((q / SB) & 1) ^ 1), abort_v, st))
                     break;
-                const long long unit = q / kslices;
-                const int ch = (int)(unit % nch), ks = (int)(q % kslices);
-                mbar_expect_tx(&bars.b_full[slot], Sbytes);
-                bulk_load(sB + (size_t)slot * Sbytes, a.Cb + ((size_t)ch * kslices + ks) * Sbytes,
-                          Sbytes, &bars.b_full[slot]);
+                const long long unit = q / kunits;
+                const int ch = (int)(unit % nch), ks0 = (int)(q % kunits) * kPerSlot;
+                const uint32_t bytes = Kbytes * (uint32_t)min(kPerSlot, kslices - ks0);
+                mbar_expect_tx(&bars.b_full[slot], bytes);
+                bulk_load(sB + (size_t)slot * Sbytes, a.Cb + ((size_t)ch * kslices + ks0) * Kbytes,
+                          bytes, &bars.b_full[slot]);
             }
             for (long long r = q > SB ? q - SB : 0; r < q; ++r)
                 tc::mbar_wait(&bars.b_full[r % SB], (uint32_t)((r / SB) & 1), kWaitTries);
@@ -361,35 +369,38 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
                         break;
                     tc::fence_after_sync();
                     const uint32_t d0 = tmem + (uint32_t)(b0 * NC), d1 = tmem + (uint32_t)(b1 * NC);
-                    for (int ks = 0; ks < kslices; ++ks, ++q) {
+                    for (int u = 0; u < kunits; ++u, ++q) {
                         const int slot = (int)(q % SB);
                         if (!(ok = wait_bar(&bars.b_full[slot], (uint32_t)((q / SB) & 1), abort_v, st, ctries)))
                             break;
                         tc::fence_after_sync();
-                        const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes;
-                        if (ks < ksteps && SINGLE) {
+                        const int ks0 = u * kPerSlot, ks1 = min(ks0 + kPerSlot, kslices);
+                        for (int ks = ks0; ks < ks1; ++ks) {
+                            const uint32_t bh = sBaddr + (uint32_t)slot * Sbytes + (uint32_t)(ks - ks0) * Kbytes;
+                            if (ks < ksteps && SINGLE) {
 #pragma unroll
-                            for (int t = 0; t < 2; ++t) {
-                                if (t == 1 && !two) break;
-                                const uint32_t dt = t ? d1 : d0;
-                                const uint32_t ah = sAaddr + (uint32_t)t * Abytes + (uint32_t)ks * 4096u;
-                                tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc16, ks > 0 ? 1u : 0u);
-                            }
-                        } else if (ks < ksteps) {
-                            const uint32_t bl = bh + (uint32_t)NC * 32u;
+                                for (int t = 0; t < 2; ++t) {
+                                    if (t == 1 && !two) break;
+                                    const uint32_t dt = t ? d1 : d0;
+                                    const uint32_t ah = sAaddr + (uint32_t)t * Abytes + (uint32_t)ks * 4096u;
+                                    tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc16, ks > 0 ? 1u : 0u);
+                                }
+                            } else if (ks < ksteps) {
+                                const uint32_t bl = bh + (uint32_t)NC * 32u;
 #pragma unroll
-                            for (int t = 0; t < 2; ++t) {
-                                if (t == 1 && !two) break;
-                                const uint32_t dt = t ? d1 : d0;
-                                const uint32_t ah = sAaddr + (uint32_t)t * Abytes + (uint32_t)ks * 4096u;
-                                tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
-                                tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
-                                tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                                for (int t = 0; t < 2; ++t) {
+                                    if (t == 1 && !two) break;
+                                    const uint32_t dt = t ? d1 : d0;
+                                    const uint32_t ah = sAaddr + (uint32_t)t * Abytes + (uint32_t)ks * 4096u;
+                                    tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bh), idesc, ks > 0 ? 1u : 0u);
+                                    tc::mma_bf16(dt, tc::smem_desc(ah), tc::smem_desc(bl), idesc, 1u);
+                                    tc::mma_bf16(dt, tc::smem_desc(ah + Ahalf), tc::smem_desc(bh), idesc, 1u);
+                                }
+                            } else {
+                                // + ||c||^2: ones x (nh, nm, nl)
+                                tc::mma_bf16(d0, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
+                                if (two) tc::mma_bf16(d1, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
                             }
-                        } else {
-                            // + ||c||^2: ones x (nh, nm, nl)
-                            tc::mma_bf16(d0, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
-                            if (two) tc::mma_bf16(d1, tc::smem_desc(sOnesAddr), tc::smem_desc(bh), idesc, 1u);
                         }
                         tc::mma_commit(&bars.b_empty[slot]);
                     }
@@ -955,13 +966,20 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     uint32_t cols = 32;
     while (cols < (uint32_t)(kEpiGroups * (NC >= 256 ? 1 : 2) * NC)) cols <<= 1;
     const size_t parts = single ? 1 : 2;
-    const size_t abytes = parts * 2 * kRows * d, sbytes = (size_t)NC * 32 * parts;
-    int sb = (int)((kSmemBudget - kStaticSmem - kSA * abytes - 4096) / sbytes);
-    if (sb > kMaxSB) sb = kMaxSB;
-    if (sb < 2) {
+    const size_t abytes = parts * 2 * kRows * d, kbytes = (size_t)NC * 32 * parts;
+    // a B ring slot holds kps K-steps of a chunk: five in the single-pass form,
+    // one in the split form, fewer when the ring would drop below two slots
+    int kps = single ? 5 : 1, sb = 0;
+    for (; kps >= 1; --kps) {
+        sb = (int)((kSmemBudget - kStaticSmem - kSA * abytes - 4096) / (kbytes * kps));
+        if (sb >= 2) break;
+    }
+    if (kps < 1 || sb < 2) {
         set_last_error_text("assign_bf16: shared-memory budget too small for this d");
         return KMEANS2_ERR_UNSUPPORTED;
     }
+    if (sb > kMaxSB) sb = kMaxSB;
+    const size_t sbytes = kbytes * kps;
     const size_t smem = kSA * abytes + (size_t)sb * sbytes + 4096;
     // one fixed limit for both instantiations (the static part holds the
     // barriers, the side ring and the recheck queues)
@@ -987,6 +1005,7 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     a.nc = NC;
     a.nch = nch;
     a.sb = sb;
+    a.kps = kps;
     a.lab_bulk = (reinterpret_cast<uintptr_t>(labels) & 15) == 0 ? 1 : 0;
     a.tmem_cols = cols;
     a.kappa = single ? f16_kappa(d) : bf16_kappa(d);
