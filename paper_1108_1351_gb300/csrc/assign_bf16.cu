@@ -247,8 +247,9 @@ assign_bf16(Bf16Args a, Centers c, int* __restrict__ labels, StageState* st, Acc
     const uint32_t Abytes = kParts * Ahalf;
     // A slot of the B ring holds kps consecutive (chunk, K-step) slices of one
     // chunk (contiguous in Cb): one bulk copy and one commit per slot, so the
-    // commits per chunk drop from d/16 + 1 to (d/16 + 1) / kps.
-    const int kPerSlot = a.kps;
+    // commits per chunk drop from d/16 + 1 to (d/16 + 1) / kps.  The split
+    // form keeps one slice per slot (a compile-time 1, no extra issuer work).
+    const int kPerSlot = SINGLE ? a.kps : 1;
     const uint32_t Kbytes = (uint32_t)NC * 32u * kParts;         // one (chunk, K-step) slice
     const uint32_t Sbytes = Kbytes * (uint32_t)kPerSlot;         // one slot of the B ring
     const int kunits = (kslices + kPerSlot - 1) / kPerSlot;      // slots per chunk
@@ -967,8 +968,8 @@ int launch_assign_bf16(const float* X, const unsigned char* Xt, const float* xn2
     while (cols < (uint32_t)(kEpiGroups * (NC >= 256 ? 1 : 2) * NC)) cols <<= 1;
     const size_t parts = single ? 1 : 2;
     const size_t abytes = parts * 2 * kRows * d, kbytes = (size_t)NC * 32 * parts;
-    // a B ring slot holds kps K-steps of a chunk: five in the single-pass form,
-    // one in the split form, fewer when the ring would drop below two slots
+    // a B ring slot holds kps K-steps of a chunk: five in the single-pass form
+    // (fewer when the ring would drop below two slots), one in the split form
     int kps = single ? 5 : 1, sb = 0;
     for (; kps >= 1; --kps) {
         sb = (int)((kSmemBudget - kStaticSmem - kSA * abytes - 4096) / (kbytes * kps));
