@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(kThreads) batch_mode_kernel(BatchInst* insts, 
 
 // ---------------------------------------------------------------- assign
 
-// Tile shape of a dimension class.  G lanes share each point: lane q of a
-// group holds coordinates 4 (c G + q) .. 4 (c G + q) + 3 (c = 0, 1, ...) of
+// Tile shape of a dimension class.  G lanes share each point (a group is G
+// adjacent lanes of a warp): lane q of a group holds coordinates 4 (c G + q) .. 4 (c G + q) + 3 (c = 0, 1, ...) of
 // the group's P points, so every center value a lane reads from shared memory
 // serves P FMAs while the lane keeps only P DC / G coordinates in registers.
 // The G partial dot products of a point are added across the group with xor
