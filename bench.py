@@ -198,6 +198,35 @@ def fp32_peak(dev, stream):
     return res
 
 
+def h2d_rate(Xh, dev, nbytes: int = 1 << 31):
+    """GB/s of a host -> device copy of the first `nbytes` of the pinned host
+    tensor Xh into a fresh device buffer (best of three, CUDA events on a
+    private stream; untimed diagnostic beside the end-to-end number).  None
+    if the copy cannot be made."""
+    import torch
+    try:
+        flat = Xh.reshape(-1).view(torch.uint8)
+        nbytes = min(nbytes, flat.numel())
+        src = flat[:nbytes]
+        dst = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        s = torch.cuda.Stream(dev)
+        best = None
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                dst.copy_(src, non_blocking=True)
+                e1.record(s)
+                e1.synchronize()
+                gbs = nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+                best = gbs if best is None else max(best, gbs)
+        del dst
+        return best
+    except Exception:
+        return None
+
+
 def select_loop_ceiling(dev, stream, peak):
     """The inner loop of the small-d distance kernel (d = 8, two points per
     thread, centers as interleaved pairs in shared memory) timed alone by the
@@ -530,7 +559,8 @@ def run_ours(args, cfg):
         te_ms, ee = reduce_over_ranks(1e3 * (time.perf_counter() - t0), e_evals, ws, dev)
         e2e = {"value": ee / (te_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * 4 + k * d * 8,
-               "steps": args.e2e_steps, "ms_per_step": te_ms / args.e2e_steps}
+               "steps": args.e2e_steps, "ms_per_step": te_ms / args.e2e_steps,
+               "h2d_gbs_measured": h2d_rate(Xh, dev)}
         Xh_host = Xh.numpy()
     else:
         Xh_host = X[: min(n, 2_000_000)].cpu().numpy()
