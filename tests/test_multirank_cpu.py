@@ -273,3 +273,28 @@ def test_traffic_line_is_used_only_for_the_source_it_was_measured_on(tmp_path, m
     assert bench.traffic_of("assign_small<8>", Prof, 8) is None       # no line for it
     src.write_text("// kernel v2\n")                                   # source changed since
     assert bench.traffic_of("assign_bf16", Prof, 128) is None
+
+
+def test_committed_traffic_lines_match_the_kernel_sources():
+    """Every 'traffic-per-point:' line under profiles/ is keyed to the sha256 of
+    the kernel source it was captured on, and the bench drops a line whose
+    source has changed since.  The committed lines must therefore match the
+    committed sources, or the bench's roofline would report no traffic."""
+    import glob
+    import hashlib
+    src_of = {"assign_small": "assign_fp32.cu", "assign_large": "assign_fp32.cu",
+              "assign_bf16": "assign_bf16.cu", "assign_tc32": "assign_tc32.cu"}
+    found = 0
+    for md in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(md) as fh:
+            for line in fh:
+                parts = line.strip().strip("`").split()
+                if len(parts) != 4 or parts[0] != "traffic-per-point:":
+                    continue
+                found += 1
+                src = src_of[parts[1].split("<")[0]]
+                with open(os.path.join(ROOT, "paper_1108_1351_gb300", "csrc", src), "rb") as f:
+                    sha = hashlib.sha256(f.read()).hexdigest()
+                assert parts[3] == sha, (os.path.basename(md), parts[1])
+                assert float(parts[2]) > 0
+    assert found >= 2
