@@ -20,13 +20,13 @@
 //
 // Warp-specialised pipeline, one CTA per SM, 11 warps:
 //   warp 0  A producer: one bulk TMA copy per tile into a 2-stage ring;
-//   warp 1  B producer: one bulk TMA copy per (chunk, K-step) slice into an
-//           SB-stage ring (SB <= 8);
+//   warp 1  B producer: one bulk TMA copy per ring slot (SB <= 8 slots) of
+//           one (chunk, K-step) slice, five of a chunk in the single pass;
 //   warp 2  MMA issuer: tiles go in pairs (one per epilogue group and A
 //           stage); per (pair, chunk) unit and K-step it issues 3 MMAs
 //           (M 128, N NC, K 16) for each tile of the pair into its TMEM
 //           accumulator, so each B slice is read from L2 once for 256 points;
-//           tcgen05.commit frees each slice and both tiles and hands the
+//           tcgen05.commit frees each slot and both tiles and hands the
 //           accumulators to the epilogues;
 //   warps 3-6, 7-10  two epilogue groups taking alternate tiles, each with its
 //           own two TMEM accumulators (4 x NC columns in all): a thread owns
